@@ -1,0 +1,381 @@
+"""Benchmark of the indel-free scan on the B300.
+
+Workload (one step): 10 queries of 30-40 bp against a 4 Gbp synthetic
+reference (GC 40%, log-normal contigs of 1 kbp - 5 Mbp, 0.1% N in runs of
+10-1000, 1000 planted hits per substitution count k <= 16), scanned on both
+strands in brute-force mode at maxSubs 0, 4, 8 and 16 -- one full pass of
+the reference per maxSubs value, streamed as 256 MB segments.
+
+* value: query-base comparisons per second (nominal: sum over windows of the
+  query length, both strands) with the ASCII reference already resident in
+  HBM; pack + scan + hit compaction run inside the timed region.
+* e2e: the same metric through the C ABI from pinned host memory, with the
+  host-to-device segment copies and the device-to-host hit drain inside
+  the timed region.
+* roofline: the brute-force scan kernel against the POPC pipe (one POPC per
+  window evaluation of the first 32-base word), launch durations from CUDA
+  events inside the library on the compute stream.
+* cpu_baseline: the CPU oracle on a bounded sample of the same workload.
+
+`--impl reference` times the CPU oracle instead (the reference arm).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "query-base comparisons/s and ref Gbp/s scanned (% of roofline); p50/p99 latency"
+UNIT = "query-base comparisons/s"
+SUBS = (0, 4, 8, 16)
+SEG = 256 << 20
+POPC_PER_CLK_SM = 16  # 32-bit population count issue rate per SM per clock (CUDA guide, cc 10.x)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--total", type=float, default=4e9, help="reference bases (default 4 Gbp)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(total):
+    import synth
+    return synth.workload_4gbp(total=int(total))
+
+
+def nominal_work(wl, contig_sel=None):
+    """(windows, query-base comparisons) for one maxSubs pass, both strands."""
+    lens = wl.contig_len if contig_sel is None else wl.contig_len[contig_sel]
+    win = 0
+    qb = 0
+    for q in wl.queries:
+        L = len(q)
+        w = int(np.maximum(lens - L + 1, 0).sum())
+        win += 2 * w
+        qb += 2 * w * L
+    return win, qb
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def traffic_record():
+    """DRAM bytes per scan launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "scan_brute_4gbp_traffic.txt")
+    src = os.path.join(ROOT, "paper_2607_27291_b300", "csrc", "scan_brute.cu")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if kv.get("kernel_source_sha256_16") != digest:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_sample(wl, target_bases):
+    """First contigs covering about `target_bases` (the oracle's sample)."""
+    c = np.cumsum(wl.contig_len)
+    n = int(np.searchsorted(c, target_bases)) + 1
+    n = min(n, len(wl.contig_len))
+    return np.arange(n)
+
+
+def time_oracle(wl, sel, subs=SUBS):
+    import oracle
+    threads = os.cpu_count() or 1
+    end = int(wl.contig_len[sel].sum())
+    ref = wl.ref[:end]
+    lens = wl.contig_len[sel]
+    t0 = time.perf_counter()
+    for s in subs:
+        oracle.brute(wl.queries, ref, lens, s, threads=threads)
+    dt = time.perf_counter() - t0
+    _, qb = nominal_work(wl, sel)
+    return qb * len(subs) / dt, threads, dt, end
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = make_workload(args.total)
+    sel = cpu_sample(wl, 4_000_000)
+    for _ in range(max(0, args.warmup)):
+        time_oracle(wl, sel[:1])
+    vals = []
+    dts = []
+    for _ in range(args.steps):
+        v, threads, dt, nb = time_oracle(wl, sel)
+        vals.append(v)
+        dts.append(dt)
+    value = float(np.mean(vals))
+    sample = "first %d contigs (%d bases) of the 4 Gbp reference, maxSubs %s" % (
+        len(sel), nb, "/".join(map(str, SUBS)))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(dts)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": "10q30-40bp_4Gbp_GC40_sweep0-4-8-16", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2607_27291_b300 as P
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    t_gen = time.perf_counter()
+    wl = make_workload(args.total)
+    t_gen = time.perf_counter() - t_gen
+    segs = list(P.segment_pieces(wl.contig_len, SEG))
+    ref_dev = torch.from_numpy(wl.ref).to(f"cuda:{dev}")
+    stream = torch.cuda.Stream(device=dev)
+    hcap = 1 << 28
+    h = P.ifa_create(device=dev, hit_capacity=hcap, segment_bytes=SEG, profile=1)
+    P.ifa_set_stream(h, stream)
+    P.ifa_load_queries(h, wl.queries)
+    P.ifa_set_mode(h, P.IFA_MODE_BRUTE)
+    win_pass, qb_pass = nominal_work(wl)
+
+    def one_pass(s, source, drain):
+        P.ifa_reset_results(h)
+        P.ifa_set_max_subs(h, s)
+        for a, b, pc in segs:
+            P.ifa_push_segment(h, source[a:b], pc)
+        if drain:
+            hits, _ = P.ifa_drain_hits(h)
+            return hits.size
+        return 0
+
+    # ---- device-resident timed region
+    for _ in range(args.warmup):
+        for s in SUBS:
+            one_pass(s, ref_dev, False)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = Clocks(dev)
+    clocks.start()
+    step_ms = []
+    per_s = {s: [] for s in SUBS}
+    scan_ns = 0
+    scan_launches = 0
+    launches = 0
+    hits_per_s = {}
+    ev_all0 = torch.cuda.Event(enable_timing=True)
+    ev_all1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev_all0.record(stream)
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in SUBS:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            one_pass(s, ref_dev, False)
+            b.record(stream)
+            st = P.ifa_get_stats(h)
+            scan_ns += st["scan_ns"]
+            scan_launches += st["scan_launches"]
+            launches += st["kernel_launches"]
+            dg, _ = P.ifa_get_digest(h)
+            hits_per_s[s] = dg[0]
+            per_s[s].append(a.elapsed_time(b))
+        e1 = torch.cuda.Event(enable_timing=True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    ev_all1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    total_ms = ev_all0.elapsed_time(ev_all1)
+    total_ms = allmax(total_ms, world)
+    steps = args.steps
+    qb_step = qb_pass * len(SUBS)
+    value = world * qb_step * steps / (total_ms * 1e-3)
+    gbps = world * wl.ref.size * len(SUBS) * steps / (total_ms * 1e-3) / 1e9
+
+    # ---- roofline of the scan kernel (POPC pipe)
+    peaks = measured_peaks()
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    avg_launch_s = (scan_ns * 1e-9) / max(1, scan_launches)
+    evals_per_launch = win_pass * len(SUBS) * steps / max(1, scan_launches)
+    achieved = evals_per_launch / avg_launch_s / 1e9           # G popc / s
+    peak = sms * POPC_PER_CLK_SM * sm_mhz * 1e6 / 1e9          # G popc / s
+    traffic = traffic_record()
+
+    # ---- end to end through pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        del ref_dev
+        torch.cuda.empty_cache()
+        ref_pin = torch.from_numpy(wl.ref).pin_memory()
+        one_pass(SUBS[0], ref_pin, True)  # warm the pinned path
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for s in SUBS:
+            n = one_pass(s, ref_pin, True)
+            d2h += n * 16 + 24
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        dt = allmax(dt, world)
+        e2e = {"value": world * qb_step / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(wl.ref.size) * len(SUBS), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": dt * 1e3, "pcie_h2d_gbps": wl.ref.size * len(SUBS) / dt / 1e9}
+    P.ifa_destroy(h)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sel = cpu_sample(wl, 4_000_000)
+        v, threads, dt, nb = time_oracle(wl, sel)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "first %d contigs (%d bases) at maxSubs 0/4/8/16, %.1f s" % (
+                   len(sel), nb, dt)}
+
+    if rank != 0:
+        return
+    lat = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "10q30-40bp_4Gbp_GC40_sweep0-4-8-16",
+                   "reference_bases": int(wl.ref.size), "contigs": int(wl.contig_len.size),
+                   "queries": len(wl.queries), "query_lengths": [len(q) for q in wl.queries],
+                   "max_subs": list(SUBS), "segment_bytes": SEG, "mode": "brute-force",
+                   "l2": "inputs (4 GB ASCII, 2 GB packed) exceed the 126 MB L2; no flush",
+                   "generation_s": round(t_gen, 1)},
+        "ref_gbps": gbps,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "what": "one step (4 passes over 4 Gbp)"},
+        "sweep": {str(s): {"ms": float(np.mean(per_s[s])), "hits": int(hits_per_s[s]),
+                           "qbase_per_s": qb_pass / (float(np.mean(per_s[s])) * 1e-3)}
+                  for s in SUBS},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpopc/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_scan_brute", "launches": scan_launches,
+                     "avg_launch_ms": avg_launch_s * 1e3,
+                     "peak_basis": "%d SMs x %d POPC/clk/SM x %.0f MHz (median SM clock sampled "
+                                   "during the timed region)" % (sms, POPC_PER_CLK_SM, sm_mhz)},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * ifa.h -- C ABI of the B300 indel-free (Hamming) aligner.
+ *
+ * The calls follow the paper's statement of the problem (IndelFreeAligner,
+ * Methods, "Algorithm Design" and "Memory Management"): the query set is
+ * loaded once, a maxSubs threshold with no upper limit is set, the mode is
+ * chosen explicitly or automatically, the reference is streamed past the
+ * queries segment by segment and never indexed, and hits come out as the
+ * stream goes (Methods, "Output Format").
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an ifa_status; none aborts the process.  On failure
+ *    ifa_last_error() describes the cause.
+ *  - A handle is used by one host thread at a time.
+ *  - Pointers are host pointers unless a parameter says otherwise.  The
+ *    library copies what it needs before returning unless stated otherwise;
+ *    the caller keeps ownership of every buffer it passes.
+ *  - Sequences are ASCII.  A, C, G, T in either case are bases; every other
+ *    byte is N, and N mismatches everything on either side (a reading: the
+ *    paper only says reference Ns are tracked apart from substitutions,
+ *    Methods, "Algorithm Design").
+ *  - Positions are 0-based.  Strand 0 is '+', strand 1 is '-'; a '-' hit at
+ *    pos means the reverse complement of the query lies at
+ *    ref[pos .. pos+L-1] with `mismatches` substitutions.  A window never
+ *    leaves its contig (no soft clipping), so contigs shorter than a query
+ *    give it no hit.
+ *  - Query ids are dense in load order.  Contig ids are the caller's; each
+ *    new contig's id must be larger than the previous one's.
+ *  - Device work runs on the handle's compute stream (ifa_set_stream) and
+ *    a private copy stream; results are complete after ifa_flush().
+ */
+#ifndef IFA_H
+#define IFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IFA_ABI_VERSION 1
+#define IFA_MAX_QUERY_LEN 255u   /* longest query, in bases */
+#define IFA_MAX_KLIST 8u
+
+typedef struct ifa_handle ifa_handle;
+
+typedef enum {
+    IFA_OK = 0,
+    IFA_ERR_INVALID_ARG = 1,   /* bad pointer, size, id order or piece table */
+    IFA_ERR_OOM = 2,           /* a host or device allocation failed */
+    IFA_ERR_CUDA = 3,          /* a CUDA call failed (no device, launch error) */
+    IFA_ERR_BAD_STATE = 4,     /* call not allowed now (e.g. queries after segments) */
+    IFA_ERR_HIT_OVERFLOW = 5,  /* the device hit buffer filled; see ifa_drain_hits */
+    IFA_ERR_TIMEOUT = 6        /* a bounded device wait gave up */
+} ifa_status;
+
+typedef enum {
+    IFA_MODE_AUTO = 0,     /* indexed when the query count reaches the config's crossover */
+    IFA_MODE_BRUTE = 1,    /* every window of every contig, both strands */
+    IFA_MODE_INDEXED = 2   /* query k-mer seeds + min-hits threshold + verification */
+} ifa_mode;
+
+typedef enum {
+    IFA_MEM_HOST = 0,         /* pageable host memory: copied through pinned staging */
+    IFA_MEM_HOST_PINNED = 1,  /* page-locked host memory: DMA'd directly */
+    IFA_MEM_DEVICE = 2        /* device memory on the handle's device */
+} ifa_mem;
+
+/* One reported alignment (16 bytes). */
+typedef struct {
+    uint32_t query;       /* query id */
+    uint32_t contig;      /* caller's contig id */
+    uint32_t pos;         /* leftmost forward coordinate in the contig */
+    uint8_t strand;       /* 0 '+', 1 '-' */
+    uint8_t mismatches;   /* Hamming distance of the window */
+    uint16_t reserved;    /* 0 */
+} ifa_hit;
+
+/* Order-independent digest of every hit produced so far: the count, and
+ * the sum (mod 2^64) and xor of mix(a ^ mix(b)) over hits, where
+ * a = query << 32 | contig, b = pos << 32 | strand << 8 | mismatches and
+ * mix is the splitmix64 output function.  Kept apart from the hit buffer,
+ * so it stays exact when that buffer overflows or is disabled. */
+typedef struct {
+    uint64_t count;
+    uint64_t sum;
+    uint64_t xr;
+} ifa_digest;
+
+/* One contig piece inside a pushed segment.  Pieces of one segment are
+ * given in order, are contiguous and cover the segment exactly
+ * (start_0 = 0, start_{i+1} = start_i + len_i, sum len = segment length).
+ * A piece whose `last` is 0 continues in the next segment; the next
+ * segment's first piece then carries the same contig id with
+ * offset_in_contig advanced by len.  Only a segment's last piece may have
+ * last = 0. */
+typedef struct {
+    uint32_t contig;
+    uint32_t last;
+    uint64_t offset_in_contig;
+    uint64_t start;
+    uint64_t len;
+} ifa_piece;
+
+typedef struct {
+    int32_t device;                /* CUDA device ordinal */
+    uint32_t count_only;           /* 1: keep digest/counts only, write no hit tuples */
+    uint64_t hit_capacity;         /* device hit buffer entries */
+    uint64_t segment_bytes;        /* largest segment accepted by ifa_push_segment */
+    /* indexed mode (Methods, indexed mode) */
+    uint32_t k_list[IFA_MAX_KLIST];/* candidate seed lengths, paper default 8,9,10,12,14 */
+    uint32_t n_k;
+    uint32_t kmer_step;            /* query k-mer offset step (reading: 1) */
+    uint32_t mask_width;           /* masked middle bases of each k-mer (reading: 0) */
+    uint32_t minhits_num;          /* detection probability num/den, paper default 99.9% */
+    uint32_t minhits_den;
+    uint32_t minhits_trials;       /* Monte Carlo trials, paper default 200,000 */
+    uint64_t minhits_seed;         /* Philox key of the Monte Carlo */
+    uint32_t max_clips;            /* must be 0: soft clipping is not implemented */
+    uint32_t exhaustive_fallback;  /* 1: queries with no qualifying k are scanned exhaustively */
+    uint32_t auto_crossover;       /* IFA_MODE_AUTO picks indexed from this many queries on */
+    uint32_t profile;              /* 1: time every scan kernel with CUDA events (ifa_stats.scan_ns) */
+    uint32_t reserved[6];
+} ifa_config;
+
+typedef struct {
+    uint64_t segments;        /* segments pushed */
+    uint64_t bases;           /* reference bases pushed (one strand) */
+    uint64_t h2d_bytes;       /* bytes copied host -> device for segments */
+    uint64_t windows;         /* (query, strand, window) evaluations, nominal */
+    uint64_t query_bases;     /* query-base comparisons, nominal */
+    uint64_t kernel_launches; /* device kernels launched */
+    uint64_t candidates;      /* indexed mode: candidate windows verified */
+    uint64_t scan_launches;   /* scan kernels timed (config.profile = 1) */
+    uint64_t scan_ns;         /* their summed device time, from CUDA events on the compute stream */
+} ifa_stats;
+
+/* Fill *cfg with the defaults (paper defaults where it gives one).
+ * INVALID_ARG if cfg is NULL. */
+ifa_status ifa_config_default(ifa_config *cfg);
+
+/* Create a handle on cfg->device; allocates device buffers for one segment
+ * pair, the hit buffer and the digest.  *out is NULL on failure.
+ * Errors: INVALID_ARG (NULL, max_clips != 0, bad k list), CUDA (no such
+ * device), OOM. */
+ifa_status ifa_create(const ifa_config *cfg, ifa_handle **out);
+
+/* Free everything the handle owns (waits for its device work).  NULL is a
+ * no-op. */
+void ifa_destroy(ifa_handle *h);
+
+/* Use `stream` (a cudaStream_t of the handle's device, or NULL for the
+ * library's own stream) as the compute stream for later calls. */
+ifa_status ifa_set_stream(ifa_handle *h, void *stream);
+
+/* Append n queries (the query set is loaded once at startup, Methods,
+ * "Memory Management").  seqs[i] points at lens[i] ASCII bytes,
+ * 1 <= lens[i] <= IFA_MAX_QUERY_LEN.  *first_id (may be NULL) receives the
+ * id of the first appended query.  Copies the sequences.
+ * BAD_STATE once a segment has been pushed since the last reset. */
+ifa_status ifa_load_queries(ifa_handle *h, const uint8_t *const *seqs, const uint32_t *lens,
+                            uint32_t n, uint32_t *first_id);
+
+/* maxSubs for segments pushed from now on; any value (no upper limit,
+ * Methods; a value >= L reports every window). */
+ifa_status ifa_set_max_subs(ifa_handle *h, uint32_t max_subs);
+
+/* Brute force, indexed, or automatic by query count (Discussion). */
+ifa_status ifa_set_mode(ifa_handle *h, ifa_mode mode);
+
+/* Stream one reference segment past the queries (Methods, "Algorithm
+ * Design": reference processed on demand, no preprocessing).  `ascii`
+ * holds len bytes in memory of kind `mem`; `pieces` (host memory) maps it
+ * onto contigs as described at ifa_piece.  Windows that straddle two
+ * segments of one contig are found through a halo of the previous
+ * segment's last bases.
+ * IFA_MEM_HOST / IFA_MEM_HOST_PINNED: returns once the bytes are on the
+ * device (the caller may then reuse its buffer); the scan continues
+ * asynchronously.  IFA_MEM_DEVICE: the buffer must stay unchanged until
+ * ifa_flush() returns.
+ * Errors: INVALID_ARG (len > segment_bytes, bad piece table, contig order),
+ * BAD_STATE (no queries), CUDA. */
+ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len,
+                            const ifa_piece *pieces, uint32_t n_pieces, ifa_mem mem);
+
+/* Wait until every pushed segment is scanned.  Returns HIT_OVERFLOW if the
+ * hit buffer filled since the last ifa_reset_results (hits already written
+ * stay valid; digest and counts stay exact). */
+ifa_status ifa_flush(ifa_handle *h);
+
+/* Copy up to cap buffered hits into out (host memory) and release them from
+ * the device buffer; *n_out gets the number copied, *more (may be NULL)
+ * whether buffered hits remain.  Order is unspecified (compare as sets).
+ * Implies ifa_flush().  Returns HIT_OVERFLOW (with the data) if hits were
+ * dropped. */
+ifa_status ifa_drain_hits(ifa_handle *h, ifa_hit *out, uint64_t cap, uint64_t *n_out, int *more);
+
+/* Digest of all hits since the last reset; per_query_counts (may be NULL)
+ * receives one count per loaded query.  Implies ifa_flush(). */
+ifa_status ifa_get_digest(ifa_handle *h, ifa_digest *d, uint64_t *per_query_counts);
+
+/* Forget hits, digest, counts, overflow, statistics and the stream
+ * position (the next segment may start any contig); keeps the queries,
+ * maxSubs and mode. */
+ifa_status ifa_reset_results(ifa_handle *h);
+
+/* Counters since the last reset. */
+ifa_status ifa_get_stats(ifa_handle *h, ifa_stats *s);
+
+/* Indexed-mode plan of each loaded query under the current maxSubs: its
+ * seed length k, min-hits threshold and whether it is scanned exhaustively
+ * (no listed k fits, or none qualifies and exhaustive_fallback is set, or
+ * the query holds an N).  Arrays hold one entry per query; any may be NULL.
+ * Computed on the device (MinHitsCalculator, Methods, indexed mode). */
+ifa_status ifa_get_query_plan(ifa_handle *h, uint32_t *k, uint32_t *minhits, uint8_t *exhaustive);
+
+/* MinHitsCalculator on the device for n bins (Methods, indexed mode): for
+ * bin i, the query length L[i], substitutions subs[i] and seed length
+ * k[i]; step, mask width, clip count, probability num/den, trials and seed
+ * are shared.  out[i] receives the threshold (the largest m such that
+ * at least num/den of the trials keep >= m error-free k-mers; the
+ * deterministic bound when num >= den).  Host arrays.  Stateless apart from
+ * the device choice. */
+ifa_status ifa_minhits(int32_t device, const uint32_t *L, const uint32_t *subs, const uint32_t *k,
+                       uint32_t n, uint32_t step, uint32_t mask_width, uint32_t max_clips,
+                       uint32_t num, uint32_t den, uint32_t trials, uint64_t seed, uint32_t *out);
+
+/* Human-readable description of the last failure on h (or of the last
+ * failed ifa_create/ifa_minhits when h is NULL).  Never NULL. */
+const char *ifa_last_error(const ifa_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IFA_H */

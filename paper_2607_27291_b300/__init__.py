@@ -1,0 +1,330 @@
+"""B300-native indel-free (Hamming) aligner: thin ctypes binding over libifa.so.
+
+The functions below carry the names of the C ABI in ``include/ifa.h`` and
+only marshal arguments; every step of the scan runs in the library's CUDA
+kernels.  Importing this package does not need a GPU; calling into the
+library does, and a missing library raises at once (there is no CPU
+fallback).  PyTorch is optional: it may supply device buffers and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libifa.so")
+
+IFA_OK = 0
+IFA_ERR_INVALID_ARG = 1
+IFA_ERR_OOM = 2
+IFA_ERR_CUDA = 3
+IFA_ERR_BAD_STATE = 4
+IFA_ERR_HIT_OVERFLOW = 5
+IFA_ERR_TIMEOUT = 6
+
+IFA_MODE_AUTO, IFA_MODE_BRUTE, IFA_MODE_INDEXED = 0, 1, 2
+IFA_MEM_HOST, IFA_MEM_HOST_PINNED, IFA_MEM_DEVICE = 0, 1, 2
+IFA_MAX_QUERY_LEN = 255
+
+HIT_DTYPE = np.dtype([("query", "<u4"), ("contig", "<u4"), ("pos", "<u4"),
+                      ("strand", "u1"), ("mismatches", "u1"), ("reserved", "<u2")])
+PIECE_DTYPE = np.dtype([("contig", "<u4"), ("last", "<u4"), ("offset_in_contig", "<u8"),
+                        ("start", "<u8"), ("len", "<u8")])
+
+
+class ifa_config(C.Structure):
+    _fields_ = [("device", C.c_int32), ("count_only", C.c_uint32), ("hit_capacity", C.c_uint64),
+                ("segment_bytes", C.c_uint64), ("k_list", C.c_uint32 * 8), ("n_k", C.c_uint32),
+                ("kmer_step", C.c_uint32), ("mask_width", C.c_uint32), ("minhits_num", C.c_uint32),
+                ("minhits_den", C.c_uint32), ("minhits_trials", C.c_uint32),
+                ("minhits_seed", C.c_uint64), ("max_clips", C.c_uint32),
+                ("exhaustive_fallback", C.c_uint32), ("auto_crossover", C.c_uint32),
+                ("profile", C.c_uint32), ("reserved", C.c_uint32 * 6)]
+
+
+class ifa_digest(C.Structure):
+    _fields_ = [("count", C.c_uint64), ("sum", C.c_uint64), ("xr", C.c_uint64)]
+
+
+class ifa_stats(C.Structure):
+    _fields_ = [("segments", C.c_uint64), ("bases", C.c_uint64), ("h2d_bytes", C.c_uint64),
+                ("windows", C.c_uint64), ("query_bases", C.c_uint64),
+                ("kernel_launches", C.c_uint64), ("candidates", C.c_uint64),
+                ("scan_launches", C.c_uint64), ("scan_ns", C.c_uint64)]
+
+
+class IfaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("ifa status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+_SYMBOLS = {
+    "ifa_config_default": (C.c_int, [C.POINTER(ifa_config)]),
+    "ifa_create": (C.c_int, [C.POINTER(ifa_config), C.POINTER(C.c_void_p)]),
+    "ifa_destroy": (None, [C.c_void_p]),
+    "ifa_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ifa_load_queries": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
+                                   C.c_uint32, C.POINTER(C.c_uint32)]),
+    "ifa_set_max_subs": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "ifa_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "ifa_push_segment": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32,
+                                   C.c_int]),
+    "ifa_flush": (C.c_int, [C.c_void_p]),
+    "ifa_drain_hits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64),
+                                 C.POINTER(C.c_int)]),
+    "ifa_get_digest": (C.c_int, [C.c_void_p, C.POINTER(ifa_digest), C.c_void_p]),
+    "ifa_reset_results": (C.c_int, [C.c_void_p]),
+    "ifa_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ifa_stats)]),
+    "ifa_get_query_plan": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ifa_minhits": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32,
+                              C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                              C.c_uint32, C.c_uint64, C.c_void_p]),
+    "ifa_last_error": (C.c_char_p, [C.c_void_p]),
+}
+
+
+def lib():
+    """The loaded libifa.so (raises if it was never built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libifa.so is not built; run `python -m paper_2607_27291_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SYMBOLS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> List[str]:
+    return list(_SYMBOLS)
+
+
+def _check(st: int, h=None, allow=(IFA_OK,)):
+    if st not in allow:
+        raise IfaError(st, lib().ifa_last_error(h).decode(errors="replace"))
+    return st
+
+
+# ------------------------------------------------------------ C ABI by name
+
+def ifa_config_default() -> ifa_config:
+    cfg = ifa_config()
+    _check(lib().ifa_config_default(C.byref(cfg)))
+    return cfg
+
+
+def ifa_create(cfg: Optional[ifa_config] = None, **overrides) -> C.c_void_p:
+    cfg = cfg or ifa_config_default()
+    for k, v in overrides.items():
+        if k == "k_list":
+            for i, x in enumerate(v):
+                cfg.k_list[i] = x
+            cfg.n_k = len(v)
+        else:
+            setattr(cfg, k, v)
+    h = C.c_void_p()
+    _check(lib().ifa_create(C.byref(cfg), C.byref(h)))
+    return h
+
+
+def ifa_destroy(h) -> None:
+    lib().ifa_destroy(h)
+
+
+def ifa_set_stream(h, stream) -> None:
+    """`stream`: a torch.cuda.Stream, a raw cudaStream_t as int, or None."""
+    ptr = getattr(stream, "cuda_stream", stream)
+    _check(lib().ifa_set_stream(h, C.c_void_p(ptr or None)), h)
+
+
+def ifa_load_queries(h, queries: Sequence[bytes]) -> int:
+    n = len(queries)
+    bufs = [C.create_string_buffer(bytes(q), len(q)) for q in queries]
+    ptrs = (C.c_void_p * max(1, n))(*[C.cast(b, C.c_void_p) for b in bufs])
+    lens = (C.c_uint32 * max(1, n))(*[len(q) for q in queries])
+    first = C.c_uint32()
+    _check(lib().ifa_load_queries(h, ptrs, lens, n, C.byref(first)), h)
+    return first.value
+
+
+def ifa_set_max_subs(h, s: int) -> None:
+    _check(lib().ifa_set_max_subs(h, int(s)), h)
+
+
+def ifa_set_mode(h, mode: int) -> None:
+    _check(lib().ifa_set_mode(h, int(mode)), h)
+
+
+def _as_pieces(pieces) -> np.ndarray:
+    if isinstance(pieces, np.ndarray) and pieces.dtype == PIECE_DTYPE:
+        return np.ascontiguousarray(pieces)
+    arr = np.zeros(len(pieces), PIECE_DTYPE)
+    for i, (contig, off, start, ln, last) in enumerate(pieces):
+        arr[i] = (contig, 1 if last else 0, off, start, ln)
+    return arr
+
+
+def ifa_push_segment(h, data, pieces, mem: Optional[int] = None) -> None:
+    """Push one segment.  `data`: a numpy uint8 array (pageable host), a torch
+    uint8 tensor (CUDA, or pinned CPU), or a (pointer, length, mem) tuple.
+    `pieces`: PIECE_DTYPE array or (contig, offset_in_contig, start, len,
+    last) tuples."""
+    pa = _as_pieces(pieces)
+    if isinstance(data, tuple):
+        ptr, ln, mem = data
+    elif isinstance(data, np.ndarray):
+        assert data.dtype == np.uint8 and data.flags.c_contiguous
+        ptr, ln = data.ctypes.data, data.size
+        mem = IFA_MEM_HOST if mem is None else mem
+    else:  # torch tensor
+        assert data.is_contiguous()
+        ptr, ln = data.data_ptr(), data.numel()
+        if mem is None:
+            mem = IFA_MEM_DEVICE if data.is_cuda else (
+                IFA_MEM_HOST_PINNED if data.is_pinned() else IFA_MEM_HOST)
+    _check(lib().ifa_push_segment(h, C.c_void_p(ptr), ln, pa.ctypes.data, pa.size, mem), h)
+
+
+def ifa_flush(h) -> int:
+    """Returns IFA_OK or IFA_ERR_HIT_OVERFLOW; raises on other errors."""
+    return _check(lib().ifa_flush(h), h, allow=(IFA_OK, IFA_ERR_HIT_OVERFLOW))
+
+
+def ifa_drain_hits(h, cap: Optional[int] = None) -> Tuple[np.ndarray, bool]:
+    """Drain buffered hits; returns (hits, overflowed)."""
+    parts = []
+    overflowed = False
+    chunk = cap or (1 << 22)
+    while True:
+        out = np.zeros(chunk, HIT_DTYPE)
+        n = C.c_uint64()
+        more = C.c_int()
+        st = _check(lib().ifa_drain_hits(h, out.ctypes.data, chunk, C.byref(n), C.byref(more)), h,
+                    allow=(IFA_OK, IFA_ERR_HIT_OVERFLOW))
+        overflowed |= st == IFA_ERR_HIT_OVERFLOW
+        parts.append(out[:n.value])
+        if cap is not None or not more.value:
+            break
+    return (np.concatenate(parts) if parts else np.zeros(0, HIT_DTYPE)), overflowed
+
+
+def ifa_get_digest(h, nq: Optional[int] = None):
+    d = ifa_digest()
+    counts = np.zeros(max(1, nq or 0), np.uint64)
+    _check(lib().ifa_get_digest(h, C.byref(d), counts.ctypes.data if nq else None), h)
+    return (int(d.count), int(d.sum), int(d.xr)), (counts[:nq] if nq else None)
+
+
+def ifa_reset_results(h) -> None:
+    _check(lib().ifa_reset_results(h), h)
+
+
+def ifa_get_stats(h) -> dict:
+    s = ifa_stats()
+    _check(lib().ifa_get_stats(h, C.byref(s)), h)
+    return {f: int(getattr(s, f)) for f, _ in ifa_stats._fields_}
+
+
+def ifa_get_query_plan(h, nq: int):
+    k = np.zeros(nq, np.uint32)
+    m = np.zeros(nq, np.uint32)
+    ex = np.zeros(nq, np.uint8)
+    _check(lib().ifa_get_query_plan(h, k.ctypes.data, m.ctypes.data, ex.ctypes.data), h)
+    return k, m, ex
+
+
+def ifa_minhits(device: int, L, subs, k, step: int = 1, mask_width: int = 0, max_clips: int = 0,
+                num: int = 999, den: int = 1000, trials: int = 200_000, seed: int = 1) -> np.ndarray:
+    L = np.ascontiguousarray(L, np.uint32)
+    subs = np.ascontiguousarray(subs, np.uint32)
+    k = np.ascontiguousarray(k, np.uint32)
+    out = np.zeros(L.size, np.uint32)
+    _check(lib().ifa_minhits(device, L.ctypes.data, subs.ctypes.data, k.ctypes.data, L.size, step,
+                             mask_width, max_clips, num, den, trials, seed, out.ctypes.data))
+    return out
+
+
+def ifa_last_error(h=None) -> str:
+    return lib().ifa_last_error(h).decode(errors="replace")
+
+
+# ------------------------------------------------------------ convenience
+
+def sort_hits(h: np.ndarray) -> np.ndarray:
+    if h.size == 0:
+        return h
+    order = np.lexsort((h["mismatches"], h["strand"], h["pos"], h["contig"], h["query"]))
+    return h[order]
+
+
+def segment_pieces(contig_len: np.ndarray, seg_bytes: int, contig_ids=None):
+    """Cut a concatenated reference into (begin, end, PIECE_DTYPE array)."""
+    starts = np.concatenate([[0], np.cumsum(np.asarray(contig_len, np.int64))]).astype(np.int64)
+    total = int(starts[-1])
+    ids = np.arange(len(contig_len), dtype=np.int64) if contig_ids is None else np.asarray(contig_ids)
+    pos = 0
+    while pos < total:
+        end = min(total, pos + seg_bytes)
+        a = int(np.searchsorted(starts, pos, side="right")) - 1
+        b = int(np.searchsorted(starts, end, side="left"))
+        cs = starts[a:b]
+        ce = starts[a + 1:b + 1]
+        ps = np.maximum(cs, pos)
+        pe = np.minimum(ce, end)
+        arr = np.zeros(b - a, PIECE_DTYPE)
+        arr["contig"] = ids[a:b]
+        arr["offset_in_contig"] = ps - cs
+        arr["start"] = ps - pos
+        arr["len"] = pe - ps
+        arr["last"] = (pe == ce).astype(np.uint32)
+        keep = arr["len"] > 0
+        yield pos, end, arr[keep]
+        pos = end
+
+
+class Aligner:
+    """One handle: load queries once, stream the reference, drain hits."""
+
+    def __init__(self, queries: Sequence[bytes] = (), max_subs: int = 0,
+                 mode: int = IFA_MODE_BRUTE, **cfg):
+        self.h = ifa_create(**cfg)
+        self.nq = 0
+        if queries:
+            self.load_queries(queries)
+        ifa_set_max_subs(self.h, max_subs)
+        ifa_set_mode(self.h, mode)
+
+    def close(self):
+        if self.h:
+            ifa_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def load_queries(self, queries):
+        ifa_load_queries(self.h, queries)
+        self.nq += len(queries)
+
+    def scan(self, ref, contig_len, seg_bytes: Optional[int] = None, contig_ids=None,
+             drain: bool = True):
+        """Push a concatenated reference (numpy or torch) through in segments."""
+        seg = seg_bytes or 256 << 20
+        for a, b, pieces in segment_pieces(contig_len, seg, contig_ids):
+            ifa_push_segment(self.h, ref[a:b], pieces)
+        if drain:
+            return ifa_drain_hits(self.h)
+        return ifa_flush(self.h)

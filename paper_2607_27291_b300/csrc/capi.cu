@@ -1,0 +1,703 @@
+// capi.cu -- the handle-based C ABI (include/ifa.h) and its streaming engine.
+//
+// One handle = one device, one query set, one streamed reference pass at a
+// time.  Segments are double-buffered: while the compute stream packs and
+// scans segment k, the copy stream moves segment k+1 from host to device;
+// a slot is reused only after the compute that read it has finished
+// (event per slot).  Memory on the device is bounded by the segment size,
+// not by the reference size (Methods, "Memory Management").
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ifa_internal.cuh"
+#include "indexed.cuh"
+
+using namespace ifa;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+constexpr uint32_t kHaloCap = 256;   // > IFA_MAX_QUERY_LEN - 1
+constexpr uint64_t kWordPad = 16;    // zeroed words after the last packed word
+
+struct Chunk {
+    uint32_t e0, e1, lmin, lmax;
+};
+
+}  // namespace
+
+struct ifa_handle {
+    ifa_config cfg{};
+    int dev = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    std::string err = "no error";
+
+    // queries
+    std::vector<std::string> qs;
+    uint32_t lmin = 0, lmax = 0, wmax = 1;
+    bool qdirty = true;
+    uint4 *d_qwords = nullptr;
+    uint32_t *d_qmeta = nullptr;
+    std::vector<Chunk> chunks;
+    std::vector<uint32_t> qmeta_host;
+    std::vector<uint4> qwords_host;
+
+    // segment slots
+    uint8_t *d_seg[2] = {nullptr, nullptr};
+    uint8_t *h_stage[2] = {nullptr, nullptr};
+    DevPiece *d_pieces[2] = {nullptr, nullptr};
+    DevPiece *h_pieces[2] = {nullptr, nullptr};
+    uint32_t pieces_cap[2] = {0, 0};
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+    bool slot_used[2] = {false, false};
+    int slot = 0;
+
+    uint8_t *d_halo[2] = {nullptr, nullptr};
+    int halo_cur = 0;
+    uint32_t halo_len = 0;
+
+    uint4 *d_words = nullptr;
+    uint64_t words_cap = 0;
+
+    // results
+    ifa_hit *d_ring = nullptr;
+    unsigned long long *d_head = nullptr;
+    uint32_t *d_overflow = nullptr;
+    unsigned long long *d_digest = nullptr;
+    unsigned long long *d_qcount = nullptr;
+    uint64_t drained = 0;
+
+    // stream position
+    bool open = false;
+    uint32_t open_contig = 0;
+    uint64_t open_next = 0;
+    bool any_contig = false;
+    uint32_t last_contig = 0;
+    bool pushed = false;
+
+    uint32_t max_subs = 0;
+    ifa_mode mode = IFA_MODE_BRUTE;
+    ifa_stats stats{};
+
+    // optional per-launch timing of the scan kernels (config.profile)
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
+
+    IndexedState idx;
+};
+
+namespace {
+
+ifa_status fail(ifa_handle *h, ifa_status st, const std::string &msg) {
+    if (h) h->err = msg; else g_err = msg;
+    return st;
+}
+
+ifa_status fail_cuda(ifa_handle *h, const char *what, cudaError_t e) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? IFA_ERR_OOM : IFA_ERR_CUDA, m);
+}
+
+#define CK(h, call)                                           \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return fail_cuda((h), #call, e_); \
+    } while (0)
+
+void encode_entry(const std::string &q, bool rc, uint32_t wmax, uint4 *out, uint32_t *meta) {
+    const uint32_t L = static_cast<uint32_t>(q.size());
+    for (uint32_t j = 0; j < wmax; j++) out[j] = make_uint4(0, 0, 0, 0);
+    uint32_t nN = 0;
+    for (uint32_t i = 0; i < L; i++) {
+        const uint32_t c = static_cast<uint8_t>(rc ? q[L - 1 - i] : q[i]);
+        const uint32_t w = i >> 5, bit = 1u << (i & 31);
+        if (is_base(c)) {
+            uint32_t code = base_code(c);
+            if (rc) code ^= 2u;  // complement: A<->T, C<->G
+            if (code >> 1) out[w].x |= bit;
+            if (code & 1u) out[w].y |= bit;
+            out[w].z |= bit;
+        } else {
+            nN++;
+        }
+        out[w].w |= bit;
+    }
+    *meta = L | (((L + 31) / 32) << 8) | (nN << 16);
+}
+
+ifa_status upload_queries(ifa_handle *h) {
+    if (!h->qdirty) return IFA_OK;
+    const uint32_t nq = static_cast<uint32_t>(h->qs.size());
+    uint32_t wneed = (h->lmax + 31) / 32;
+    uint32_t w = 1;
+    while (w < wneed) w <<= 1;
+    h->wmax = w;
+    const uint32_t ne = 2 * nq;
+    std::vector<uint4> &words = h->qwords_host;
+    words.assign(static_cast<size_t>(ne) * w, make_uint4(0, 0, 0, 0));
+    h->qmeta_host.assign(ne, 0);
+    for (uint32_t q = 0; q < nq; q++)
+        for (uint32_t t = 0; t < 2; t++)
+            encode_entry(h->qs[q], t == 1, w, &words[static_cast<size_t>(2 * q + t) * w],
+                         &h->qmeta_host[2 * q + t]);
+    cudaFree(h->d_qwords);
+    cudaFree(h->d_qmeta);
+    h->d_qwords = nullptr;
+    h->d_qmeta = nullptr;
+    CK(h, cudaMalloc(&h->d_qwords, words.size() * sizeof(uint4)));
+    CK(h, cudaMalloc(&h->d_qmeta, ne * sizeof(uint32_t)));
+    CK(h, cudaMemcpy(h->d_qwords, words.data(), words.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->d_qmeta, h->qmeta_host.data(), ne * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    // entry chunks that fit the scan kernel's shared-memory budget
+    uint32_t cap = scan_brute_chunk_entries(w) & ~1u;
+    if (cap < 2) cap = 2;
+    h->chunks.clear();
+    for (uint32_t e0 = 0; e0 < ne; e0 += cap) {
+        Chunk c{e0, std::min(ne, e0 + cap), 0xffffffffu, 0};
+        for (uint32_t e = c.e0; e < c.e1; e++) {
+            uint32_t L = h->qmeta_host[e] & 0xffu;
+            c.lmin = std::min(c.lmin, L);
+            c.lmax = std::max(c.lmax, L);
+        }
+        h->chunks.push_back(c);
+    }
+    h->qdirty = false;
+    h->idx.invalidate();
+    return IFA_OK;
+}
+
+ifa_status ensure_pieces(ifa_handle *h, int slot, uint32_t n) {
+    if (n <= h->pieces_cap[slot]) return IFA_OK;
+    uint32_t cap = std::max<uint32_t>(n, 2 * h->pieces_cap[slot]);
+    cudaFree(h->d_pieces[slot]);
+    cudaFreeHost(h->h_pieces[slot]);
+    h->d_pieces[slot] = nullptr;
+    h->h_pieces[slot] = nullptr;
+    h->pieces_cap[slot] = 0;
+    CK(h, cudaMalloc(&h->d_pieces[slot], static_cast<size_t>(cap) * sizeof(DevPiece)));
+    CK(h, cudaHostAlloc(&h->h_pieces[slot], static_cast<size_t>(cap) * sizeof(DevPiece), cudaHostAllocDefault));
+    h->pieces_cap[slot] = cap;
+    return IFA_OK;
+}
+
+ifa_mode resolve_mode(const ifa_handle *h) {
+    if (h->mode != IFA_MODE_AUTO) return h->mode;
+    return h->qs.size() >= h->cfg.auto_crossover ? IFA_MODE_INDEXED : IFA_MODE_BRUTE;
+}
+
+HitSink make_sink(const ifa_handle *h) {
+    HitSink s;
+    s.ring = h->d_ring;
+    s.head = h->d_head;
+    s.capacity = h->cfg.count_only ? 0 : h->cfg.hit_capacity;
+    s.digest = h->d_digest;
+    s.qcount = h->d_qcount;
+    s.overflow = h->d_overflow;
+    s.count_only = h->cfg.count_only ? 1 : 0;
+    return s;
+}
+
+ifa_status sync_all(ifa_handle *h) {
+    CK(h, cudaStreamSynchronize(h->copy_stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return IFA_OK;
+}
+
+// Start/stop a timed region around scan kernels on the compute stream.
+ifa_status prof_begin(ifa_handle *h, cudaEvent_t *stop_out) {
+    *stop_out = nullptr;
+    if (!h->cfg.profile) return IFA_OK;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (!h->ev_free.empty()) {
+        ev = h->ev_free.back();
+        h->ev_free.pop_back();
+    } else {
+        CK(h, cudaEventCreate(&ev.first));
+        CK(h, cudaEventCreate(&ev.second));
+    }
+    CK(h, cudaEventRecord(ev.first, h->stream));
+    h->ev_pending.push_back(ev);
+    *stop_out = ev.second;
+    return IFA_OK;
+}
+
+ifa_status prof_end(ifa_handle *h, cudaEvent_t stop, int launches) {
+    if (!stop) return IFA_OK;
+    CK(h, cudaEventRecord(stop, h->stream));
+    h->stats.scan_launches += launches;
+    return IFA_OK;
+}
+
+// Fold finished timed regions into the statistics (after a stream sync).
+ifa_status prof_collect(ifa_handle *h) {
+    for (auto &ev : h->ev_pending) {
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, ev.first, ev.second));
+        h->stats.scan_ns += static_cast<uint64_t>(ms * 1e6);
+        h->ev_free.push_back(ev);
+    }
+    h->ev_pending.clear();
+    return IFA_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------ API
+
+extern "C" {
+
+ifa_status ifa_config_default(ifa_config *cfg) {
+    if (!cfg) return fail(nullptr, IFA_ERR_INVALID_ARG, "cfg is NULL");
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->device = 0;
+    cfg->count_only = 0;
+    cfg->hit_capacity = 1ull << 26;
+    cfg->segment_bytes = 256ull << 20;
+    const uint32_t ks[5] = {8, 9, 10, 12, 14};  // paper default k list
+    for (int i = 0; i < 5; i++) cfg->k_list[i] = ks[i];
+    cfg->n_k = 5;
+    cfg->kmer_step = 1;
+    cfg->mask_width = 0;
+    cfg->minhits_num = 999;   // 99.9%, paper default
+    cfg->minhits_den = 1000;
+    cfg->minhits_trials = 200000;  // paper default iterations
+    cfg->minhits_seed = 1;
+    cfg->max_clips = 0;
+    cfg->exhaustive_fallback = 0;
+    cfg->auto_crossover = 150;  // paper: crossover between 100 and 200 queries (RefSeq)
+    return IFA_OK;
+}
+
+ifa_status ifa_create(const ifa_config *cfg, ifa_handle **out) {
+    if (!out) return fail(nullptr, IFA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, IFA_ERR_INVALID_ARG, "cfg is NULL");
+    if (cfg->max_clips != 0)
+        return fail(nullptr, IFA_ERR_INVALID_ARG, "max_clips must be 0 (soft clipping not implemented)");
+    if (cfg->n_k == 0 || cfg->n_k > IFA_MAX_KLIST)
+        return fail(nullptr, IFA_ERR_INVALID_ARG, "n_k must be in 1..8");
+    for (uint32_t i = 0; i < cfg->n_k; i++)
+        if (cfg->k_list[i] == 0 || cfg->k_list[i] > 16 || cfg->k_list[i] <= cfg->mask_width)
+            return fail(nullptr, IFA_ERR_INVALID_ARG, "k_list entries must be in (mask_width, 16]");
+    if (cfg->kmer_step == 0 || cfg->minhits_den == 0)
+        return fail(nullptr, IFA_ERR_INVALID_ARG, "kmer_step and minhits_den must be > 0");
+    if (cfg->segment_bytes == 0 || cfg->segment_bytes > (1ull << 36))
+        return fail(nullptr, IFA_ERR_INVALID_ARG, "segment_bytes out of range");
+    if (!cfg->count_only && cfg->hit_capacity == 0)
+        return fail(nullptr, IFA_ERR_INVALID_ARG, "hit_capacity must be > 0 unless count_only");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail_cuda(nullptr, "cudaGetDeviceCount", e);
+    if (cfg->device < 0 || cfg->device >= ndev)
+        return fail(nullptr, IFA_ERR_CUDA, "no such CUDA device");
+    ifa_handle *h = new ifa_handle();
+    h->cfg = *cfg;
+    h->dev = cfg->device;
+    auto bail = [&](ifa_status st) {
+        g_err = h->err;
+        ifa_destroy(h);
+        return st;
+    };
+#define CKC(call)                                                     \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return bail(fail_cuda(h, #call, e_));  \
+    } while (0)
+    CKC(cudaSetDevice(h->dev));
+    CKC(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    h->stream = h->own_stream;
+    const uint64_t sb = cfg->segment_bytes;
+    h->words_cap = (sb + kHaloCap + 31) / 32 + kWordPad;
+    CKC(cudaMalloc(&h->d_words, h->words_cap * sizeof(uint4)));
+    for (int i = 0; i < 2; i++) {
+        CKC(cudaMalloc(&h->d_seg[i], sb));
+        CKC(cudaMalloc(&h->d_halo[i], kHaloCap));
+        CKC(cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming));
+        CKC(cudaEventCreateWithFlags(&h->ev_consumed[i], cudaEventDisableTiming));
+    }
+    if (!cfg->count_only) CKC(cudaMalloc(&h->d_ring, cfg->hit_capacity * sizeof(ifa_hit)));
+    CKC(cudaMalloc(&h->d_head, sizeof(unsigned long long)));
+    CKC(cudaMalloc(&h->d_overflow, sizeof(uint32_t)));
+    CKC(cudaMalloc(&h->d_digest, 3 * sizeof(unsigned long long)));
+    CKC(cudaMemset(h->d_head, 0, sizeof(unsigned long long)));
+    CKC(cudaMemset(h->d_overflow, 0, sizeof(uint32_t)));
+    CKC(cudaMemset(h->d_digest, 0, 3 * sizeof(unsigned long long)));
+#undef CKC
+    ifa_status st = ensure_pieces(h, 0, 1024);
+    if (st == IFA_OK) st = ensure_pieces(h, 1, 1024);
+    if (st != IFA_OK) return bail(st);
+    *out = h;
+    return IFA_OK;
+}
+
+void ifa_destroy(ifa_handle *h) {
+    if (!h) return;
+    cudaSetDevice(h->dev);
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->idx.release();
+    for (int i = 0; i < 2; i++) {
+        cudaFree(h->d_seg[i]);
+        cudaFreeHost(h->h_stage[i]);
+        cudaFree(h->d_pieces[i]);
+        cudaFreeHost(h->h_pieces[i]);
+        cudaFree(h->d_halo[i]);
+        if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
+        if (h->ev_consumed[i]) cudaEventDestroy(h->ev_consumed[i]);
+    }
+    for (auto *v : {&h->ev_pending, &h->ev_free})
+        for (auto &ev : *v) {
+            cudaEventDestroy(ev.first);
+            cudaEventDestroy(ev.second);
+        }
+    cudaFree(h->d_words);
+    cudaFree(h->d_qwords);
+    cudaFree(h->d_qmeta);
+    cudaFree(h->d_ring);
+    cudaFree(h->d_head);
+    cudaFree(h->d_overflow);
+    cudaFree(h->d_digest);
+    cudaFree(h->d_qcount);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+ifa_status ifa_set_stream(ifa_handle *h, void *stream) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    CK(h, cudaSetDevice(h->dev));
+    ifa_status st = sync_all(h);
+    if (st != IFA_OK) return st;
+    h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
+    return IFA_OK;
+}
+
+ifa_status ifa_load_queries(ifa_handle *h, const uint8_t *const *seqs, const uint32_t *lens, uint32_t n,
+                            uint32_t *first_id) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    if (h->pushed) return fail(h, IFA_ERR_BAD_STATE, "queries must be loaded before the first segment");
+    if (n && (!seqs || !lens)) return fail(h, IFA_ERR_INVALID_ARG, "seqs/lens is NULL");
+    for (uint32_t i = 0; i < n; i++) {
+        if (lens[i] == 0 || lens[i] > IFA_MAX_QUERY_LEN)
+            return fail(h, IFA_ERR_INVALID_ARG, "query length must be in 1..255");
+        if (!seqs[i]) return fail(h, IFA_ERR_INVALID_ARG, "query pointer is NULL");
+    }
+    if (h->qs.size() + n > (1u << 24))
+        return fail(h, IFA_ERR_INVALID_ARG, "at most 2^24 queries");
+    if (first_id) *first_id = static_cast<uint32_t>(h->qs.size());
+    CK(h, cudaSetDevice(h->dev));
+    for (uint32_t i = 0; i < n; i++) {
+        h->qs.emplace_back(reinterpret_cast<const char *>(seqs[i]), lens[i]);
+        h->lmin = h->qs.size() == 1 ? lens[i] : std::min(h->lmin, lens[i]);
+        h->lmax = std::max(h->lmax, lens[i]);
+    }
+    h->qdirty = true;
+    cudaFree(h->d_qcount);
+    h->d_qcount = nullptr;
+    CK(h, cudaMalloc(&h->d_qcount, std::max<size_t>(1, h->qs.size()) * sizeof(unsigned long long)));
+    CK(h, cudaMemset(h->d_qcount, 0, std::max<size_t>(1, h->qs.size()) * sizeof(unsigned long long)));
+    return IFA_OK;
+}
+
+ifa_status ifa_set_max_subs(ifa_handle *h, uint32_t s) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    h->max_subs = s;
+    return IFA_OK;
+}
+
+ifa_status ifa_set_mode(ifa_handle *h, ifa_mode m) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    if (m != IFA_MODE_AUTO && m != IFA_MODE_BRUTE && m != IFA_MODE_INDEXED)
+        return fail(h, IFA_ERR_INVALID_ARG, "unknown mode");
+    h->mode = m;
+    return IFA_OK;
+}
+
+ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, const ifa_piece *pieces,
+                            uint32_t n, ifa_mem mem) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    if (len == 0 && n == 0) return IFA_OK;
+    if (len == 0 || n == 0 || !ascii || !pieces)
+        return fail(h, IFA_ERR_INVALID_ARG, "a segment needs bytes and at least one piece");
+    if (len > h->cfg.segment_bytes) return fail(h, IFA_ERR_INVALID_ARG, "segment longer than segment_bytes");
+    if (mem != IFA_MEM_HOST && mem != IFA_MEM_HOST_PINNED && mem != IFA_MEM_DEVICE)
+        return fail(h, IFA_ERR_INVALID_ARG, "unknown memory kind");
+    if (h->qs.empty()) return fail(h, IFA_ERR_BAD_STATE, "no queries loaded");
+    // piece table checks
+    uint64_t at = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        const ifa_piece &p = pieces[i];
+        if (p.start != at || p.len == 0) return fail(h, IFA_ERR_INVALID_ARG, "pieces must be contiguous, non-empty and start at 0");
+        at += p.len;
+        if (!p.last && i + 1 != n) return fail(h, IFA_ERR_INVALID_ARG, "only a segment's last piece may continue");
+        if (i == 0 && h->open) {
+            if (p.contig != h->open_contig || p.offset_in_contig != h->open_next)
+                return fail(h, IFA_ERR_INVALID_ARG, "segment must continue the open contig");
+        } else {
+            if (p.offset_in_contig != 0) return fail(h, IFA_ERR_INVALID_ARG, "a new contig must start at offset 0");
+            const bool have_prev = i > 0 || h->any_contig;
+            const uint32_t prev = i > 0 ? pieces[i - 1].contig : h->last_contig;
+            if (have_prev && p.contig <= prev) return fail(h, IFA_ERR_INVALID_ARG, "contig ids must increase");
+        }
+        if (p.offset_in_contig + p.len > 0xffffffffull)
+            return fail(h, IFA_ERR_INVALID_ARG, "contig longer than 2^32 - 1 bases");
+    }
+    if (at != len) return fail(h, IFA_ERR_INVALID_ARG, "pieces must cover the segment exactly");
+
+    CK(h, cudaSetDevice(h->dev));
+    ifa_status st = upload_queries(h);
+    if (st != IFA_OK) return st;
+    const ifa_mode mode = resolve_mode(h);
+    if (mode == IFA_MODE_INDEXED) {
+        st = indexed_prepare(h->idx, h->qs, h->qmeta_host, h->qwords_host, h->wmax, h->cfg, h->max_subs,
+                             h->stream, h->err);
+        if (st != IFA_OK) return st;
+    }
+
+    const int slot = h->slot;
+    h->slot ^= 1;
+    if (h->slot_used[slot]) CK(h, cudaEventSynchronize(h->ev_consumed[slot]));
+    st = ensure_pieces(h, slot, n);
+    if (st != IFA_OK) return st;
+
+    const uint32_t hlen = h->open ? h->halo_len : 0u;
+    DevPiece *hp = h->h_pieces[slot];
+    for (uint32_t i = 0; i < n; i++) {
+        hp[i].start = i == 0 ? 0 : hlen + pieces[i].start;
+        hp[i].contig_off = pieces[i].offset_in_contig - (i == 0 ? hlen : 0);
+        hp[i].contig = pieces[i].contig;
+        hp[i].pad = 0;
+    }
+    CK(h, cudaMemcpyAsync(h->d_pieces[slot], hp, n * sizeof(DevPiece), cudaMemcpyHostToDevice, h->copy_stream));
+    const uint8_t *dsrc = ascii;
+    if (mem == IFA_MEM_HOST) {
+        if (!h->h_stage[slot]) CK(h, cudaHostAlloc(&h->h_stage[slot], h->cfg.segment_bytes, cudaHostAllocDefault));
+        std::memcpy(h->h_stage[slot], ascii, len);
+        CK(h, cudaMemcpyAsync(h->d_seg[slot], h->h_stage[slot], len, cudaMemcpyHostToDevice, h->copy_stream));
+        dsrc = h->d_seg[slot];
+        h->stats.h2d_bytes += len;
+    } else if (mem == IFA_MEM_HOST_PINNED) {
+        CK(h, cudaMemcpyAsync(h->d_seg[slot], ascii, len, cudaMemcpyHostToDevice, h->copy_stream));
+        dsrc = h->d_seg[slot];
+        h->stats.h2d_bytes += len;
+    }
+    CK(h, cudaEventRecord(h->ev_copied[slot], h->copy_stream));
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_copied[slot], 0));
+
+    const uint64_t nbases = hlen + len;
+    const uint64_t nwords = (nbases + 31) / 32 + kWordPad;
+    int launches = 0;
+    CK(h, launch_pack(h->d_halo[h->halo_cur], hlen, dsrc, len, h->d_words, nwords, h->stream));
+    launches++;
+    if (n > 1) {
+        CK(h, launch_mark_pieces(h->d_pieces[slot], n, h->d_words, h->stream));
+        launches++;
+    }
+    Batch b;
+    b.words = h->d_words;
+    b.nbases = nbases;
+    b.halo = hlen;
+    b.pieces = h->d_pieces[slot];
+    b.npieces = n;
+    QueryTable qt;
+    qt.words = h->d_qwords;
+    qt.meta = h->d_qmeta;
+    qt.ids = nullptr;
+    qt.n_entries = 2 * static_cast<uint32_t>(h->qs.size());
+    qt.wmax = h->wmax;
+    const HitSink sink = make_sink(h);
+    cudaEvent_t prof_stop = nullptr;
+    st = prof_begin(h, &prof_stop);
+    if (st != IFA_OK) return st;
+    const int before_scan = launches;
+    if (mode == IFA_MODE_INDEXED) {
+        st = indexed_scan(h->idx, b, qt, h->max_subs, sink, h->stream, &launches, h->err);
+        if (st != IFA_OK) return st;
+    }
+    if (mode == IFA_MODE_BRUTE)
+        for (const Chunk &c : h->chunks)
+            CK(h, launch_scan_brute(b, qt, c.e0, c.e1, h->max_subs, c.lmin, c.lmax, sink, h->stream, &launches));
+    st = prof_end(h, prof_stop, launches - before_scan);
+    if (st != IFA_OK) return st;
+    // halo for the next segment when the last piece continues
+    const ifa_piece &lp = pieces[n - 1];
+    if (!lp.last) {
+        const uint64_t avail = lp.len + (n == 1 ? hlen : 0);
+        const uint32_t new_len = static_cast<uint32_t>(std::min<uint64_t>(avail, h->lmax > 0 ? h->lmax - 1 : 0));
+        CK(h, launch_halo_update(h->d_halo[h->halo_cur], hlen, dsrc, len, new_len, h->d_halo[h->halo_cur ^ 1], h->stream));
+        if (new_len) launches++;
+        h->halo_cur ^= 1;
+        h->halo_len = new_len;
+        h->open = true;
+        h->open_contig = lp.contig;
+        h->open_next = lp.offset_in_contig + lp.len;
+    } else {
+        h->open = false;
+        h->halo_len = 0;
+    }
+    h->any_contig = true;
+    h->last_contig = lp.contig;
+    h->pushed = true;
+    CK(h, cudaEventRecord(h->ev_consumed[slot], h->stream));
+    h->slot_used[slot] = true;
+    if (mem == IFA_MEM_HOST_PINNED) CK(h, cudaEventSynchronize(h->ev_copied[slot]));
+
+    // nominal work counters: windows owned by this batch
+    h->stats.segments++;
+    h->stats.bases += len;
+    h->stats.kernel_launches += launches;
+    for (uint32_t i = 0; i < n; i++) {
+        const uint64_t plen = pieces[i].len + (i == 0 ? hlen : 0);
+        const uint64_t first_new = (i == 0 ? hlen : 0);
+        for (uint32_t q = 0; q < h->qs.size(); q++) {
+            const uint64_t L = h->qs[q].size();
+            if (plen < L) continue;
+            // windows whose last base is new: ends in [max(L-1, first_new), plen)
+            const uint64_t lo = std::max<uint64_t>(L - 1, first_new);
+            if (plen > lo) {
+                h->stats.windows += 2 * (plen - lo);
+                h->stats.query_bases += 2 * (plen - lo) * L;
+            }
+        }
+    }
+    return IFA_OK;
+}
+
+ifa_status ifa_flush(ifa_handle *h) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    CK(h, cudaSetDevice(h->dev));
+    ifa_status st = sync_all(h);
+    if (st != IFA_OK) return st;
+    st = prof_collect(h);
+    if (st != IFA_OK) return st;
+    uint32_t ov = 0;
+    CK(h, cudaMemcpy(&ov, h->d_overflow, sizeof(ov), cudaMemcpyDeviceToHost));
+    if (ov) return fail(h, IFA_ERR_HIT_OVERFLOW, "hit buffer overflowed; some hit tuples were dropped");
+    return IFA_OK;
+}
+
+ifa_status ifa_drain_hits(ifa_handle *h, ifa_hit *out, uint64_t cap, uint64_t *n_out, int *more) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    if (!n_out || (cap && !out)) return fail(h, IFA_ERR_INVALID_ARG, "out/n_out is NULL");
+    *n_out = 0;
+    if (more) *more = 0;
+    ifa_status st = ifa_flush(h);
+    if (st != IFA_OK && st != IFA_ERR_HIT_OVERFLOW) return st;
+    const ifa_status ret = st;
+    if (h->cfg.count_only) return ret;
+    unsigned long long head = 0;
+    CK(h, cudaMemcpy(&head, h->d_head, sizeof(head), cudaMemcpyDeviceToHost));
+    const uint64_t total = std::min<uint64_t>(head, h->cfg.hit_capacity);
+    const uint64_t avail = total - h->drained;
+    const uint64_t take = std::min<uint64_t>(avail, cap);
+    if (take) {
+        CK(h, cudaMemcpy(out, h->d_ring + h->drained, take * sizeof(ifa_hit), cudaMemcpyDeviceToHost));
+        h->drained += take;
+    }
+    *n_out = take;
+    const bool left = h->drained < total;
+    if (more) *more = left ? 1 : 0;
+    if (!left && total > 0) {
+        CK(h, cudaMemsetAsync(h->d_head, 0, sizeof(unsigned long long), h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->drained = 0;
+    }
+    return ret;
+}
+
+ifa_status ifa_get_digest(ifa_handle *h, ifa_digest *d, uint64_t *per_query_counts) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    ifa_status st = ifa_flush(h);
+    if (st != IFA_OK && st != IFA_ERR_HIT_OVERFLOW) return st;
+    if (d) {
+        unsigned long long v[3];
+        CK(h, cudaMemcpy(v, h->d_digest, sizeof(v), cudaMemcpyDeviceToHost));
+        d->count = v[0];
+        d->sum = v[1];
+        d->xr = v[2];
+    }
+    if (per_query_counts && !h->qs.empty())
+        CK(h, cudaMemcpy(per_query_counts, h->d_qcount, h->qs.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    return IFA_OK;
+}
+
+ifa_status ifa_reset_results(ifa_handle *h) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    CK(h, cudaSetDevice(h->dev));
+    ifa_status st = sync_all(h);
+    if (st != IFA_OK) return st;
+    CK(h, cudaMemset(h->d_head, 0, sizeof(unsigned long long)));
+    CK(h, cudaMemset(h->d_overflow, 0, sizeof(uint32_t)));
+    CK(h, cudaMemset(h->d_digest, 0, 3 * sizeof(unsigned long long)));
+    if (h->d_qcount) CK(h, cudaMemset(h->d_qcount, 0, std::max<size_t>(1, h->qs.size()) * sizeof(unsigned long long)));
+    h->drained = 0;
+    h->open = false;
+    h->halo_len = 0;
+    h->any_contig = false;
+    h->pushed = false;
+    st = prof_collect(h);
+    if (st != IFA_OK) return st;
+    h->stats = ifa_stats{};
+    if (h->idx.d_candidates) CK(h, cudaMemset(h->idx.d_candidates, 0, sizeof(unsigned long long)));
+    return IFA_OK;
+}
+
+ifa_status ifa_get_stats(ifa_handle *h, ifa_stats *s) {
+    if (!h || !s) return fail(h, IFA_ERR_INVALID_ARG, "NULL argument");
+    CK(h, cudaSetDevice(h->dev));
+    ifa_status st = sync_all(h);
+    if (st != IFA_OK) return st;
+    st = prof_collect(h);
+    if (st != IFA_OK) return st;
+    *s = h->stats;
+    s->candidates = h->idx.candidates_host(h->stream);
+    return IFA_OK;
+}
+
+ifa_status ifa_get_query_plan(ifa_handle *h, uint32_t *k, uint32_t *minhits, uint8_t *exhaustive) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    if (h->qs.empty()) return fail(h, IFA_ERR_BAD_STATE, "no queries loaded");
+    CK(h, cudaSetDevice(h->dev));
+    ifa_status st = upload_queries(h);
+    if (st != IFA_OK) return st;
+    st = indexed_plan(h->idx, h->qs, h->cfg, h->max_subs, h->stream, h->err);
+    if (st != IFA_OK) return st;
+    for (size_t q = 0; q < h->qs.size(); q++) {
+        if (k) k[q] = h->idx.plan_k[q];
+        if (minhits) minhits[q] = h->idx.plan_minhits[q];
+        if (exhaustive) exhaustive[q] = h->idx.plan_exhaustive[q];
+    }
+    return IFA_OK;
+}
+
+ifa_status ifa_minhits(int32_t device, const uint32_t *L, const uint32_t *subs, const uint32_t *k, uint32_t n,
+                       uint32_t step, uint32_t mask_width, uint32_t max_clips, uint32_t num, uint32_t den,
+                       uint32_t trials, uint64_t seed, uint32_t *out) {
+    if (n == 0) return IFA_OK;
+    if (!L || !subs || !k || !out) return fail(nullptr, IFA_ERR_INVALID_ARG, "NULL array");
+    if (step == 0 || den == 0) return fail(nullptr, IFA_ERR_INVALID_ARG, "step and den must be > 0");
+    uint32_t maxK = 1;
+    for (uint32_t i = 0; i < n; i++) {
+        if (L[i] == 0 || L[i] > IFA_MAX_QUERY_LEN || k[i] == 0 || k[i] > 64 || k[i] <= mask_width)
+            return fail(nullptr, IFA_ERR_INVALID_ARG, "bins need 1 <= L <= 255 and mask_width < k <= 64");
+        if (k[i] <= L[i]) maxK = std::max(maxK, (L[i] - k[i]) / step + 2);
+    }
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail_cuda(nullptr, "cudaSetDevice", e);
+    std::string err;
+    ifa_status st = minhits_device(L, subs, k, n, step, mask_width, max_clips, num, den, trials, seed, out,
+                                   nullptr, maxK, err);
+    if (st != IFA_OK) g_err = err;
+    return st;
+}
+
+const char *ifa_last_error(const ifa_handle *h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

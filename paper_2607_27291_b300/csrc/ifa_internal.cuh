@@ -1,0 +1,119 @@
+// ifa_internal.cuh -- device-side layouts shared by the kernels and the host engine.
+//
+// Reference layout in HBM ("packed words"): base i of a batch lives in bit
+// (i & 31) of word i >> 5 of four planes, stored interleaved as one uint4
+// per 32 bases:
+//   .x  hi plane   (code >> 1)
+//   .y  lo plane   (code & 1)
+//   .z  N plane    (1 where the byte is not A/C/G/T)
+//   .w  B plane    (1 at the first base of every contig piece but the first)
+// with code A=0, C=1, T=2, G=3 (the byte's bits 1..2), so the complement of
+// a base is code ^ 2.  One 16-byte load gives a thread all four planes of
+// 32 bases; 0.5 byte per base.
+//
+// Query table ("entries"): entry e = 2*q + t holds query q on strand t
+// (t = 1: reverse complement, precomputed) as WMAX uint4 words
+//   .x hi, .y lo,
+//   .z care mask: 1 where position < L and the query base is A/C/G/T,
+//   .w length mask: 1 where position < L,
+// and a meta word L | W << 8 | nN << 16 (W = words used, nN = query Ns,
+// which always count as mismatches).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ifa.h"
+
+namespace ifa {
+
+constexpr int kWarp = 32;
+
+struct DevPiece {
+    uint64_t start;        // first base of the piece in batch coordinates
+    uint64_t contig_off;   // contig coordinate of `start`
+    uint32_t contig;       // caller's contig id
+    uint32_t pad;
+};
+
+struct HitSink {
+    ifa_hit *ring;                 // hit buffer (may be null in count-only mode)
+    unsigned long long *head;      // total hits claimed (can exceed capacity)
+    unsigned long long capacity;
+    unsigned long long *digest;    // [count, sum, xor]
+    unsigned long long *qcount;    // per query
+    uint32_t *overflow;            // set to 1 when a hit is dropped
+    int count_only;
+};
+
+struct QueryTable {
+    const uint4 *words;      // entries x wmax
+    const uint32_t *meta;    // entries
+    const uint32_t *ids;     // optional: original entry id of each entry (null = identity)
+    uint32_t n_entries;      // 2 * queries
+    uint32_t wmax;
+};
+
+struct Batch {
+    const uint4 *words;       // packed planes, >= nbases/32 + 9 words, padding zeroed
+    uint64_t nbases;          // halo + segment
+    uint32_t halo;            // windows must end at or after this base
+    const DevPiece *pieces;
+    uint32_t npieces;
+};
+
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ inline uint64_t hit_digest_item(uint32_t q, uint32_t contig, uint32_t pos,
+                                                    uint32_t strand, uint32_t mm) {
+    uint64_t a = (static_cast<uint64_t>(q) << 32) | contig;
+    uint64_t b = (static_cast<uint64_t>(pos) << 32) | (strand << 8) | mm;
+    return mix64(a ^ mix64(b));
+}
+
+// 2-bit code of an ASCII byte and whether it is a base.
+__host__ __device__ inline uint32_t base_code(uint32_t c) { return (c >> 1) & 3u; }
+__host__ __device__ inline bool is_base(uint32_t c) {
+    uint32_t u = c & 0xDFu;
+    return u == 'A' || u == 'C' || u == 'G' || u == 'T';
+}
+
+// Last piece whose start is <= p (pieces sorted by start, pieces[0].start == 0).
+__device__ inline uint32_t find_piece(const DevPiece *pc, uint32_t n, uint64_t p) {
+    uint32_t lo = 0, hi = n;  // answer in [lo, hi)
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (pc[mid].start <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- launchers
+// (defined in the .cu files; all enqueue on `st`)
+
+cudaError_t launch_pack(const uint8_t *halo, uint32_t hlen, const uint8_t *seg, uint64_t slen,
+                        uint4 *words, uint64_t nwords_padded, cudaStream_t st);
+cudaError_t launch_mark_pieces(const DevPiece *pieces, uint32_t n, uint4 *words, cudaStream_t st);
+cudaError_t launch_halo_update(const uint8_t *old_halo, uint32_t old_len, const uint8_t *seg,
+                               uint64_t slen, uint32_t new_len, uint8_t *new_halo, cudaStream_t st);
+
+struct ScanLaunch {
+    int grid;
+    int block;
+    size_t smem;
+};
+cudaError_t launch_scan_brute(const Batch &b, const QueryTable &qt, uint32_t e0, uint32_t e1,
+                              uint32_t max_subs, uint32_t lmin, uint32_t lmax, const HitSink &sink,
+                              cudaStream_t st, int *launches);
+uint32_t scan_brute_chunk_entries(uint32_t wmax);
+
+cudaError_t launch_minhits(const uint32_t *dL, const uint32_t *dsubs, const uint32_t *dk,
+                           uint32_t nbins, uint32_t step, uint32_t mask_w, uint32_t max_clips,
+                           uint32_t num, uint32_t den, uint32_t trials, uint64_t seed,
+                           uint32_t *dhist_scratch, uint32_t hist_stride, uint32_t *dout,
+                           cudaStream_t st);
+
+}  // namespace ifa

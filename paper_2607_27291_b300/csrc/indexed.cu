@@ -1,0 +1,515 @@
+// indexed.cu -- indexed mode (Methods, indexed mode).
+//
+// The paper indexes each reference contig (PackedIndex) and looks the query
+// seeds up in it, counting seed hits per diagonal before verifying
+// candidates.  On the GPU the roles are inverted: the query k-mers are
+// tabulated once, and every reference position's k-mer is looked up in
+// that table as the segment streams past.  The set of (query, strand,
+// window) candidates is the same either way.
+//
+// Per-diagonal counting without counters: each seed hit (query entry e,
+// offset o, reference position j) names the window p = j - o, which is
+// verified at once.  Verification builds the window's mismatch bitmask x;
+// the k-mer at offset o' is error-free exactly when x has no set bit among
+// its counted positions, so the window's full seed count S and its first
+// seed come out of x.  The window is reported by the seed hit whose offset
+// is that first seed (so exactly once), when mm <= maxSubs and
+// |S| >= minHits.  This equals "seed count on the diagonal reaches the
+// threshold, then Hamming verification".
+//
+// Queries that contain N, or that get no usable seed length, are scanned
+// exhaustively by the brute-force kernel (compacted table).
+#include <algorithm>
+#include <cstring>
+#include <map>
+
+#include "hits.cuh"
+#include "indexed.cuh"
+
+namespace ifa {
+
+namespace {
+
+constexpr int kSeedThreads = 256;
+constexpr int kSeedWarps = kSeedThreads / kWarp;
+
+template <int WMAX>
+__global__ void __launch_bounds__(kSeedThreads)
+k_seed_scan(Batch b, QueryTable qt, KTablesArg tabs, const uint32_t *__restrict__ entry_minhits,
+            uint32_t step, uint32_t s, HitSink sink, unsigned long long *candidates) {
+    __shared__ ifa_hit wbuf[kSeedWarps][32];
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = threadIdx.x >> 5;
+    WarpHits wh;
+    wh.init(wbuf[warp]);
+    unsigned long long ncand = 0;
+
+    const uint64_t nblocks = (b.nbases + 31) >> 5;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kSeedWarps;
+    for (uint64_t blk = static_cast<uint64_t>(blockIdx.x) * kSeedWarps + warp; blk < nblocks; blk += stride) {
+        const uint64_t j = (blk << 5) + lane;
+        const uint4 A = __ldg(b.words + blk), B = __ldg(b.words + blk + 1);
+        const uint32_t hiw = __funnelshift_r(A.x, B.x, lane);
+        const uint32_t low = __funnelshift_r(A.y, B.y, lane);
+        const uint32_t nw = __funnelshift_r(A.z, B.z, lane);
+        const uint32_t bw = __funnelshift_r(A.w, B.w, lane);
+        for (uint32_t ti = 0; ti < tabs.n; ti++) {
+            const KTableDev &T = tabs.t[ti];
+            const uint32_t k = T.k;
+            const uint32_t full = (k >= 32) ? 0xffffffffu : ((1u << k) - 1u);
+            uint32_t beg = 0, end = 0;
+            if (j + k <= b.nbases && (nw & full) == 0u && ((bw >> 1) & (full >> 1)) == 0u) {
+                const uint32_t key = ((hiw & T.care) << k) | (low & T.care);
+                if (T.direct) {
+                    beg = __ldg(T.off + key);
+                    end = __ldg(T.off + key + 1);
+                } else if ((__ldg(T.bits + (key >> 5)) >> (key & 31)) & 1u) {
+                    uint32_t lo = 0, hi = T.nuniq;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (__ldg(T.keys + mid) < key) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo < T.nuniq && __ldg(T.keys + lo) == key) {
+                        beg = __ldg(T.off + lo);
+                        end = __ldg(T.off + lo + 1);
+                    }
+                }
+            }
+            // warp-synchronous walk over each lane's postings so hits can be
+            // compacted by ballot
+            while (__any_sync(0xffffffffu, beg < end)) {
+                bool hit = false;
+                uint32_t id = 0, contig = 0, pos = 0, mm = 0;
+                if (beg < end) {
+                    const uint32_t pv = __ldg(T.post + beg);
+                    beg++;
+                    const uint32_t e = pv >> 8, o = pv & 0xffu;
+                    const uint32_t meta = __ldg(qt.meta + e);
+                    const uint32_t L = meta & 0xffu, W = (meta >> 8) & 0xffu;
+                    if (o <= j) {
+                        const uint64_t p = j - o;
+                        if (p + L <= b.nbases && p + L >= static_cast<uint64_t>(b.halo) + 1) {
+                            ncand++;
+                            const uint64_t w0 = p >> 5;
+                            const uint32_t sh = static_cast<uint32_t>(p & 31);
+                            uint32_t x[WMAX + 1];
+                            uint32_t bnd = 0;
+                            mm = 0;
+                            uint4 cur = __ldg(b.words + w0);
+#pragma unroll
+                            for (int w = 0; w < WMAX; w++) {
+                                x[w] = 0;
+                                if (w < static_cast<int>(W)) {
+                                    const uint4 nx = __ldg(b.words + w0 + w + 1);
+                                    const uint32_t rh = __funnelshift_r(cur.x, nx.x, sh);
+                                    const uint32_t rl = __funnelshift_r(cur.y, nx.y, sh);
+                                    const uint32_t rn = __funnelshift_r(cur.z, nx.z, sh);
+                                    uint32_t rb = __funnelshift_r(cur.w, nx.w, sh);
+                                    if (w == 0) rb &= ~1u;
+                                    const uint4 q = __ldg(qt.words + static_cast<size_t>(e) * WMAX + w);
+                                    x[w] = ((rh ^ q.x) | (rl ^ q.y) | rn) & q.w;
+                                    mm += __popc(x[w]);
+                                    bnd |= rb & q.w;
+                                    cur = nx;
+                                }
+                            }
+                            x[WMAX] = 0;
+                            if (bnd == 0u && mm <= s) {
+                                // error-free k-mer offsets from the mismatch mask
+                                const uint32_t last = L - k;  // largest offset
+                                uint32_t nseed = 0, first = 0xffffffffu;
+#pragma unroll
+                                for (int w = 0; w < WMAX; w++) {
+                                    if (w < static_cast<int>(W) && static_cast<uint32_t>(w) * 32 <= last) {
+                                        uint32_t c = 0;
+                                        for (uint32_t i = 0; i < k; i++)
+                                            if ((T.care >> i) & 1u) c |= __funnelshift_r(x[w], x[w + 1], i);
+                                        uint32_t valid = 0xffffffffu;
+                                        const uint32_t base = static_cast<uint32_t>(w) * 32;
+                                        if (last - base < 31) valid = (2u << (last - base)) - 1u;
+                                        uint32_t S = ~c & valid;
+                                        if (step > 1) {
+                                            uint32_t sm = 0;
+                                            for (uint32_t bi = 0; bi < 32; bi++)
+                                                if ((base + bi) % step == 0) sm |= 1u << bi;
+                                            S &= sm;
+                                        }
+                                        nseed += __popc(S);
+                                        if (first == 0xffffffffu && S) first = base + __ffs(S) - 1;
+                                    }
+                                }
+                                if (first == o && nseed >= __ldg(entry_minhits + e)) {
+                                    hit = true;
+                                    const DevPiece pc = b.pieces[find_piece(b.pieces, b.npieces, p)];
+                                    contig = pc.contig;
+                                    pos = static_cast<uint32_t>(pc.contig_off + (p - pc.start));
+                                    id = e;
+                                }
+                            }
+                        }
+                    }
+                }
+                wh.emit(sink, lane, hit, id >> 1, contig, pos, id & 1u, mm, nullptr);
+            }
+        }
+    }
+    wh.finish(sink, lane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
+    if (lane == 0 && ncand) atomicAdd(candidates, ncand);
+}
+
+template <int WMAX>
+cudaError_t seed_launch_t(const Batch &b, const QueryTable &qt, const KTablesArg &tabs,
+                          const uint32_t *emh, uint32_t step, uint32_t s, const HitSink &sink,
+                          unsigned long long *cand, cudaStream_t st) {
+    static int grids[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &grid = grids[dev & 63];
+    if (grid == 0) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed_scan<WMAX>, kSeedThreads, 0);
+        grid = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const uint64_t nblocks = (b.nbases + 31) >> 5;
+    const uint64_t need = (nblocks + kSeedWarps - 1) / kSeedWarps;
+    int g = static_cast<int>(need < static_cast<uint64_t>(grid) ? need : grid);
+    if (g < 1) g = 1;
+    k_seed_scan<WMAX><<<g, kSeedThreads, 0, st>>>(b, qt, tabs, emh, step, s, sink, cand);
+    return cudaGetLastError();
+}
+
+// k-mer key of query q (strand t) at offset o: planar hi/lo bits of the
+// counted positions (same code as the device: A=0, C=1, T=2, G=3).
+uint32_t query_key(const std::string &q, bool rc, uint32_t o, uint32_t k, uint32_t care) {
+    const uint32_t L = static_cast<uint32_t>(q.size());
+    uint32_t hi = 0, lo = 0;
+    for (uint32_t i = 0; i < k; i++) {
+        if (!((care >> i) & 1u)) continue;
+        const uint32_t pos = o + i;
+        const uint32_t c = static_cast<uint8_t>(rc ? q[L - 1 - pos] : q[pos]);
+        uint32_t code = base_code(c);
+        if (rc) code ^= 2u;
+        hi |= (code >> 1) << i;
+        lo |= (code & 1u) << i;
+    }
+    return (hi << k) | lo;
+}
+
+bool has_n(const std::string &q) {
+    for (char c : q)
+        if (!is_base(static_cast<uint8_t>(c))) return true;
+    return false;
+}
+
+uint32_t care_mask(uint32_t k, uint32_t mask_w) {
+    uint32_t full = (k >= 32) ? 0xffffffffu : ((1u << k) - 1u);
+    if (!mask_w) return full;
+    const uint32_t mlo = (k - mask_w) / 2;
+    return full & ~(((1u << mask_w) - 1u) << mlo);
+}
+
+}  // namespace
+
+cudaError_t launch_seed_scan(const Batch &b, const QueryTable &qt, const KTablesArg &tabs,
+                             const uint32_t *emh, uint32_t step, uint32_t s, const HitSink &sink,
+                             unsigned long long *cand, cudaStream_t st) {
+    switch (qt.wmax) {
+    case 1: return seed_launch_t<1>(b, qt, tabs, emh, step, s, sink, cand, st);
+    case 2: return seed_launch_t<2>(b, qt, tabs, emh, step, s, sink, cand, st);
+    case 4: return seed_launch_t<4>(b, qt, tabs, emh, step, s, sink, cand, st);
+    case 8: return seed_launch_t<8>(b, qt, tabs, emh, step, s, sink, cand, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+void IndexedState::free_tables() {
+    for (void *p : allocs) cudaFree(p);
+    allocs.clear();
+    targ = KTablesArg{};
+    cudaFree(d_entry_minhits);
+    d_entry_minhits = nullptr;
+    cudaFree(d_ex_words);
+    cudaFree(d_ex_meta);
+    cudaFree(d_ex_ids);
+    d_ex_words = nullptr;
+    d_ex_meta = nullptr;
+    d_ex_ids = nullptr;
+    ex_entries = 0;
+    ex_chunks.clear();
+    any_exhaustive = false;
+    tables_valid = false;
+}
+
+void IndexedState::release() {
+    free_tables();
+    cudaFree(d_candidates);
+    d_candidates = nullptr;
+}
+
+uint64_t IndexedState::candidates_host(cudaStream_t st) const {
+    if (!d_candidates) return 0;
+    unsigned long long v = 0;
+    cudaStreamSynchronize(st);
+    cudaMemcpy(&v, d_candidates, sizeof(v), cudaMemcpyDeviceToHost);
+    return v;
+}
+
+ifa_status minhits_device(const uint32_t *L, const uint32_t *subs, const uint32_t *k, uint32_t n,
+                          uint32_t step, uint32_t mask_w, uint32_t max_clips, uint32_t num, uint32_t den,
+                          uint32_t trials, uint64_t seed, uint32_t *out, cudaStream_t st,
+                          uint32_t stride, std::string &err) {
+    if (n == 0) return IFA_OK;
+    uint32_t *dL = nullptr, *dS = nullptr, *dK = nullptr, *dH = nullptr, *dO = nullptr;
+    const size_t nb = static_cast<size_t>(n) * sizeof(uint32_t);
+    cudaError_t e = cudaSuccess;
+    auto ck = [&](cudaError_t r) {
+        if (e == cudaSuccess && r != cudaSuccess) e = r;
+    };
+    ck(cudaMalloc(&dL, nb));
+    ck(cudaMalloc(&dS, nb));
+    ck(cudaMalloc(&dK, nb));
+    ck(cudaMalloc(&dO, nb));
+    ck(cudaMalloc(&dH, static_cast<size_t>(n) * stride * sizeof(uint32_t)));
+    if (e == cudaSuccess) {
+        ck(cudaMemcpyAsync(dL, L, nb, cudaMemcpyHostToDevice, st));
+        ck(cudaMemcpyAsync(dS, subs, nb, cudaMemcpyHostToDevice, st));
+        ck(cudaMemcpyAsync(dK, k, nb, cudaMemcpyHostToDevice, st));
+        ck(launch_minhits(dL, dS, dK, n, step, mask_w, max_clips, num, den, trials, seed, dH, stride, dO, st));
+        ck(cudaMemcpyAsync(out, dO, nb, cudaMemcpyDeviceToHost, st));
+        ck(cudaStreamSynchronize(st));
+    }
+    cudaFree(dL);
+    cudaFree(dS);
+    cudaFree(dK);
+    cudaFree(dH);
+    cudaFree(dO);
+    if (e != cudaSuccess) {
+        err = std::string("MinHits on the device: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? IFA_ERR_OOM : IFA_ERR_CUDA;
+    }
+    return IFA_OK;
+}
+
+ifa_status indexed_plan(IndexedState &S, const std::vector<std::string> &qs, const ifa_config &cfg,
+                        uint32_t s, cudaStream_t st, std::string &err) {
+    if (S.plan_valid && S.plan_s == s) return IFA_OK;
+    const uint32_t nq = static_cast<uint32_t>(qs.size());
+    std::vector<uint32_t> lens;
+    for (const auto &q : qs) lens.push_back(static_cast<uint32_t>(q.size()));
+    std::vector<uint32_t> ul = lens;
+    std::sort(ul.begin(), ul.end());
+    ul.erase(std::unique(ul.begin(), ul.end()), ul.end());
+    std::vector<uint32_t> bL, bS, bK;
+    uint32_t stride = 2;
+    for (uint32_t L : ul)
+        for (uint32_t i = 0; i < cfg.n_k; i++) {
+            const uint32_t k = cfg.k_list[i];
+            if (k > L || k <= cfg.mask_width) continue;
+            bL.push_back(L);
+            bS.push_back(s);
+            bK.push_back(k);
+            stride = std::max(stride, (L - k) / cfg.kmer_step + 2);
+        }
+    std::vector<uint32_t> bm(bL.size());
+    ifa_status r = minhits_device(bL.data(), bS.data(), bK.data(), static_cast<uint32_t>(bL.size()),
+                                  cfg.kmer_step, cfg.mask_width, cfg.max_clips, cfg.minhits_num,
+                                  cfg.minhits_den, cfg.minhits_trials, cfg.minhits_seed, bm.data(), st,
+                                  stride, err);
+    if (r != IFA_OK) return r;
+    // per length: the longest k with threshold >= 1, else the smallest k clamped to 1
+    std::map<uint32_t, std::pair<int, std::pair<uint32_t, uint32_t>>> choice;  // L -> (status, (k, m))
+    for (uint32_t L : ul) choice[L] = {-1, {0, 0}};
+    for (size_t i = 0; i < bL.size(); i++) {
+        auto &c = choice[bL[i]];
+        if (bm[i] >= 1 && (c.first != 1 || bK[i] > c.second.first)) c = {1, {bK[i], bm[i]}};
+    }
+    for (size_t i = 0; i < bL.size(); i++) {
+        auto &c = choice[bL[i]];
+        if (c.first == 1) continue;
+        if (c.first == -1 || bK[i] < c.second.first) c = {0, {bK[i], 1u}};
+    }
+    S.plan_k.assign(nq, 0);
+    S.plan_minhits.assign(nq, 0);
+    S.plan_exhaustive.assign(nq, 0);
+    for (uint32_t q = 0; q < nq; q++) {
+        const auto &c = choice[lens[q]];
+        S.plan_k[q] = c.second.first;
+        S.plan_minhits[q] = c.second.second;
+        const bool ex = c.first < 0 || (c.first == 0 && cfg.exhaustive_fallback) || has_n(qs[q]);
+        S.plan_exhaustive[q] = ex ? 1 : 0;
+    }
+    S.plan_valid = true;
+    S.plan_s = s;
+    S.tables_valid = false;
+    return IFA_OK;
+}
+
+ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
+                           const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
+                           uint32_t wmax, const ifa_config &cfg, uint32_t s, cudaStream_t st,
+                           std::string &err) {
+    ifa_status r = indexed_plan(S, qs, cfg, s, st, err);
+    if (r != IFA_OK) return r;
+    if (S.tables_valid && S.tables_s == s && S.wmax == wmax) return IFA_OK;
+    S.free_tables();
+    S.wmax = wmax;
+    S.step = cfg.kmer_step;
+    cudaError_t e = cudaSuccess;
+    auto ck = [&](cudaError_t x) {
+        if (e == cudaSuccess && x != cudaSuccess) e = x;
+    };
+    auto dalloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        ck(cudaMalloc(&p, bytes ? bytes : 4));
+        if (p) S.allocs.push_back(p);
+        return p;
+    };
+    const uint32_t nq = static_cast<uint32_t>(qs.size());
+    if (!S.d_candidates) {
+        ck(cudaMalloc(&S.d_candidates, sizeof(unsigned long long)));
+        ck(cudaMemset(S.d_candidates, 0, sizeof(unsigned long long)));
+    }
+    // per-entry thresholds
+    std::vector<uint32_t> emh(2 * nq);
+    for (uint32_t q = 0; q < nq; q++) emh[2 * q] = emh[2 * q + 1] = S.plan_minhits[q];
+    ck(cudaMalloc(&S.d_entry_minhits, emh.size() * sizeof(uint32_t)));
+    ck(cudaMemcpy(S.d_entry_minhits, emh.data(), emh.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    // tables per distinct k among seeded queries
+    std::vector<uint32_t> ks;
+    for (uint32_t q = 0; q < nq; q++)
+        if (!S.plan_exhaustive[q]) ks.push_back(S.plan_k[q]);
+    std::sort(ks.begin(), ks.end());
+    ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+    S.targ.n = static_cast<uint32_t>(ks.size());
+    for (size_t ti = 0; ti < ks.size() && e == cudaSuccess; ti++) {
+        const uint32_t k = ks[ti];
+        const uint32_t care = care_mask(k, cfg.mask_width);
+        std::vector<std::pair<uint32_t, uint32_t>> kv;  // (key, posting)
+        for (uint32_t q = 0; q < nq; q++) {
+            if (S.plan_exhaustive[q] || S.plan_k[q] != k) continue;
+            const uint32_t L = static_cast<uint32_t>(qs[q].size());
+            for (uint32_t t = 0; t < 2; t++)
+                for (uint32_t o = 0; o + k <= L; o += cfg.kmer_step)
+                    kv.push_back({query_key(qs[q], t == 1, o, k, care), ((2 * q + t) << 8) | o});
+        }
+        std::sort(kv.begin(), kv.end());
+        KTableDev &T = S.targ.t[ti];
+        T.k = k;
+        T.care = care;
+        std::vector<uint32_t> post(kv.size());
+        for (size_t i = 0; i < kv.size(); i++) post[i] = kv[i].second;
+        uint32_t *dpost = static_cast<uint32_t *>(dalloc(post.size() * sizeof(uint32_t)));
+        if (dpost) ck(cudaMemcpy(dpost, post.data(), post.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        T.post = dpost;
+        if (k <= kDirectMaxK) {
+            const size_t nkeys = size_t(1) << (2 * k);
+            std::vector<uint32_t> off(nkeys + 1, 0);
+            for (const auto &p : kv) off[p.first + 1]++;
+            for (size_t i = 0; i < nkeys; i++) off[i + 1] += off[i];
+            uint32_t *doff = static_cast<uint32_t *>(dalloc(off.size() * sizeof(uint32_t)));
+            if (doff) ck(cudaMemcpy(doff, off.data(), off.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+            T.direct = 1;
+            T.off = doff;
+            T.keys = nullptr;
+            T.bits = nullptr;
+            T.nuniq = 0;
+        } else {
+            std::vector<uint32_t> keys, off;
+            for (size_t i = 0; i < kv.size(); i++) {
+                if (i == 0 || kv[i].first != kv[i - 1].first) {
+                    keys.push_back(kv[i].first);
+                    off.push_back(static_cast<uint32_t>(i));
+                }
+            }
+            off.push_back(static_cast<uint32_t>(kv.size()));
+            const size_t nbits = size_t(1) << (2 * k);
+            std::vector<uint32_t> bits(nbits / 32, 0);
+            for (uint32_t kk : keys) bits[kk >> 5] |= 1u << (kk & 31);
+            uint32_t *dk = static_cast<uint32_t *>(dalloc(keys.size() * sizeof(uint32_t)));
+            uint32_t *doff = static_cast<uint32_t *>(dalloc(off.size() * sizeof(uint32_t)));
+            uint32_t *db = static_cast<uint32_t *>(dalloc(bits.size() * sizeof(uint32_t)));
+            if (dk && !keys.empty()) ck(cudaMemcpy(dk, keys.data(), keys.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+            if (doff) ck(cudaMemcpy(doff, off.data(), off.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+            if (db) ck(cudaMemcpy(db, bits.data(), bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+            T.direct = 0;
+            T.off = doff;
+            T.keys = dk;
+            T.bits = db;
+            T.nuniq = static_cast<uint32_t>(keys.size());
+        }
+    }
+    // exhaustive queries: compact table for the brute-force kernel
+    std::vector<uint32_t> exq;
+    for (uint32_t q = 0; q < nq; q++)
+        if (S.plan_exhaustive[q]) exq.push_back(q);
+    S.any_exhaustive = !exq.empty();
+    if (S.any_exhaustive && e == cudaSuccess) {
+        const uint32_t ne = 2 * static_cast<uint32_t>(exq.size());
+        std::vector<uint32_t> ids(ne), meta(ne);
+        std::vector<uint4> words(static_cast<size_t>(ne) * wmax);
+        S.ex_entries = ne;
+        ck(cudaMalloc(&S.d_ex_words, static_cast<size_t>(ne) * wmax * sizeof(uint4)));
+        ck(cudaMalloc(&S.d_ex_meta, ne * sizeof(uint32_t)));
+        ck(cudaMalloc(&S.d_ex_ids, ne * sizeof(uint32_t)));
+        for (uint32_t i = 0; i < ne; i++) {
+            const uint32_t src = 2 * exq[i / 2] + (i & 1);
+            ids[i] = src;
+            meta[i] = qmeta[src];
+            for (uint32_t w = 0; w < wmax; w++) words[static_cast<size_t>(i) * wmax + w] = qwords[static_cast<size_t>(src) * wmax + w];
+        }
+        if (e == cudaSuccess) {
+            ck(cudaMemcpy(S.d_ex_words, words.data(), words.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+            ck(cudaMemcpy(S.d_ex_meta, meta.data(), ne * sizeof(uint32_t), cudaMemcpyHostToDevice));
+            ck(cudaMemcpy(S.d_ex_ids, ids.data(), ne * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        }
+        uint32_t cap = scan_brute_chunk_entries(wmax) & ~1u;
+        if (cap < 2) cap = 2;
+        for (uint32_t e0 = 0; e0 < ne; e0 += cap) {
+            IndexedState::ExChunk c{e0, std::min(ne, e0 + cap), 0xffffffffu, 0};
+            for (uint32_t i = c.e0; i < c.e1; i++) {
+                c.lmin = std::min(c.lmin, meta[i] & 0xffu);
+                c.lmax = std::max(c.lmax, meta[i] & 0xffu);
+            }
+            S.ex_chunks.push_back(c);
+        }
+    }
+    if (e != cudaSuccess) {
+        err = std::string("indexed tables: ") + cudaGetErrorString(e);
+        S.free_tables();
+        return e == cudaErrorMemoryAllocation ? IFA_ERR_OOM : IFA_ERR_CUDA;
+    }
+    S.tables_valid = true;
+    S.tables_s = s;
+    return IFA_OK;
+}
+
+ifa_status indexed_scan(IndexedState &S, const Batch &b, const QueryTable &qt, uint32_t s,
+                        const HitSink &sink, cudaStream_t st, int *launches, std::string &err) {
+    cudaError_t e = cudaSuccess;
+    if (S.targ.n) {
+        e = launch_seed_scan(b, qt, S.targ, S.d_entry_minhits, S.step, s, sink, S.d_candidates, st);
+        if (launches) (*launches)++;
+    }
+    if (e == cudaSuccess && S.any_exhaustive) {
+        QueryTable ex;
+        ex.words = S.d_ex_words;
+        ex.meta = S.d_ex_meta;
+        ex.ids = S.d_ex_ids;
+        ex.n_entries = S.ex_entries;
+        ex.wmax = qt.wmax;
+        for (const auto &c : S.ex_chunks) {
+            e = launch_scan_brute(b, ex, c.e0, c.e1, s, c.lmin, c.lmax, sink, st, launches);
+            if (e != cudaSuccess) break;
+        }
+    }
+    if (e != cudaSuccess) {
+        err = std::string("indexed scan: ") + cudaGetErrorString(e);
+        return IFA_ERR_CUDA;
+    }
+    return IFA_OK;
+}
+
+}  // namespace ifa

@@ -1,0 +1,90 @@
+// indexed.cuh -- indexed mode (Methods, indexed mode): per-query seed length
+// and min-hits threshold from the MinHitsCalculator, query k-mer tables on
+// the device, and the seed scan with verification.
+#pragma once
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "ifa_internal.cuh"
+
+namespace ifa {
+
+constexpr int kMaxTables = IFA_MAX_KLIST;
+constexpr uint32_t kDirectMaxK = 12;   // k <= 12: direct-address offsets (4^k + 1 words)
+
+// One seed length's query k-mer table.  Keys are "planar": the k hi-plane
+// bits of the k-mer above its k lo-plane bits (masked positions zeroed), an
+// injective code of the unmasked bases.  Postings are (entry << 8 | offset).
+struct KTableDev {
+    uint32_t k;
+    uint32_t care;         // k-bit mask of the positions that count
+    uint32_t direct;       // 1: off[] indexed by key
+    uint32_t nuniq;        // hashed: number of distinct keys
+    const uint32_t *off;   // direct: 4^k + 1; hashed: nuniq + 1
+    const uint32_t *keys;  // hashed: sorted distinct keys
+    const uint32_t *bits;  // hashed: presence bitmap of 4^k bits
+    const uint32_t *post;  // postings grouped by key
+};
+
+struct KTablesArg {
+    KTableDev t[kMaxTables];
+    uint32_t n;
+};
+
+struct IndexedState {
+    // plan (per query) for plan_s
+    bool plan_valid = false;
+    uint32_t plan_s = 0;
+    std::vector<uint32_t> plan_k, plan_minhits;
+    std::vector<uint8_t> plan_exhaustive;
+
+    // device tables for tables_s
+    bool tables_valid = false;
+    uint32_t tables_s = 0;
+    KTablesArg targ{};
+    std::vector<void *> allocs;
+    uint32_t *d_entry_minhits = nullptr;
+    unsigned long long *d_candidates = nullptr;
+    uint32_t wmax = 1;
+    uint32_t step = 1;
+
+    // exhaustive queries: compacted table scanned by the brute kernel
+    bool any_exhaustive = false;
+    uint4 *d_ex_words = nullptr;
+    uint32_t *d_ex_meta = nullptr;
+    uint32_t *d_ex_ids = nullptr;
+    uint32_t ex_entries = 0;
+    struct ExChunk { uint32_t e0, e1, lmin, lmax; };
+    std::vector<ExChunk> ex_chunks;
+
+    void invalidate() {
+        plan_valid = false;
+        tables_valid = false;
+    }
+    void free_tables();
+    void release();
+    uint64_t candidates_host(cudaStream_t st) const;
+};
+
+ifa_status minhits_device(const uint32_t *L, const uint32_t *subs, const uint32_t *k, uint32_t n,
+                          uint32_t step, uint32_t mask_w, uint32_t max_clips, uint32_t num,
+                          uint32_t den, uint32_t trials, uint64_t seed, uint32_t *out,
+                          cudaStream_t st, uint32_t hist_stride, std::string &err);
+
+ifa_status indexed_plan(IndexedState &S, const std::vector<std::string> &qs, const ifa_config &cfg,
+                        uint32_t max_subs, cudaStream_t st, std::string &err);
+
+ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
+                           const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
+                           uint32_t wmax, const ifa_config &cfg, uint32_t max_subs, cudaStream_t st,
+                           std::string &err);
+
+ifa_status indexed_scan(IndexedState &S, const Batch &b, const QueryTable &qt, uint32_t max_subs,
+                        const HitSink &sink, cudaStream_t st, int *launches, std::string &err);
+
+cudaError_t launch_seed_scan(const Batch &b, const QueryTable &qt, const KTablesArg &tabs,
+                             const uint32_t *entry_minhits, uint32_t step, uint32_t max_subs,
+                             const HitSink &sink, unsigned long long *candidates, cudaStream_t st);
+
+}  // namespace ifa

@@ -1,0 +1,126 @@
+"""Host-side checks of the C ABI: no GPU needed.
+
+The library must load, export every function include/ifa.h declares, lay
+out its structs as the header says (checked with gcc against the header
+itself), carry the paper's defaults, and refuse bad arguments before
+touching a device."""
+import ctypes as C
+import json
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import paper_2607_27291_b300 as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ifa.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ifa_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = P.lib()
+    names = _declared()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(P.exported_symbols()) == names
+
+
+def test_struct_layout_matches_header():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "ifa.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(ifa_hit), sizeof(ifa_digest), sizeof(ifa_piece),
+         sizeof(ifa_config), sizeof(ifa_stats));
+  printf("%zu %zu %zu %zu\n", offsetof(ifa_hit, strand), offsetof(ifa_hit, mismatches),
+         offsetof(ifa_config, minhits_seed), offsetof(ifa_config, auto_crossover));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        out = subprocess.check_output([exe]).decode().split()
+    sizes = list(map(int, out[:5]))
+    offs = list(map(int, out[5:]))
+    assert sizes == [16, 24, 32, C.sizeof(P.ifa_config), C.sizeof(P.ifa_stats)]
+    assert P.HIT_DTYPE.itemsize == 16 and P.PIECE_DTYPE.itemsize == 32
+    assert offs == [12, 13, P.ifa_config.minhits_seed.offset, P.ifa_config.auto_crossover.offset]
+
+
+def test_defaults_are_the_papers():
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_defaults.json")))
+    cfg = P.ifa_config_default()
+    assert list(cfg.k_list)[:cfg.n_k] == g["k_list"]["value"]
+    assert (cfg.minhits_num, cfg.minhits_den) == (g["minhits_probability"]["num"],
+                                                  g["minhits_probability"]["den"])
+    assert cfg.minhits_trials == g["minhits_trials"]["value"]
+    assert g["crossover_queries"]["low"] <= cfg.auto_crossover <= g["crossover_queries"]["high"]
+    assert cfg.max_clips == 0 and cfg.kmer_step == 1 and cfg.mask_width == 0
+
+
+def test_bad_config_rejected_before_device():
+    for kw in ({"max_clips": 1}, {"n_k": 0}, {"kmer_step": 0}, {"minhits_den": 0},
+               {"k_list": [40]}, {"segment_bytes": 0}):
+        with pytest.raises(P.IfaError) as ei:
+            P.ifa_create(**kw)
+        assert ei.value.status == P.IFA_ERR_INVALID_ARG, kw
+    # NULL pointers return a status, they do not crash
+    assert P.lib().ifa_create(None, None) == P.IFA_ERR_INVALID_ARG
+    assert P.lib().ifa_flush(None) == P.IFA_ERR_INVALID_ARG
+    assert P.lib().ifa_push_segment(None, None, 0, None, 0, 0) == P.IFA_ERR_INVALID_ARG
+    assert P.ifa_last_error(None)
+
+
+def test_minhits_entry_point_validates():
+    with pytest.raises(P.IfaError):
+        P.ifa_minhits(0, [20], [2], [0])          # k = 0
+    with pytest.raises(P.IfaError):
+        P.ifa_minhits(0, [300], [2], [8])         # L > 255
+    with pytest.raises(P.IfaError):
+        P.ifa_minhits(0, [20], [2], [8], step=0)
+
+
+def test_segment_pieces_cover_reference():
+    lens = np.array([5, 1, 17, 3, 40, 2], np.int64)
+    for seg in (1, 4, 7, 16, 100):
+        covered = []
+        prev_open = None
+        for a, b, pc in P.segment_pieces(lens, seg):
+            assert pc["start"][0] == 0
+            assert (np.diff(pc["start"].astype(np.int64)) == pc["len"][:-1].astype(np.int64)).all()
+            assert int(pc["len"].sum()) == b - a
+            assert (pc["last"][:-1] == 1).all()
+            if prev_open is not None:
+                assert pc["contig"][0] == prev_open[0] and pc["offset_in_contig"][0] == prev_open[1]
+            prev_open = None if pc["last"][-1] else (pc["contig"][-1],
+                                                     pc["offset_in_contig"][-1] + pc["len"][-1])
+            for r in pc:
+                covered.append((int(r["contig"]), int(r["offset_in_contig"]), int(r["len"])))
+        per = {}
+        for c, o, ln in covered:
+            assert per.get(c, 0) == o
+            per[c] = o + ln
+        assert [per[i] for i in range(len(lens))] == lens.tolist()
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(P.IfaError) as ei:
+        P.ifa_create()
+    assert ei.value.status == P.IFA_ERR_CUDA
