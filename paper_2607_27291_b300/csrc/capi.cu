@@ -21,7 +21,7 @@ namespace {
 
 thread_local std::string g_err = "no error";
 
-constexpr uint32_t kHaloCap = 256;   // > IFA_MAX_QUERY_LEN - 1
+constexpr uint32_t kHaloCap = 256;   // >= halo region H = 32 * ceil((IFA_MAX_QUERY_LEN - 1) / 32)
 constexpr uint64_t kWordPad = 16;    // zeroed words after the last packed word
 
 struct Chunk {
@@ -467,10 +467,13 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
     st = ensure_pieces(h, slot, n);
     if (st != IFA_OK) return st;
 
+    // halo region: H bases (a multiple of 32), the continuing contig's last
+    // hlen bases at its end, 'N' padding before them
     const uint32_t hlen = h->open ? h->halo_len : 0u;
+    const uint32_t H = h->open ? ((h->lmax + 30u) / 32u) * 32u : 0u;
     DevPiece *hp = h->h_pieces[slot];
     for (uint32_t i = 0; i < n; i++) {
-        hp[i].start = i == 0 ? 0 : hlen + pieces[i].start;
+        hp[i].start = i == 0 ? H - hlen : H + pieces[i].start;
         hp[i].contig_off = pieces[i].offset_in_contig - (i == 0 ? hlen : 0);
         hp[i].contig = pieces[i].contig;
         hp[i].pad = 0;
@@ -491,19 +494,19 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
     CK(h, cudaEventRecord(h->ev_copied[slot], h->copy_stream));
     CK(h, cudaStreamWaitEvent(h->stream, h->ev_copied[slot], 0));
 
-    const uint64_t nbases = hlen + len;
+    const uint64_t nbases = H + len;
     const uint64_t nwords = (nbases + 31) / 32 + kWordPad;
     int launches = 0;
-    CK(h, launch_pack(h->d_halo[h->halo_cur], hlen, dsrc, len, h->d_words, nwords, h->stream));
+    CK(h, launch_pack(h->d_halo[h->halo_cur], hlen, H, dsrc, len, h->d_words, nwords, h->stream));
     launches++;
-    if (n > 1) {
+    if (n > 1 || H > hlen) {
         CK(h, launch_mark_pieces(h->d_pieces[slot], n, h->d_words, h->stream));
         launches++;
     }
     Batch b;
     b.words = h->d_words;
     b.nbases = nbases;
-    b.halo = hlen;
+    b.halo = H;
     b.pieces = h->d_pieces[slot];
     b.npieces = n;
     QueryTable qt;

@@ -6,7 +6,7 @@
 //   .x  hi plane   (code >> 1)
 //   .y  lo plane   (code & 1)
 //   .z  N plane    (1 where the byte is not A/C/G/T)
-//   .w  B plane    (1 at the first base of every contig piece but the first)
+//   .w  B plane    (1 at the first base of every contig piece not at base 0)
 // with code A=0, C=1, T=2, G=3 (the byte's bits 1..2), so the complement of
 // a base is code ^ 2.  One 16-byte load gives a thread all four planes of
 // 32 bases; 0.5 byte per base.
@@ -55,8 +55,8 @@ struct QueryTable {
 
 struct Batch {
     const uint4 *words;       // packed planes, >= nbases/32 + 9 words, padding zeroed
-    uint64_t nbases;          // halo + segment
-    uint32_t halo;            // windows must end at or after this base
+    uint64_t nbases;          // halo region + segment
+    uint32_t halo;            // halo region length H; windows must end at or after base H
     const DevPiece *pieces;
     uint32_t npieces;
 };
@@ -94,17 +94,12 @@ __device__ inline uint32_t find_piece(const DevPiece *pc, uint32_t n, uint64_t p
 // ---------------------------------------------------------------- launchers
 // (defined in the .cu files; all enqueue on `st`)
 
-cudaError_t launch_pack(const uint8_t *halo, uint32_t hlen, const uint8_t *seg, uint64_t slen,
-                        uint4 *words, uint64_t nwords_padded, cudaStream_t st);
+cudaError_t launch_pack(const uint8_t *halo, uint32_t hlen, uint32_t H, const uint8_t *seg,
+                        uint64_t slen, uint4 *words, uint64_t nwords_padded, cudaStream_t st);
 cudaError_t launch_mark_pieces(const DevPiece *pieces, uint32_t n, uint4 *words, cudaStream_t st);
 cudaError_t launch_halo_update(const uint8_t *old_halo, uint32_t old_len, const uint8_t *seg,
                                uint64_t slen, uint32_t new_len, uint8_t *new_halo, cudaStream_t st);
 
-struct ScanLaunch {
-    int grid;
-    int block;
-    size_t smem;
-};
 cudaError_t launch_scan_brute(const Batch &b, const QueryTable &qt, uint32_t e0, uint32_t e1,
                               uint32_t max_subs, uint32_t lmin, uint32_t lmax, const HitSink &sink,
                               cudaStream_t st, int *launches);

@@ -2,61 +2,69 @@
 //
 // The reference is streamed as ASCII and never pre-indexed (Methods,
 // "Algorithm Design"); each pushed segment is packed here, in HBM, right
-// before it is scanned.  A batch is the previous segment's halo (the last
-// L_max - 1 bases of a contig that continues) followed by the new segment.
+// before it is scanned.  A batch is a halo region of H bases (H a multiple
+// of 32: 'N' padding, then the last <= L_max - 1 bases of a contig that
+// continues from the previous segment) followed by the new segment, which
+// therefore starts on a word boundary and is read with aligned vectors.
 #include "ifa_internal.cuh"
 
 namespace ifa {
 
 namespace {
 
-constexpr int kPackThreads = 256;                 // one output word per thread
-constexpr int kPackBases = kPackThreads * 32;     // bases per CTA
+constexpr int kPackThreads = 256;  // one output word (32 bases) per thread
 
+__device__ __forceinline__ void pack_byte(uint32_t c, uint32_t bit, uint32_t &hi, uint32_t &lo,
+                                          uint32_t &nn) {
+    const uint32_t ok = is_base(c) ? 1u : 0u;
+    const uint32_t code = base_code(c) * ok;
+    hi |= (code >> 1) << bit;
+    lo |= (code & 1u) << bit;
+    nn |= (ok ^ 1u) << bit;
+}
+
+// Word w of the batch.  Words below H/32 hold the halo region: 'N' padding
+// up to H - hlen, then the hlen halo bases.  Word H/32 + i holds segment
+// bytes [32 i, 32 i + 32), read as two 16-byte vectors when the segment is
+// 16-byte aligned; bytes past the segment end are N.
+template <bool ALIGNED>
 __global__ void __launch_bounds__(kPackThreads)
-k_pack(const uint8_t *__restrict__ halo, uint32_t hlen, const uint8_t *__restrict__ seg,
+k_pack(const uint8_t *__restrict__ halo, uint32_t hlen, uint32_t H, const uint8_t *__restrict__ seg,
        uint64_t slen, uint4 *__restrict__ words, uint64_t nwords) {
-    __shared__ uint32_t sbuf[kPackBases / 4];
-    uint8_t *sb = reinterpret_cast<uint8_t *>(sbuf);
-    const uint64_t base0 = static_cast<uint64_t>(blockIdx.x) * kPackBases;
-    const uint64_t total = hlen + slen;
-    // coalesced byte loads: a warp reads 32 consecutive bytes per step
-    for (int i = threadIdx.x; i < kPackBases; i += kPackThreads) {
-        uint64_t g = base0 + i;
-        uint8_t c = 'N';
-        if (g < hlen) c = halo[g];
-        else if (g < total) c = seg[g - hlen];
-        sb[i] = c;
-    }
-    __syncthreads();
     const uint64_t w = static_cast<uint64_t>(blockIdx.x) * kPackThreads + threadIdx.x;
     if (w >= nwords) return;
     uint32_t hi = 0, lo = 0, nn = 0;
-    const uint32_t t = threadIdx.x;
+    const uint64_t hw = H >> 5;
+    if (w < hw) {
+        const uint32_t pad = H - hlen;
+        for (uint32_t b = 0; b < 32; b++) {
+            const uint32_t i = static_cast<uint32_t>(w) * 32 + b;
+            pack_byte(i < pad ? 'N' : halo[i - pad], b, hi, lo, nn);
+        }
+    } else {
+        const uint64_t o = (w - hw) * 32;
+        if (ALIGNED && o + 32 <= slen) {
+            const uint4 *v = reinterpret_cast<const uint4 *>(seg + o);
+            const uint4 a = __ldg(v), c = __ldg(v + 1);
+            const uint32_t u[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
 #pragma unroll
-    for (int jj = 0; jj < 8; jj++) {
-        // rotated order: lanes t = a + 4m read banks 8a + (jj + t + t/8) mod 8,
-        // which are distinct over the warp, so the reads are conflict-free
-        const uint32_t j = (jj + t + (t >> 3)) & 7u;
-        const uint32_t v = sbuf[t * 8 + j];
+            for (int j = 0; j < 8; j++)
 #pragma unroll
-        for (int b = 0; b < 4; b++) {
-            const uint32_t c = (v >> (8 * b)) & 0xFFu;
-            const uint32_t bit = j * 4 + b;
-            const uint32_t ok = is_base(c) ? 1u : 0u;
-            const uint32_t code = base_code(c) * ok;
-            hi |= (code >> 1) << bit;
-            lo |= (code & 1u) << bit;
-            nn |= (ok ^ 1u) << bit;
+                for (int b = 0; b < 4; b++) pack_byte((u[j] >> (8 * b)) & 0xffu, j * 4 + b, hi, lo, nn);
+        } else {
+            for (uint32_t b = 0; b < 32; b++)
+                pack_byte(o + b < slen ? seg[o + b] : 'N', b, hi, lo, nn);
         }
     }
     words[w] = make_uint4(hi, lo, nn, 0u);
 }
 
+// B plane: a bit at the first base of every piece that does not start the batch.
 __global__ void k_mark_pieces(const DevPiece *__restrict__ pc, uint32_t n, uint4 *__restrict__ words) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x + 1;  // piece 0 starts the batch
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint64_t p = pc[i].start;
+    const uint64_t p = pc[i].start;
+    if (p == 0) return;
     uint32_t *w = reinterpret_cast<uint32_t *>(words + (p >> 5)) + 3;
     atomicOr(w, 1u << (p & 31));
 }
@@ -73,18 +81,22 @@ __global__ void k_halo_update(const uint8_t *__restrict__ old_halo, uint32_t old
 
 }  // namespace
 
-cudaError_t launch_pack(const uint8_t *halo, uint32_t hlen, const uint8_t *seg, uint64_t slen,
-                        uint4 *words, uint64_t nwords_padded, cudaStream_t st) {
+cudaError_t launch_pack(const uint8_t *halo, uint32_t hlen, uint32_t H, const uint8_t *seg,
+                        uint64_t slen, uint4 *words, uint64_t nwords_padded, cudaStream_t st) {
     if (nwords_padded == 0) return cudaSuccess;
-    uint64_t grid = (nwords_padded + kPackThreads - 1) / kPackThreads;
-    k_pack<<<static_cast<unsigned>(grid), kPackThreads, 0, st>>>(halo, hlen, seg, slen, words,
-                                                                 nwords_padded);
+    const uint64_t grid = (nwords_padded + kPackThreads - 1) / kPackThreads;
+    if ((reinterpret_cast<uintptr_t>(seg) & 15u) == 0)
+        k_pack<true><<<static_cast<unsigned>(grid), kPackThreads, 0, st>>>(halo, hlen, H, seg, slen, words,
+                                                                           nwords_padded);
+    else
+        k_pack<false><<<static_cast<unsigned>(grid), kPackThreads, 0, st>>>(halo, hlen, H, seg, slen, words,
+                                                                            nwords_padded);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mark_pieces(const DevPiece *pieces, uint32_t n, uint4 *words, cudaStream_t st) {
-    if (n <= 1) return cudaSuccess;
-    unsigned grid = (n - 1 + 255) / 256;
+    if (n == 0) return cudaSuccess;
+    unsigned grid = (n + 255) / 256;
     k_mark_pieces<<<grid, 256, 0, st>>>(pieces, n, words);
     return cudaGetLastError();
 }
