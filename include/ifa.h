@@ -226,8 +226,51 @@ ifa_status ifa_minhits(int32_t device, const uint32_t *L, const uint32_t *subs, 
                        uint32_t n, uint32_t step, uint32_t mask_width, uint32_t max_clips,
                        uint32_t num, uint32_t den, uint32_t trials, uint64_t seed, uint32_t *out);
 
+/* Brute-force scan of one reference chunk that allocates no memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc at the point where they scan -- for example code
+ * inside a framework whose caching allocator already holds the device
+ * memory, where any allocation outside it fails, or a serving loop with a
+ * fixed memory plan.  The caller passes every input and output buffer; the
+ * library's own scratch (packed reference planes, encoded queries, piece
+ * table, per-query counts when per_query_counts_device is NULL) lives in one
+ * file-scope device array of about 17 MB, which every GPU that loads the
+ * library holds until the process exits.  No call allocates device or
+ * pinned memory (torch's allocator included).
+ *
+ * Limits: 1..256 queries (1..255 bp each), 1..32 MiB of reference, 1..32768
+ * whole contigs (every piece has last = 1 and offset_in_contig = 0; no
+ * halo is carried between calls).  Larger sizes return
+ * IFA_ERR_INVALID_ARG with a message naming the limit, before anything is
+ * enqueued.
+ *
+ * queries/qlens: host ASCII, as for ifa_load_queries.  ref_device: len
+ * ASCII bytes in device memory.  pieces: host, as for ifa_push_segment.
+ * hits_device: room for hit_capacity ifa_hit (device).  counters_device:
+ * 5 uint64 on the device, set to {hits claimed (may exceed hit_capacity),
+ * overflow flag, digest count, digest sum, digest xor}.
+ * per_query_counts_device: nq uint64 on the device, or NULL.  stream: the
+ * cudaStream_t to enqueue on (NULL = legacy default stream).  Results are
+ * in the caller's buffers once the stream has passed this call's work; hit
+ * order is unspecified.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one scratch array and leaves its
+ * contents behind; each call clears what must start at zero (the counters
+ * and per-query counts) itself.  Calls whose device work overlaps -- two
+ * streams, or two threads -- race on the scratch and give wrong results. */
+ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *const *queries,
+                                  const uint32_t *qlens, uint32_t nq, const uint8_t *ref_device,
+                                  uint64_t len, const ifa_piece *pieces, uint32_t n_pieces,
+                                  uint32_t max_subs, ifa_hit *hits_device, uint64_t hit_capacity,
+                                  uint64_t *counters_device, uint64_t *per_query_counts_device,
+                                  void *stream);
+
 /* Human-readable description of the last failure on h (or of the last
- * failed ifa_create/ifa_minhits when h is NULL).  Never NULL. */
+ * failed ifa_create/ifa_minhits/ifa_scan_brute_noalloc when h is NULL).
+ * Never NULL. */
 const char *ifa_last_error(const ifa_handle *h);
 
 #ifdef __cplusplus

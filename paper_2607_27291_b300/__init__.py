@@ -85,6 +85,10 @@ _SYMBOLS = {
                               C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                               C.c_uint32, C.c_uint64, C.c_void_p]),
     "ifa_last_error": (C.c_char_p, [C.c_void_p]),
+    "ifa_scan_brute_noalloc": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
+                                         C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32,
+                                         C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]),
 }
 
 
@@ -250,6 +254,24 @@ def ifa_minhits(device: int, L, subs, k, step: int = 1, mask_width: int = 0, max
     _check(lib().ifa_minhits(device, L.ctypes.data, subs.ctypes.data, k.ctypes.data, L.size, step,
                              mask_width, max_clips, num, den, trials, seed, out.ctypes.data))
     return out
+
+
+def ifa_scan_brute_noalloc(device: int, queries: Sequence[bytes], ref_ptr: int, length: int,
+                           pieces, max_subs: int, hits_ptr: int, hit_capacity: int,
+                           counters_ptr: int, per_query_counts_ptr: int = 0, stream=None) -> None:
+    """Allocation-free brute-force scan of one chunk of whole contigs; every
+    buffer is the caller's (device pointers as ints)."""
+    n = len(queries)
+    bufs = [C.create_string_buffer(bytes(q), len(q)) for q in queries]
+    ptrs = (C.c_void_p * max(1, n))(*[C.cast(b, C.c_void_p) for b in bufs])
+    lens = (C.c_uint32 * max(1, n))(*[len(q) for q in queries])
+    pa = _as_pieces(pieces)
+    sptr = getattr(stream, "cuda_stream", stream)
+    _check(lib().ifa_scan_brute_noalloc(device, ptrs, lens, n, C.c_void_p(ref_ptr), length,
+                                        pa.ctypes.data, pa.size, max_subs, C.c_void_p(hits_ptr),
+                                        hit_capacity, C.c_void_p(counters_ptr),
+                                        C.c_void_p(per_query_counts_ptr or None),
+                                        C.c_void_p(sptr or None)))
 
 
 def ifa_last_error(h=None) -> str:

@@ -248,6 +248,11 @@ ifa_status prof_collect(ifa_handle *h) {
 
 }  // namespace
 
+namespace ifa {
+// Record a failure for ifa_last_error(NULL) from entry points in other files.
+void set_global_error(const std::string &msg) { g_err = msg; }
+}  // namespace ifa
+
 // ------------------------------------------------------------------------ API
 
 extern "C" {

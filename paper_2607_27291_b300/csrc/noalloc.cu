@@ -1,0 +1,202 @@
+// noalloc.cu -- brute-force scan of one reference chunk without allocating.
+//
+// Some callers cannot call cudaMalloc: code that runs where a framework's
+// caching allocator already owns the device memory and any allocation
+// outside it fails, or a host that must not allocate at a given point (a
+// serving loop with a fixed memory plan).  For them this file offers one
+// entry point that takes the caller's input and output buffers and keeps
+// all of its scratch -- the packed reference planes, the encoded query
+// table, the piece table and the per-query counts -- in a file-scope
+// device array of fixed size.  Every GPU that loads the library holds that
+// array (about 17 MB) until the process exits.
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ifa_internal.cuh"
+
+namespace ifa {
+void set_global_error(const std::string &msg);
+}
+
+using namespace ifa;
+
+namespace {
+
+constexpr uint64_t kNaMaxBases = 32ull << 20;  // reference bytes per call
+constexpr uint32_t kNaMaxQueries = 256;        // queries per call
+constexpr uint32_t kNaMaxPieces = 1u << 15;    // contigs per call
+constexpr uint32_t kNaWmax = 8;                // words per query entry (255 bp)
+constexpr uint64_t kNaWords = kNaMaxBases / 32 + 16;
+
+// Byte offsets of the parts inside the scratch array (256-aligned each).
+constexpr uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+constexpr uint64_t kOffWords = 0;
+constexpr uint64_t kOffQWords = align256(kOffWords + kNaWords * sizeof(uint4));
+constexpr uint64_t kOffQMeta = align256(kOffQWords + 2ull * kNaMaxQueries * kNaWmax * sizeof(uint4));
+constexpr uint64_t kOffPieces = align256(kOffQMeta + 2ull * kNaMaxQueries * sizeof(uint32_t));
+constexpr uint64_t kOffQCount = align256(kOffPieces + uint64_t(kNaMaxPieces) * sizeof(DevPiece));
+constexpr uint64_t kScratchBytes = align256(kOffQCount + kNaMaxQueries * sizeof(unsigned long long));
+
+// The scratch: one array, shared by every call on a device.
+static __device__ __align__(256) unsigned char g_na_scratch[kScratchBytes];
+
+// Device address of g_na_scratch per device (host code cannot use the
+// symbol itself: on the host it names a stand-in, not device memory).
+std::mutex g_na_mutex;
+unsigned char *g_na_addr[64] = {nullptr};
+
+ifa_status na_fail(ifa_status st, const std::string &msg) {
+    set_global_error(msg);
+    return st;
+}
+
+void na_encode(const uint8_t *q, uint32_t L, bool rc, uint32_t wmax, uint4 *out, uint32_t *meta) {
+    for (uint32_t j = 0; j < wmax; j++) out[j] = make_uint4(0, 0, 0, 0);
+    uint32_t nN = 0;
+    for (uint32_t i = 0; i < L; i++) {
+        const uint32_t c = rc ? q[L - 1 - i] : q[i];
+        const uint32_t w = i >> 5, bit = 1u << (i & 31);
+        if (is_base(c)) {
+            uint32_t code = base_code(c);
+            if (rc) code ^= 2u;
+            if (code >> 1) out[w].x |= bit;
+            if (code & 1u) out[w].y |= bit;
+            out[w].z |= bit;
+        } else {
+            nN++;
+        }
+        out[w].w |= bit;
+    }
+    *meta = L | (((L + 31) / 32) << 8) | (nN << 16);
+}
+
+}  // namespace
+
+extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *const *queries,
+                                             const uint32_t *qlens, uint32_t nq,
+                                             const uint8_t *ref_device, uint64_t len,
+                                             const ifa_piece *pieces, uint32_t n_pieces,
+                                             uint32_t max_subs, ifa_hit *hits_device,
+                                             uint64_t hit_capacity, uint64_t *counters_device,
+                                             uint64_t *per_query_counts_device, void *stream) {
+    // ---- arguments (host only; nothing is enqueued before they pass)
+    if (nq == 0 || nq > kNaMaxQueries)
+        return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: 1 to 256 queries per call");
+    if (!queries || !qlens) return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: queries/qlens is NULL");
+    for (uint32_t i = 0; i < nq; i++)
+        if (!queries[i] || qlens[i] == 0 || qlens[i] > IFA_MAX_QUERY_LEN)
+            return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: query length must be in 1..255");
+    if (len == 0 || len > kNaMaxBases)
+        return na_fail(IFA_ERR_INVALID_ARG,
+                       "ifa_scan_brute_noalloc: reference length must be in 1..33554432 bytes (32 MiB)");
+    if (n_pieces == 0 || n_pieces > kNaMaxPieces)
+        return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: 1 to 32768 contigs per call");
+    if (!ref_device || !pieces || !hits_device || !counters_device || hit_capacity == 0)
+        return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: NULL buffer or zero hit capacity");
+    uint64_t at = 0;
+    for (uint32_t i = 0; i < n_pieces; i++) {
+        const ifa_piece &p = pieces[i];
+        if (p.start != at || p.len == 0 || !p.last || p.offset_in_contig != 0 || p.len > 0xffffffffull)
+            return na_fail(IFA_ERR_INVALID_ARG,
+                           "ifa_scan_brute_noalloc: pieces must be whole contigs, contiguous from 0");
+        if (i > 0 && p.contig <= pieces[i - 1].contig)
+            return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: contig ids must increase");
+        at += p.len;
+    }
+    if (at != len) return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: pieces must cover the reference");
+
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return na_fail(IFA_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    if (device < 0 || device >= 64) return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: device ordinal");
+
+    // ---- set-up, once per device, with that device current
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_na_mutex);
+        if (!g_na_addr[device]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_na_scratch);
+            if (e != cudaSuccess)
+                return na_fail(IFA_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_na_addr[device] = static_cast<unsigned char *>(ptr);
+        }
+        base = g_na_addr[device];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint4 *words = reinterpret_cast<uint4 *>(base + kOffWords);
+    uint4 *qwords = reinterpret_cast<uint4 *>(base + kOffQWords);
+    uint32_t *qmeta = reinterpret_cast<uint32_t *>(base + kOffQMeta);
+    DevPiece *dpieces = reinterpret_cast<DevPiece *>(base + kOffPieces);
+    unsigned long long *qcount = reinterpret_cast<unsigned long long *>(base + kOffQCount);
+
+    // ---- host-side encoding of the queries and the piece table
+    uint32_t lmax = 0;
+    for (uint32_t i = 0; i < nq; i++) lmax = qlens[i] > lmax ? qlens[i] : lmax;
+    uint32_t wmax = 1;
+    while (wmax * 32 < lmax) wmax <<= 1;
+    const uint32_t ne = 2 * nq;
+    std::vector<uint4> hw(static_cast<size_t>(ne) * wmax);
+    std::vector<uint32_t> hm(ne);
+    for (uint32_t q = 0; q < nq; q++)
+        for (uint32_t t = 0; t < 2; t++)
+            na_encode(queries[q], qlens[q], t == 1, wmax, &hw[static_cast<size_t>(2 * q + t) * wmax], &hm[2 * q + t]);
+    std::vector<DevPiece> hp(n_pieces);
+    for (uint32_t i = 0; i < n_pieces; i++) {
+        hp[i].start = pieces[i].start;
+        hp[i].contig_off = 0;
+        hp[i].contig = pieces[i].contig;
+        hp[i].pad = 0;
+    }
+
+    // ---- enqueue: copies into the scratch, zeroing, pack, scan
+    auto ck = [&](cudaError_t r) {
+        if (e == cudaSuccess && r != cudaSuccess) e = r;
+    };
+    ck(cudaMemcpyAsync(qwords, hw.data(), hw.size() * sizeof(uint4), cudaMemcpyHostToDevice, st));
+    ck(cudaMemcpyAsync(qmeta, hm.data(), hm.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    ck(cudaMemcpyAsync(dpieces, hp.data(), hp.size() * sizeof(DevPiece), cudaMemcpyHostToDevice, st));
+    unsigned long long *qc = per_query_counts_device ? reinterpret_cast<unsigned long long *>(per_query_counts_device)
+                                                     : qcount;
+    ck(cudaMemsetAsync(qc, 0, nq * sizeof(unsigned long long), st));
+    ck(cudaMemsetAsync(counters_device, 0, 5 * sizeof(uint64_t), st));
+    const uint64_t nwords = (len + 31) / 32 + 16;
+    ck(launch_pack(nullptr, 0, 0, ref_device, len, words, nwords, st));
+    ck(launch_mark_pieces(dpieces, n_pieces, words, st));
+    Batch b;
+    b.words = words;
+    b.nbases = len;
+    b.halo = 0;
+    b.pieces = dpieces;
+    b.npieces = n_pieces;
+    QueryTable qt;
+    qt.words = qwords;
+    qt.meta = qmeta;
+    qt.ids = nullptr;
+    qt.n_entries = ne;
+    qt.wmax = wmax;
+    HitSink sink;
+    sink.ring = hits_device;
+    sink.head = reinterpret_cast<unsigned long long *>(counters_device);
+    sink.capacity = hit_capacity;
+    sink.overflow = reinterpret_cast<uint32_t *>(counters_device + 1);
+    sink.digest = reinterpret_cast<unsigned long long *>(counters_device + 2);
+    sink.qcount = qc;
+    sink.count_only = 0;
+    uint32_t cap = scan_brute_chunk_entries(wmax) & ~1u;
+    if (cap < 2) cap = 2;
+    for (uint32_t e0 = 0; e0 < ne && e == cudaSuccess; e0 += cap) {
+        const uint32_t e1 = e0 + cap < ne ? e0 + cap : ne;
+        uint32_t lo = 0xffffffffu, hi = 0;
+        for (uint32_t i = e0; i < e1; i++) {
+            const uint32_t L = hm[i] & 0xffu;
+            lo = L < lo ? L : lo;
+            hi = L > hi ? L : hi;
+        }
+        ck(launch_scan_brute(b, qt, e0, e1, max_subs, lo, hi, sink, st, nullptr));
+    }
+    if (e != cudaSuccess)
+        return na_fail(IFA_ERR_CUDA, std::string("ifa_scan_brute_noalloc: ") + cudaGetErrorString(e));
+    return IFA_OK;
+}
