@@ -243,7 +243,7 @@ def run_ours(args, rank, world):
         for a, b, pc in segs:
             P.ifa_push_segment(h, source[a:b], pc)
         if drain:
-            hits, _ = P.ifa_drain_hits(h)
+            hits, _ = P.ifa_drain_hits(h, copy=False)
             return hits.size
         return 0
 

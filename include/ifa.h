@@ -226,6 +226,54 @@ ifa_status ifa_minhits(int32_t device, const uint32_t *L, const uint32_t *subs, 
                        uint32_t n, uint32_t step, uint32_t mask_width, uint32_t max_clips,
                        uint32_t num, uint32_t den, uint32_t trials, uint64_t seed, uint32_t *out);
 
+/* ---- Many query sets against a device-resident reference ------------
+ *
+ * Batching and serving (the paper's mode choice by query count,
+ * Discussion, generalised): the reference is packed once into a store on
+ * the device, any number of query sets -- each with its own maxSubs and
+ * mode -- are registered, and one call scans all of them.  Hits, digest
+ * and per-query counts go to the handle's usual outputs (ifa_drain_hits,
+ * ifa_get_digest); query ids are global, a set's queries being the range
+ * [first_query, first_query + n). */
+
+/* Append len reference bytes to the store (packed on the device, 0.5 byte
+ * per base).  pieces: as for ifa_push_segment, in this chunk's coordinates;
+ * a contig may continue into the next append (its piece has last = 0).
+ * Every append except the last must hold a multiple of 32 bytes.
+ * Errors: INVALID_ARG (pieces, alignment, contig order), OOM, CUDA. */
+ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, const ifa_piece *pieces,
+                          uint32_t n_pieces, ifa_mem mem);
+
+/* Drop the store (frees its device memory). */
+ifa_status ifa_ref_reset(ifa_handle *h);
+
+/* Register n queries as one set with its own maxSubs (0..255 used as is;
+ * larger values act as 255) and mode (IFA_MODE_AUTO: the autotuner picks
+ * brute force or indexed).  *set_id and *first_query (may be NULL) receive
+ * the set's id and its first global query id.  BAD_STATE after
+ * ifa_push_segment (streaming and batching do not share a handle). */
+ifa_status ifa_set_add(ifa_handle *h, const uint8_t *const *seqs, const uint32_t *lens, uint32_t n,
+                       uint32_t max_subs, ifa_mode mode, uint32_t *set_id, uint32_t *first_query);
+
+typedef enum {
+    IFA_BATCH_PERSISTENT = 0,  /* one persistent launch over a device work queue, replayed from a CUDA graph */
+    IFA_BATCH_PER_SET = 1      /* each set scanned by its own launches, one set after the other */
+} ifa_batch_kind;
+
+typedef struct {
+    uint32_t mode;        /* IFA_MODE_BRUTE or IFA_MODE_INDEXED as run */
+    uint32_t queries;     /* queries in the set */
+    uint64_t hits;        /* hits of the set's queries in this run */
+    float done_ms;        /* device time from the run's start to the set's completion */
+    float pad;
+} ifa_set_result;
+
+/* Scan every registered set against the store; per_set (may be NULL)
+ * receives one ifa_set_result per set.  Results add to the handle's
+ * outputs (call ifa_reset_results between runs).  Waits for completion.
+ * Errors: BAD_STATE (empty store or no sets), OOM, CUDA. */
+ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per_set);
+
 /* Brute-force scan of one reference chunk that allocates no memory.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -85,6 +85,11 @@ _SYMBOLS = {
                               C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                               C.c_uint32, C.c_uint64, C.c_void_p]),
     "ifa_last_error": (C.c_char_p, [C.c_void_p]),
+    "ifa_ref_append": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32, C.c_int]),
+    "ifa_ref_reset": (C.c_int, [C.c_void_p]),
+    "ifa_set_add": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.c_uint32,
+                              C.c_uint32, C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+    "ifa_batch_run": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "ifa_scan_brute_noalloc": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
                                          C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32,
                                          C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p,
@@ -140,6 +145,8 @@ def ifa_create(cfg: Optional[ifa_config] = None, **overrides) -> C.c_void_p:
 
 
 def ifa_destroy(h) -> None:
+    if h is not None and h.value is not None:
+        _PINNED.pop(h.value, None)
     lib().ifa_destroy(h)
 
 
@@ -202,21 +209,55 @@ def ifa_flush(h) -> int:
     return _check(lib().ifa_flush(h), h, allow=(IFA_OK, IFA_ERR_HIT_OVERFLOW))
 
 
-def ifa_drain_hits(h, cap: Optional[int] = None) -> Tuple[np.ndarray, bool]:
-    """Drain buffered hits; returns (hits, overflowed)."""
+_PINNED = {}
+
+
+def _pinned_hits(h, n: int):
+    """A page-locked hit array of at least n entries kept per handle (the
+    device-to-host copy of hits runs at full PCIe speed only into pinned
+    memory).  None when torch is unavailable."""
+    try:
+        import torch
+    except ImportError:
+        return None
+    key = h.value
+    buf = _PINNED.get(key)
+    if buf is None or buf[1].size < n:
+        t = torch.empty(max(n, 1) * HIT_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+        buf = (t, t.numpy().view(HIT_DTYPE))
+        _PINNED[key] = buf
+    return buf[1]
+
+
+def ifa_drain_hits(h, cap: Optional[int] = None, copy: bool = True) -> Tuple[np.ndarray, bool]:
+    """Drain buffered hits; returns (hits, overflowed).  The hits are copied
+    from the device into a page-locked buffer owned by the handle; with
+    copy=False the returned array is a view of that buffer, valid until the
+    next drain on the handle."""
+    d = ifa_digest()
+    st = lib().ifa_get_digest(h, C.byref(d), None)
+    _check(st, h)
+    want = int(d.count) if cap is None else int(cap)
+    pinned = _pinned_hits(h, want) if want else None
     parts = []
     overflowed = False
-    chunk = cap or (1 << 22)
     while True:
-        out = np.zeros(chunk, HIT_DTYPE)
+        if pinned is not None and want:
+            out, chunk = pinned, pinned.size
+        else:
+            chunk = cap or (1 << 22)
+            out = np.zeros(chunk, HIT_DTYPE)
         n = C.c_uint64()
         more = C.c_int()
         st = _check(lib().ifa_drain_hits(h, out.ctypes.data, chunk, C.byref(n), C.byref(more)), h,
                     allow=(IFA_OK, IFA_ERR_HIT_OVERFLOW))
         overflowed |= st == IFA_ERR_HIT_OVERFLOW
-        parts.append(out[:n.value])
+        got = out[:n.value]
+        parts.append(got.copy() if (copy or more.value) and out is pinned else got)
         if cap is not None or not more.value:
             break
+    if len(parts) == 1:
+        return parts[0], overflowed
     return (np.concatenate(parts) if parts else np.zeros(0, HIT_DTYPE)), overflowed
 
 
@@ -254,6 +295,51 @@ def ifa_minhits(device: int, L, subs, k, step: int = 1, mask_width: int = 0, max
     _check(lib().ifa_minhits(device, L.ctypes.data, subs.ctypes.data, k.ctypes.data, L.size, step,
                              mask_width, max_clips, num, den, trials, seed, out.ctypes.data))
     return out
+
+
+IFA_BATCH_PERSISTENT, IFA_BATCH_PER_SET = 0, 1
+SET_RESULT_DTYPE = np.dtype([("mode", "<u4"), ("queries", "<u4"), ("hits", "<u8"),
+                             ("done_ms", "<f4"), ("pad", "<f4")])
+
+
+def ifa_ref_append(h, data, pieces, mem: Optional[int] = None) -> None:
+    """Append to the device-resident reference store (same data/pieces forms
+    as ifa_push_segment)."""
+    pa = _as_pieces(pieces)
+    if isinstance(data, tuple):
+        ptr, ln, mem = data
+    elif isinstance(data, np.ndarray):
+        ptr, ln = data.ctypes.data, data.size
+        mem = IFA_MEM_HOST if mem is None else mem
+    else:
+        ptr, ln = data.data_ptr(), data.numel()
+        if mem is None:
+            mem = IFA_MEM_DEVICE if data.is_cuda else (
+                IFA_MEM_HOST_PINNED if data.is_pinned() else IFA_MEM_HOST)
+    _check(lib().ifa_ref_append(h, C.c_void_p(ptr), ln, pa.ctypes.data, pa.size, mem), h)
+
+
+def ifa_ref_reset(h) -> None:
+    _check(lib().ifa_ref_reset(h), h)
+
+
+def ifa_set_add(h, queries: Sequence[bytes], max_subs: int, mode: int = IFA_MODE_AUTO) -> Tuple[int, int]:
+    """Register a query set; returns (set_id, first_query)."""
+    n = len(queries)
+    bufs = [C.create_string_buffer(bytes(q), len(q)) for q in queries]
+    ptrs = (C.c_void_p * max(1, n))(*[C.cast(b, C.c_void_p) for b in bufs])
+    lens = (C.c_uint32 * max(1, n))(*[len(q) for q in queries])
+    sid = C.c_uint32()
+    first = C.c_uint32()
+    _check(lib().ifa_set_add(h, ptrs, lens, n, int(max_subs), int(mode), C.byref(sid), C.byref(first)), h)
+    return sid.value, first.value
+
+
+def ifa_batch_run(h, kind: int, n_sets: int) -> np.ndarray:
+    """Scan all sets against the store; returns one SET_RESULT_DTYPE row per set."""
+    out = np.zeros(max(1, n_sets), SET_RESULT_DTYPE)
+    _check(lib().ifa_batch_run(h, int(kind), out.ctypes.data), h)
+    return out[:n_sets]
 
 
 def ifa_scan_brute_noalloc(device: int, queries: Sequence[bytes], ref_ptr: int, length: int,

@@ -1,0 +1,790 @@
+// batch.cu -- many query sets against a device-resident reference.
+//
+// The paper picks brute force or indexed mode per run by query count
+// (Discussion; crossover 100-200 queries on RefSeq) and streams the
+// reference once per run.  Here the reference is packed once into a store
+// in HBM, query sets of uneven sizes -- each with its own maxSubs -- are
+// registered, and one call scans all of them:
+//
+//  * the autotuner decides brute force or indexed for every IFA_MODE_AUTO
+//    set from rates it measures on a slice of the store (brute-force
+//    entry x base evaluations per second, seed-scan positions per second,
+//    verified candidates per second), comparing the set's brute-force cost
+//    with the cost of scanning it alone in indexed mode -- the per-set
+//    crossover -- and sizes the work tiles;
+//  * brute-force sets share one compact entry table cut into shared-memory
+//    chunks; indexed sets share one set of merged k-mer tables (a window's
+//    threshold and maxSubs are per query, carried in the entry's meta word);
+//  * IFA_BATCH_PERSISTENT runs everything in one persistent kernel whose
+//    CTAs pull (chunk, tile) and (seed, tile) items from a device work
+//    queue; the launch and its queue reset are captured once in a CUDA graph
+//    and replayed;
+//  * IFA_BATCH_PER_SET is the baseline: every set is scanned by its own
+//    launches over the whole store (its own tables in indexed mode), one set
+//    after another.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "handle.cuh"
+#include "scan_brute.cuh"
+#include "seed_scan.cuh"
+
+using namespace ifa;
+
+namespace {
+
+constexpr int kBThreads = 256;
+constexpr int kBWarps = kBThreads / kWarp;
+constexpr uint64_t kStorePad = 16;  // zeroed words after the last packed word
+
+ifa_status bfail(ifa_handle *h, ifa_status st, const std::string &msg) {
+    h->err = msg;
+    return st;
+}
+
+#define BCK(h, call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return bfail((h), e_ == cudaErrorMemoryAllocation ? IFA_ERR_OOM : IFA_ERR_CUDA, \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+// One persistent launch: CTAs pull items from w.queue until it runs dry.
+// Items [0, n_items - n_brute_items) are seed tiles, the rest brute-force
+// (chunk, tile) items in chunk-major order, so a CTA reloads its shared
+// query chunk rarely.
+template <int WMAX>
+__global__ void __launch_bounds__(kBThreads)
+k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
+    using namespace brute;
+    constexpr int NW = Stage<WMAX>::kWords;
+    extern __shared__ uint4 smem4[];
+    __shared__ ifa_hit wbuf[kBWarps][32];
+    __shared__ uint4 stage[kBWarps][2][NW];
+    __shared__ uint32_t s_nF, s_nM, s_item;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = threadIdx.x >> 5;
+    WarpHits wh;
+    wh.init(wbuf[warp]);
+    uint32_t mul[kWin];
+    lane_multipliers(mul);
+    unsigned long long ncand = 0;
+    int loaded = -1;
+    Smem m{};
+    uint32_t nent = 0, e0 = 0, lmin = 0, lmax = 0;
+    const uint64_t nbblk = (b.nbases + 32 * kWin - 1) / (32 * kWin);
+    const uint64_t nsblk = (b.nbases + 31) >> 5;
+    const uint32_t n_seed = w.n_items - w.n_brute_items;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(w.queue, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= w.n_items) break;
+        if (item < n_seed) {
+            const uint64_t lo = static_cast<uint64_t>(item) * w.tile_sblocks;
+            const uint64_t hi = lo + w.tile_sblocks < nsblk ? lo + w.tile_sblocks : nsblk;
+            seed::seed_blocks<WMAX>(b, ft, w.tabs, w.emh, w.step, kSPerEntry, sink, wh, lo + warp, hi,
+                                    kBWarps, lane, ncand);
+        } else {
+            const uint32_t bi = item - n_seed;
+            const uint32_t chunk = bi / w.n_btiles, tile = bi % w.n_btiles;
+            if (static_cast<int>(chunk) != loaded) {
+                if (loaded >= 0) {
+                    flush_counts(bt, m, nent, e0, sink);
+                    __syncthreads();
+                }
+                e0 = w.chunk_e0[chunk];
+                const uint32_t e1 = w.chunk_e1[chunk];
+                lmin = w.chunk_lmin[chunk];
+                lmax = w.chunk_lmax[chunk];
+                m = load_chunk<WMAX>(bt, e0, e1, kSPerEntry, smem4, &s_nF, &s_nM);
+                nent = e1 - e0;
+                loaded = static_cast<int>(chunk);
+            }
+            const uint64_t lo = static_cast<uint64_t>(tile) * w.tile_bblocks;
+            const uint64_t hi = lo + w.tile_bblocks < nbblk ? lo + w.tile_bblocks : nbblk;
+            scan_blocks<WMAX>(b, bt, m, nent, s_nF, s_nM, e0, kSPerEntry, lmin, lmax, sink, wh, stage[warp], mul,
+                              lo + warp, hi, kBWarps, lane);
+        }
+        __syncthreads();
+    }
+    if (loaded >= 0) flush_counts(bt, m, nent, e0, sink);
+    wh.finish(sink, lane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
+    if (lane == 0 && ncand) atomicAdd(w.candidates, ncand);
+}
+
+template <int WMAX>
+cudaError_t launch_batch_t(const Batch &b, const BatchWork &w, const QueryTable &bt, const QueryTable &ft,
+                           const HitSink &sink, int grid, size_t smem, cudaStream_t st) {
+    k_batch<WMAX><<<grid, kBThreads, smem, st>>>(b, w, bt, ft, sink);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(uint32_t wmax, const Batch &b, const BatchWork &w, const QueryTable &bt,
+                         const QueryTable &ft, const HitSink &sink, int grid, size_t smem, cudaStream_t st) {
+    switch (wmax) {
+    case 1: return launch_batch_t<1>(b, w, bt, ft, sink, grid, smem, st);
+    case 2: return launch_batch_t<2>(b, w, bt, ft, sink, grid, smem, st);
+    case 4: return launch_batch_t<4>(b, w, bt, ft, sink, grid, smem, st);
+    case 8: return launch_batch_t<8>(b, w, bt, ft, sink, grid, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int batch_grid(uint32_t wmax) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = brute::kScanSmemBudget;
+    cudaError_t e = cudaSuccess;
+    switch (wmax) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<1>, kBThreads, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<2>, kBThreads, smem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<4>, kBThreads, smem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<8>, kBThreads, smem); break;
+    }
+    if (e != cudaSuccess || per < 1) per = 1;
+    return sms * per;
+}
+
+Batch store_batch(const BatchState &B) {
+    Batch b;
+    b.words = B.d_words;
+    b.nbases = B.nbases;
+    b.halo = 0;
+    b.pieces = B.d_pieces;
+    b.npieces = B.d_pieces_n;
+    return b;
+}
+
+HitSink handle_sink(const ifa_handle *h) {
+    HitSink s;
+    s.ring = h->d_ring;
+    s.head = h->d_head;
+    s.capacity = h->cfg.count_only ? 0 : h->cfg.hit_capacity;
+    s.digest = h->d_digest;
+    s.qcount = h->d_qcount;
+    s.overflow = h->d_overflow;
+    s.count_only = h->cfg.count_only ? 1 : 0;
+    return s;
+}
+
+ifa_status sync_pieces(ifa_handle *h) {
+    BatchState &B = h->batch;
+    if (!B.pieces_dirty) return IFA_OK;
+    cudaFree(B.d_pieces);
+    B.d_pieces = nullptr;
+    BCK(h, cudaMalloc(&B.d_pieces, std::max<size_t>(1, B.pieces.size()) * sizeof(DevPiece)));
+    if (!B.pieces.empty())
+        BCK(h, cudaMemcpy(B.d_pieces, B.pieces.data(), B.pieces.size() * sizeof(DevPiece), cudaMemcpyHostToDevice));
+    B.d_pieces_n = static_cast<uint32_t>(B.pieces.size());
+    B.pieces_dirty = false;
+    return IFA_OK;
+}
+
+void free_plan(BatchState &B) {
+    for (void *p : B.allocs) cudaFree(p);
+    B.allocs.clear();
+    B.merged.release();
+    for (auto &p : B.per_set)
+        if (p) p->release();
+    B.per_set.clear();
+    if (B.graph) cudaGraphExecDestroy(B.graph);
+    B.graph = nullptr;
+    B.graph_stream = nullptr;
+    B.plan_valid = false;
+}
+
+template <typename T>
+T *plan_alloc(ifa_handle *h, size_t n, cudaError_t &e) {
+    void *p = nullptr;
+    cudaError_t r = cudaMalloc(&p, std::max<size_t>(1, n) * sizeof(T));
+    if (r != cudaSuccess) {
+        if (e == cudaSuccess) e = r;
+        return nullptr;
+    }
+    h->batch.allocs.push_back(p);
+    return static_cast<T *>(p);
+}
+
+// Expected random seed hits per reference base of one query entry: its
+// k-mer count over 4^k (both strands are separate entries).
+double seed_rate(uint32_t L, uint32_t k, uint32_t step) {
+    if (k == 0 || k > L) return 0;
+    return static_cast<double>((L - k) / step + 1) / std::pow(4.0, static_cast<double>(k));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan
+
+namespace {
+
+// Build the merged plan: modes of AUTO sets (autotuner), the compact brute
+// table with its chunks, merged and per-set k-mer tables, work descriptor.
+ifa_status build_plan(ifa_handle *h) {
+    BatchState &B = h->batch;
+    if (B.plan_valid) return IFA_OK;
+    free_plan(B);
+    ifa_status st = upload_queries(h);
+    if (st != IFA_OK) return st;
+    st = sync_pieces(h);
+    if (st != IFA_OK) return st;
+    const uint32_t nq = static_cast<uint32_t>(h->qs.size());
+    const uint32_t wmax = h->wmax;
+    B.wmax = wmax;
+    std::vector<uint32_t> svec(nq, 0);
+    for (uint32_t q = 0; q < nq; q++) svec[q] = q < h->qs_s.size() ? h->qs_s[q] : 0u;
+
+    // indexed plan over every set that may run indexed (AUTO or INDEXED)
+    std::vector<uint8_t> cand_in(nq, 0);
+    for (const QuerySet &S : B.sets)
+        if (S.mode != IFA_MODE_BRUTE)
+            for (uint32_t q = S.first; q < S.first + S.n; q++) cand_in[q] = 1;
+    IndexedState plan_all;
+    if (std::any_of(cand_in.begin(), cand_in.end(), [](uint8_t x) { return x != 0; })) {
+        st = indexed_plan_q(plan_all, h->qs, svec, cand_in, h->cfg, h->stream, h->err);
+        if (st != IFA_OK) return st;
+    }
+
+    // autotuner: brute force or indexed per AUTO set, from measured rates
+    const double bases = static_cast<double>(B.nbases);
+    for (QuerySet &S : B.sets) {
+        if (S.mode == IFA_MODE_BRUTE) { S.chosen = IFA_MODE_BRUTE; continue; }
+        if (S.mode == IFA_MODE_INDEXED) { S.chosen = IFA_MODE_INDEXED; continue; }
+        double brute_s = 2.0 * S.n * bases / std::max(1.0, B.brute_entry_bases_per_s);
+        double cand = 0;
+        std::vector<uint32_t> ks;
+        bool any_seeded = false;
+        for (uint32_t q = S.first; q < S.first + S.n; q++) {
+            if (plan_all.plan_exhaustive.empty() || plan_all.plan_exhaustive[q]) {
+                cand += 0;
+                continue;
+            }
+            any_seeded = true;
+            cand += 2.0 * bases * seed_rate(static_cast<uint32_t>(h->qs[q].size()), plan_all.plan_k[q], h->cfg.kmer_step);
+            ks.push_back(plan_all.plan_k[q]);
+        }
+        std::sort(ks.begin(), ks.end());
+        ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+        double exh = 0;  // exhaustive queries of an indexed set are scanned by brute force anyway
+        for (uint32_t q = S.first; q < S.first + S.n; q++)
+            if (plan_all.plan_exhaustive.empty() || plan_all.plan_exhaustive[q]) exh += 2.0 * bases;
+        exh /= std::max(1.0, B.brute_entry_bases_per_s);
+        const double idx_s = bases * ks.size() / std::max(1.0, B.seed_pos_per_s) +
+                             cand / std::max(1.0, B.cand_per_s) + exh;
+        S.chosen = (!any_seeded || brute_s <= idx_s) ? IFA_MODE_BRUTE : IFA_MODE_INDEXED;
+    }
+
+    // queries that run indexed (seeded ones go to the merged tables; their
+    // exhaustive ones to the compact brute table)
+    std::vector<uint8_t> idx_in(nq, 0);
+    for (const QuerySet &S : B.sets)
+        if (S.chosen == IFA_MODE_INDEXED)
+            for (uint32_t q = S.first; q < S.first + S.n; q++) idx_in[q] = 1;
+
+    // compact brute table, set by set so each set's entries are contiguous
+    std::vector<uint32_t> ids;
+    B.set_bchunk_lo.assign(B.sets.size(), 0);
+    B.set_bchunk_hi.assign(B.sets.size(), 0);
+    B.bchunk_e0.clear();
+    B.bchunk_e1.clear();
+    B.bchunk_lmin.clear();
+    B.bchunk_lmax.clear();
+    uint32_t cap = brute::kScanSmemBudget / brute::entry_smem(static_cast<int>(wmax));
+    cap = std::min<uint32_t>(cap, 65535) & ~1u;
+    if (cap < 2) cap = 2;
+    bool any_idx = false;
+    for (size_t si = 0; si < B.sets.size(); si++) {
+        const QuerySet &S = B.sets[si];
+        const uint32_t start = static_cast<uint32_t>(ids.size());
+        for (uint32_t q = S.first; q < S.first + S.n; q++) {
+            const bool brute = S.chosen == IFA_MODE_BRUTE || plan_all.plan_exhaustive[q];
+            if (S.chosen == IFA_MODE_INDEXED && !plan_all.plan_exhaustive[q]) any_idx = true;
+            if (!brute) continue;
+            ids.push_back(2 * q);
+            ids.push_back(2 * q + 1);
+        }
+        const uint32_t end = static_cast<uint32_t>(ids.size());
+        B.set_bchunk_lo[si] = static_cast<uint32_t>(B.bchunk_e0.size());
+        for (uint32_t a = start; a < end; a += cap) {
+            const uint32_t z = std::min(end, a + cap);
+            uint32_t lo = 0xffffffffu, hi = 0;
+            for (uint32_t i = a; i < z; i++) {
+                const uint32_t L = meta_L(h->qmeta_host[ids[i]]);
+                lo = std::min(lo, L);
+                hi = std::max(hi, L);
+            }
+            B.bchunk_e0.push_back(a);
+            B.bchunk_e1.push_back(z);
+            B.bchunk_lmin.push_back(lo);
+            B.bchunk_lmax.push_back(hi);
+        }
+        B.set_bchunk_hi[si] = static_cast<uint32_t>(B.bchunk_e0.size());
+    }
+    B.b_entries = static_cast<uint32_t>(ids.size());
+    cudaError_t e = cudaSuccess;
+    const uint32_t nbe = std::max<uint32_t>(1, B.b_entries);
+    std::vector<uint4> bw(static_cast<size_t>(nbe) * wmax, make_uint4(0, 0, 0, 0));
+    std::vector<uint32_t> bm(nbe, 0);
+    for (uint32_t i = 0; i < B.b_entries; i++) {
+        bm[i] = h->qmeta_host[ids[i]];
+        for (uint32_t j = 0; j < wmax; j++) bw[static_cast<size_t>(i) * wmax + j] = h->qwords_host[static_cast<size_t>(ids[i]) * wmax + j];
+    }
+    uint4 *d_bw = plan_alloc<uint4>(h, bw.size(), e);
+    uint32_t *d_bm = plan_alloc<uint32_t>(h, nbe, e);
+    uint32_t *d_bids = plan_alloc<uint32_t>(h, nbe, e);
+    const size_t nch = std::max<size_t>(1, B.bchunk_e0.size());
+    uint32_t *d_c0 = plan_alloc<uint32_t>(h, nch, e), *d_c1 = plan_alloc<uint32_t>(h, nch, e);
+    uint32_t *d_cl = plan_alloc<uint32_t>(h, nch, e), *d_ch = plan_alloc<uint32_t>(h, nch, e);
+    if (e == cudaSuccess) {
+        e = cudaMemcpy(d_bw, bw.data(), bw.size() * sizeof(uint4), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_bm, bm.data(), nbe * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !ids.empty()) e = cudaMemcpy(d_bids, ids.data(), ids.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !B.bchunk_e0.empty()) {
+            const size_t nb = B.bchunk_e0.size() * sizeof(uint32_t);
+            e = cudaMemcpy(d_c0, B.bchunk_e0.data(), nb, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(d_c1, B.bchunk_e1.data(), nb, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(d_cl, B.bchunk_lmin.data(), nb, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(d_ch, B.bchunk_lmax.data(), nb, cudaMemcpyHostToDevice);
+        }
+    }
+    if (e != cudaSuccess) return bfail(h, IFA_ERR_CUDA, std::string("batch plan: ") + cudaGetErrorString(e));
+
+    // merged tables of the indexed sets (seeded queries only)
+    if (any_idx) {
+        std::vector<uint8_t> seeded(nq, 0);
+        for (uint32_t q = 0; q < nq; q++) seeded[q] = idx_in[q] && !plan_all.plan_exhaustive[q];
+        st = indexed_plan_q(B.merged, h->qs, svec, seeded, h->cfg, h->stream, h->err);
+        if (st != IFA_OK) return st;
+        st = indexed_tables(B.merged, h->qs, h->qmeta_host, h->qwords_host, wmax, h->cfg, h->err);
+        if (st != IFA_OK) return st;
+    }
+    // per-set tables for the per-set baseline
+    B.per_set.clear();
+    for (const QuerySet &S : B.sets) {
+        B.per_set.emplace_back(new IndexedState());
+        if (S.chosen != IFA_MODE_INDEXED) continue;
+        std::vector<uint8_t> mine(nq, 0);
+        for (uint32_t q = S.first; q < S.first + S.n; q++) mine[q] = !plan_all.plan_exhaustive[q];
+        if (std::none_of(mine.begin(), mine.end(), [](uint8_t x) { return x != 0; })) continue;
+        st = indexed_plan_q(*B.per_set.back(), h->qs, svec, mine, h->cfg, h->stream, h->err);
+        if (st != IFA_OK) return st;
+        st = indexed_tables(*B.per_set.back(), h->qs, h->qmeta_host, h->qwords_host, wmax, h->cfg, h->err);
+        if (st != IFA_OK) return st;
+        cudaMalloc(&B.per_set.back()->d_candidates, sizeof(unsigned long long));
+    }
+
+    // work descriptor and tiles
+    if (!B.d_queue) BCK(h, cudaMalloc(&B.d_queue, sizeof(unsigned int)));
+    if (!B.d_cand) BCK(h, cudaMalloc(&B.d_cand, sizeof(unsigned long long)));
+    B.grid = batch_grid(wmax);
+    BatchWork &W = B.work;
+    W = BatchWork{};
+    W.bwords = d_bw;
+    W.bmeta = d_bm;
+    W.bids = d_bids;
+    W.chunk_e0 = d_c0;
+    W.chunk_e1 = d_c1;
+    W.chunk_lmin = d_cl;
+    W.chunk_lmax = d_ch;
+    W.nchunks = static_cast<uint32_t>(B.bchunk_e0.size());
+    W.tabs = B.merged.tables_valid ? B.merged.targ : KTablesArg{};
+    W.emh = B.merged.d_entry_minhits;
+    W.step = h->cfg.kmer_step;
+    W.qwords = h->d_qwords;
+    W.qmeta = h->d_qmeta;
+    const uint64_t nbblk = (B.nbases + 32 * brute::kWin - 1) / (32 * brute::kWin);
+    const uint64_t nsblk = (B.nbases + 31) / 32;
+    // tiles: about 16 items per CTA slot over all chunks, at least 32 blocks per tile
+    const uint64_t want_b = static_cast<uint64_t>(16) * B.grid;
+    const uint64_t tiles_per_chunk = W.nchunks ? std::max<uint64_t>(1, want_b / W.nchunks) : 1;
+    W.tile_bblocks = std::max<uint64_t>(32, (nbblk + tiles_per_chunk - 1) / tiles_per_chunk);
+    W.n_btiles = static_cast<uint32_t>((nbblk + W.tile_bblocks - 1) / W.tile_bblocks);
+    W.tile_sblocks = std::max<uint64_t>(64, (nsblk + 8 * B.grid - 1) / (8 * B.grid));
+    W.n_stiles = W.tabs.n ? static_cast<uint32_t>((nsblk + W.tile_sblocks - 1) / W.tile_sblocks) : 0;
+    W.n_brute_items = W.nchunks * W.n_btiles;
+    W.n_items = W.n_brute_items + W.n_stiles;
+    W.queue = B.d_queue;
+    W.candidates = B.d_cand;
+    B.plan_valid = true;
+    return IFA_OK;
+}
+
+// Measure the autotuner's three rates on a slice of the store (once per
+// handle), with a count-only sink so no result is touched.
+ifa_status calibrate(ifa_handle *h) {
+    BatchState &B = h->batch;
+    if (B.brute_entry_bases_per_s > 0) return IFA_OK;
+    ifa_status st = upload_queries(h);
+    if (st != IFA_OK) return st;
+    st = sync_pieces(h);
+    if (st != IFA_OK) return st;
+    const uint32_t nq = static_cast<uint32_t>(h->qs.size());
+    Batch b = store_batch(B);
+    b.nbases = std::min<uint64_t>(B.nbases, 32ull << 20);
+    unsigned long long *scratch = nullptr;
+    BCK(h, cudaMalloc(&scratch, (4 + nq) * sizeof(unsigned long long)));
+    HitSink sink;
+    sink.ring = nullptr;
+    sink.head = scratch;
+    sink.capacity = 0;
+    sink.digest = scratch + 1;
+    sink.overflow = reinterpret_cast<uint32_t *>(scratch + 3);
+    sink.qcount = scratch + 4;
+    sink.count_only = 1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    QueryTable qt;
+    qt.words = h->d_qwords;
+    qt.meta = h->d_qmeta;
+    qt.ids = nullptr;
+    qt.n_entries = 2 * nq;
+    qt.wmax = h->wmax;
+    float ms = 0;
+    // brute force: up to 256 entries (one shared-memory chunk), per-entry thresholds
+    const uint32_t ne = std::min<uint32_t>(std::min<uint32_t>(2 * nq, 256), scan_brute_chunk_entries(h->wmax) & ~1u);
+    uint32_t lo = 255, hi = 0;
+    for (uint32_t i = 0; i < ne; i++) {
+        lo = std::min(lo, meta_L(h->qmeta_host[i]));
+        hi = std::max(hi, meta_L(h->qmeta_host[i]));
+    }
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
+        cudaEventRecord(e0, h->stream);
+        e = launch_scan_brute(b, qt, 0, ne, kSPerEntry, lo, hi, sink, h->stream, nullptr);
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    B.brute_entry_bases_per_s = ne * static_cast<double>(b.nbases) / std::max(1e-6, ms * 1e-3);
+    // seed scan with a one-query table: positions per second per table
+    IndexedState one;
+    std::vector<uint8_t> in(nq, 0);
+    std::vector<uint32_t> svec(nq, 0);
+    for (uint32_t q = 0; q < nq; q++) svec[q] = q < h->qs_s.size() ? h->qs_s[q] : 0u;
+    uint32_t pick = 0;
+    while (pick < nq && h->qs[pick].size() < 8) pick++;
+    double pos_rate = 1e11, cand_rate = 1e10;
+    if (pick < nq && e == cudaSuccess) {
+        in[pick] = 1;
+        st = indexed_plan_q(one, h->qs, svec, in, h->cfg, h->stream, h->err);
+        if (st == IFA_OK) st = indexed_tables(one, h->qs, h->qmeta_host, h->qwords_host, h->wmax, h->cfg, h->err);
+        if (st == IFA_OK && one.targ.n) {
+            cudaMalloc(&one.d_candidates, sizeof(unsigned long long));
+            cudaMemset(one.d_candidates, 0, sizeof(unsigned long long));
+            for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
+                cudaEventRecord(e0, h->stream);
+                e = launch_seed_scan(b, qt, one.targ, one.d_entry_minhits, h->cfg.kmer_step, kSPerEntry, sink,
+                                     one.d_candidates, h->stream);
+                cudaEventRecord(e1, h->stream);
+                cudaEventSynchronize(e1);
+            }
+            cudaEventElapsedTime(&ms, e0, e1);
+            pos_rate = b.nbases / std::max(1e-6, ms * 1e-3);
+            // candidates: a dense table (every query of the handle at k = 8)
+            IndexedState dense;
+            std::vector<uint8_t> all(nq, 0);
+            for (uint32_t q = 0; q < nq && q < 4096; q++) all[q] = h->qs[q].size() >= 8;
+            ifa_config c8 = h->cfg;
+            c8.k_list[0] = 8;
+            c8.n_k = 1;
+            c8.minhits_num = 1;
+            c8.minhits_den = 1;  // deterministic bound: no Monte Carlo
+            st = indexed_plan_q(dense, h->qs, svec, all, c8, h->stream, h->err);
+            if (st == IFA_OK) st = indexed_tables(dense, h->qs, h->qmeta_host, h->qwords_host, h->wmax, c8, h->err);
+            if (st == IFA_OK && dense.targ.n) {
+                cudaMalloc(&dense.d_candidates, sizeof(unsigned long long));
+                cudaMemset(dense.d_candidates, 0, sizeof(unsigned long long));
+                cudaEventRecord(e0, h->stream);
+                e = launch_seed_scan(b, qt, dense.targ, dense.d_entry_minhits, 1, kSPerEntry, sink,
+                                     dense.d_candidates, h->stream);
+                cudaEventRecord(e1, h->stream);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                unsigned long long nc = 0;
+                cudaMemcpy(&nc, dense.d_candidates, sizeof(nc), cudaMemcpyDeviceToHost);
+                const double t = ms * 1e-3 - b.nbases / pos_rate;
+                if (nc > 1000 && t > 0) cand_rate = nc / t;
+            }
+            dense.release();
+        }
+        one.release();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    if (st != IFA_OK) return st;
+    if (e != cudaSuccess) return bfail(h, IFA_ERR_CUDA, std::string("calibration: ") + cudaGetErrorString(e));
+    B.seed_pos_per_s = pos_rate;
+    B.cand_per_s = cand_rate;
+    return IFA_OK;
+}
+
+}  // namespace
+
+namespace ifa {
+// Free the store and the plan of a handle (at ifa_destroy).
+void batch_release(ifa_handle *h) {
+    BatchState &B = h->batch;
+    free_plan(B);
+    cudaFree(B.d_words);
+    cudaFree(B.d_pieces);
+    cudaFree(B.d_queue);
+    cudaFree(B.d_cand);
+    B.d_words = nullptr;
+    B.d_pieces = nullptr;
+    B.d_queue = nullptr;
+    B.d_cand = nullptr;
+}
+}  // namespace ifa
+
+// ------------------------------------------------------------------ ABI
+
+extern "C" {
+
+ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, const ifa_piece *pieces,
+                          uint32_t n, ifa_mem mem) {
+    if (!h) return IFA_ERR_INVALID_ARG;
+    if (len == 0 && n == 0) return IFA_OK;
+    if (!ascii || !pieces || len == 0 || n == 0)
+        return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: bytes and at least one piece needed");
+    if (mem != IFA_MEM_HOST && mem != IFA_MEM_HOST_PINNED && mem != IFA_MEM_DEVICE)
+        return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: unknown memory kind");
+    BatchState &B = h->batch;
+    if (B.nbases % 32 != 0)
+        return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: the previous append was not a multiple of 32 bases");
+    uint64_t at = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        const ifa_piece &p = pieces[i];
+        if (p.start != at || p.len == 0)
+            return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: pieces must be contiguous, non-empty, from 0");
+        at += p.len;
+        if (!p.last && i + 1 != n) return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: only the last piece may continue");
+        if (i == 0 && B.open) {
+            if (p.contig != B.open_contig || p.offset_in_contig != B.open_next)
+                return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: must continue the open contig");
+        } else {
+            if (p.offset_in_contig != 0) return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: a new contig starts at 0");
+            const bool have_prev = i > 0 || B.any_contig;
+            const uint32_t prev = i > 0 ? pieces[i - 1].contig : B.last_contig;
+            if (have_prev && p.contig <= prev) return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: contig ids must increase");
+        }
+        if (p.offset_in_contig + p.len > 0xffffffffull)
+            return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: contig longer than 2^32 - 1 bases");
+    }
+    if (at != len) return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: pieces must cover the bytes");
+    BCK(h, cudaSetDevice(h->dev));
+    BCK(h, cudaStreamSynchronize(h->stream));
+    // grow the store (geometric), keeping the packed words
+    const uint64_t need = (B.nbases + len + 31) / 32 + kStorePad;
+    if (need > B.words_cap) {
+        const uint64_t cap = std::max<uint64_t>(need, B.words_cap + B.words_cap / 2);
+        uint4 *nw = nullptr;
+        BCK(h, cudaMalloc(&nw, cap * sizeof(uint4)));
+        if (B.d_words) {
+            cudaError_t e = cudaMemcpy(nw, B.d_words, (B.nbases / 32) * sizeof(uint4), cudaMemcpyDeviceToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(nw);
+                return bfail(h, IFA_ERR_CUDA, std::string("ifa_ref_append: ") + cudaGetErrorString(e));
+            }
+            cudaFree(B.d_words);
+        }
+        B.d_words = nw;
+        B.words_cap = cap;
+    }
+    // copy (via the handle's segment buffer) and pack, one segment at a time
+    const uint64_t seg = h->cfg.segment_bytes & ~uint64_t(31);
+    for (uint64_t off = 0; off < len; off += seg) {
+        const uint64_t c = std::min<uint64_t>(seg, len - off);
+        const uint8_t *src = ascii + off;
+        if (mem != IFA_MEM_DEVICE) {
+            BCK(h, cudaMemcpyAsync(h->d_seg[0], src, c, cudaMemcpyHostToDevice, h->stream));
+            src = h->d_seg[0];
+        }
+        const uint64_t w0 = (B.nbases + off) / 32;
+        BCK(h, launch_pack(nullptr, 0, 0, src, c, B.d_words + w0, (c + 31) / 32 + kStorePad, h->stream));
+        BCK(h, cudaStreamSynchronize(h->stream));
+    }
+    // pieces (a continuation extends the open piece) and their start bits
+    std::vector<DevPiece> fresh;
+    for (uint32_t i = 0; i < n; i++) {
+        if (i == 0 && B.open) continue;
+        DevPiece d;
+        d.start = B.nbases + pieces[i].start;
+        d.contig_off = 0;
+        d.contig = pieces[i].contig;
+        d.pad = 0;
+        fresh.push_back(d);
+    }
+    if (!fresh.empty()) {
+        DevPiece *tmp = nullptr;
+        BCK(h, cudaMalloc(&tmp, fresh.size() * sizeof(DevPiece)));
+        cudaError_t e = cudaMemcpy(tmp, fresh.data(), fresh.size() * sizeof(DevPiece), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_mark_pieces(tmp, static_cast<uint32_t>(fresh.size()), B.d_words, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess) return bfail(h, IFA_ERR_CUDA, std::string("ifa_ref_append: ") + cudaGetErrorString(e));
+        B.pieces.insert(B.pieces.end(), fresh.begin(), fresh.end());
+    }
+    const ifa_piece &lp = pieces[n - 1];
+    B.open = !lp.last;
+    B.open_contig = lp.contig;
+    B.open_next = lp.offset_in_contig + lp.len;
+    B.any_contig = true;
+    B.last_contig = lp.contig;
+    B.nbases += len;
+    B.pieces_dirty = true;
+    B.plan_valid = false;
+    B.brute_entry_bases_per_s = 0;
+    return IFA_OK;
+}
+
+ifa_status ifa_ref_reset(ifa_handle *h) {
+    if (!h) return IFA_ERR_INVALID_ARG;
+    BCK(h, cudaSetDevice(h->dev));
+    BCK(h, cudaStreamSynchronize(h->stream));
+    BatchState &B = h->batch;
+    free_plan(B);
+    cudaFree(B.d_words);
+    cudaFree(B.d_pieces);
+    B.d_words = nullptr;
+    B.d_pieces = nullptr;
+    B.words_cap = 0;
+    B.nbases = 0;
+    B.pieces.clear();
+    B.d_pieces_n = 0;
+    B.pieces_dirty = true;
+    B.open = false;
+    B.any_contig = false;
+    B.brute_entry_bases_per_s = 0;
+    return IFA_OK;
+}
+
+ifa_status ifa_set_add(ifa_handle *h, const uint8_t *const *seqs, const uint32_t *lens, uint32_t n,
+                       uint32_t max_subs, ifa_mode mode, uint32_t *set_id, uint32_t *first_query) {
+    if (!h) return IFA_ERR_INVALID_ARG;
+    if (mode != IFA_MODE_AUTO && mode != IFA_MODE_BRUTE && mode != IFA_MODE_INDEXED)
+        return bfail(h, IFA_ERR_INVALID_ARG, "ifa_set_add: unknown mode");
+    if (n == 0) return bfail(h, IFA_ERR_INVALID_ARG, "ifa_set_add: empty set");
+    if (h->pushed) return bfail(h, IFA_ERR_BAD_STATE, "ifa_set_add: the handle is streaming segments");
+    const uint32_t first = static_cast<uint32_t>(h->qs.size());
+    ifa_status st = ifa_load_queries(h, seqs, lens, n, nullptr);
+    if (st != IFA_OK) return st;
+    h->qs_s.resize(first, 0);
+    h->qs_s.resize(first + n, std::min<uint32_t>(max_subs, 255));
+    QuerySet S;
+    S.first = first;
+    S.n = n;
+    S.s = std::min<uint32_t>(max_subs, 255);
+    S.mode = mode;
+    h->batch.sets.push_back(S);
+    h->batch.plan_valid = false;
+    if (set_id) *set_id = static_cast<uint32_t>(h->batch.sets.size() - 1);
+    if (first_query) *first_query = first;
+    return IFA_OK;
+}
+
+ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per_set) {
+    if (!h) return IFA_ERR_INVALID_ARG;
+    BatchState &B = h->batch;
+    if (B.nbases == 0 || B.sets.empty()) return bfail(h, IFA_ERR_BAD_STATE, "ifa_batch_run: empty store or no sets");
+    if (kind != IFA_BATCH_PERSISTENT && kind != IFA_BATCH_PER_SET)
+        return bfail(h, IFA_ERR_INVALID_ARG, "ifa_batch_run: unknown kind");
+    BCK(h, cudaSetDevice(h->dev));
+    ifa_status st = calibrate(h);
+    if (st != IFA_OK) return st;
+    st = build_plan(h);
+    if (st != IFA_OK) return st;
+    const Batch b = store_batch(B);
+    const HitSink sink = handle_sink(h);
+    QueryTable bt;
+    bt.words = B.work.bwords;
+    bt.meta = B.work.bmeta;
+    bt.ids = B.work.bids;
+    bt.n_entries = B.b_entries;
+    bt.wmax = B.wmax;
+    QueryTable ft;
+    ft.words = h->d_qwords;
+    ft.meta = h->d_qmeta;
+    ft.ids = nullptr;
+    ft.n_entries = 2 * static_cast<uint32_t>(h->qs.size());
+    ft.wmax = B.wmax;
+    cudaEvent_t start, stop;
+    BCK(h, cudaEventCreate(&start));
+    BCK(h, cudaEventCreate(&stop));
+    std::vector<cudaEvent_t> done(B.sets.size(), nullptr);
+    cudaError_t e = cudaEventRecord(start, h->stream);
+    if (kind == IFA_BATCH_PERSISTENT) {
+        if (!B.graph || B.graph_stream != h->stream) {
+            if (B.graph) cudaGraphExecDestroy(B.graph);
+            B.graph = nullptr;
+            cudaGraph_t g = nullptr;
+            const size_t smem = brute::kScanSmemBudget;
+            e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e1 = cudaMemsetAsync(B.d_queue, 0, sizeof(unsigned int), h->stream);
+                cudaError_t e2 = launch_batch(B.wmax, b, B.work, bt, ft, sink, B.grid, smem, h->stream);
+                e = cudaStreamEndCapture(h->stream, &g);
+                if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&B.graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            B.graph_stream = h->stream;
+        }
+        if (e == cudaSuccess) e = cudaGraphLaunch(B.graph, h->stream);
+        h->stats.kernel_launches += 1;
+    } else {
+        for (size_t si = 0; si < B.sets.size() && e == cudaSuccess; si++) {
+            const QuerySet &S = B.sets[si];
+            for (uint32_t c = B.set_bchunk_lo[si]; c < B.set_bchunk_hi[si] && e == cudaSuccess; c++) {
+                int launches = 0;
+                e = launch_scan_brute(b, bt, B.bchunk_e0[c], B.bchunk_e1[c], kSPerEntry, B.bchunk_lmin[c],
+                                      B.bchunk_lmax[c], sink, h->stream, &launches);
+                h->stats.kernel_launches += launches;
+            }
+            IndexedState &I = *B.per_set[si];
+            if (e == cudaSuccess && S.chosen == IFA_MODE_INDEXED && I.tables_valid && I.targ.n) {
+                e = launch_seed_scan(b, ft, I.targ, I.d_entry_minhits, h->cfg.kmer_step, kSPerEntry, sink,
+                                     I.d_candidates ? I.d_candidates : B.d_cand, h->stream);
+                h->stats.kernel_launches += 1;
+            }
+            if (e == cudaSuccess) e = cudaEventCreate(&done[si]);
+            if (e == cudaSuccess) e = cudaEventRecord(done[si], h->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(stop, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(stop);
+    float total = 0;
+    if (e == cudaSuccess) cudaEventElapsedTime(&total, start, stop);
+    if (e == cudaSuccess && per_set) {
+        std::vector<unsigned long long> qc(h->qs.size(), 0);
+        e = cudaMemcpy(qc.data(), h->d_qcount, qc.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+        for (size_t si = 0; si < B.sets.size() && e == cudaSuccess; si++) {
+            const QuerySet &S = B.sets[si];
+            ifa_set_result &r = per_set[si];
+            r.mode = S.chosen;
+            r.queries = S.n;
+            r.hits = 0;
+            for (uint32_t q = S.first; q < S.first + S.n; q++) r.hits += qc[q];
+            r.done_ms = total;
+            if (done[si]) cudaEventElapsedTime(&r.done_ms, start, done[si]);
+            r.pad = 0;
+        }
+    }
+    for (cudaEvent_t d : done)
+        if (d) cudaEventDestroy(d);
+    cudaEventDestroy(start);
+    cudaEventDestroy(stop);
+    if (e != cudaSuccess) return bfail(h, IFA_ERR_CUDA, std::string("ifa_batch_run: ") + cudaGetErrorString(e));
+    return IFA_OK;
+}
+
+}  // extern "C"

@@ -12,8 +12,7 @@
 #include <string>
 #include <vector>
 
-#include "ifa_internal.cuh"
-#include "indexed.cuh"
+#include "handle.cuh"
 
 using namespace ifa;
 
@@ -24,73 +23,7 @@ thread_local std::string g_err = "no error";
 constexpr uint32_t kHaloCap = 256;   // >= halo region H = 32 * ceil((IFA_MAX_QUERY_LEN - 1) / 32)
 constexpr uint64_t kWordPad = 16;    // zeroed words after the last packed word
 
-struct Chunk {
-    uint32_t e0, e1, lmin, lmax;
-};
-
 }  // namespace
-
-struct ifa_handle {
-    ifa_config cfg{};
-    int dev = 0;
-    cudaStream_t own_stream = nullptr;
-    cudaStream_t stream = nullptr;
-    cudaStream_t copy_stream = nullptr;
-    std::string err = "no error";
-
-    // queries
-    std::vector<std::string> qs;
-    uint32_t lmin = 0, lmax = 0, wmax = 1;
-    bool qdirty = true;
-    uint4 *d_qwords = nullptr;
-    uint32_t *d_qmeta = nullptr;
-    std::vector<Chunk> chunks;
-    std::vector<uint32_t> qmeta_host;
-    std::vector<uint4> qwords_host;
-
-    // segment slots
-    uint8_t *d_seg[2] = {nullptr, nullptr};
-    uint8_t *h_stage[2] = {nullptr, nullptr};
-    DevPiece *d_pieces[2] = {nullptr, nullptr};
-    DevPiece *h_pieces[2] = {nullptr, nullptr};
-    uint32_t pieces_cap[2] = {0, 0};
-    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
-    cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
-    bool slot_used[2] = {false, false};
-    int slot = 0;
-
-    uint8_t *d_halo[2] = {nullptr, nullptr};
-    int halo_cur = 0;
-    uint32_t halo_len = 0;
-
-    uint4 *d_words = nullptr;
-    uint64_t words_cap = 0;
-
-    // results
-    ifa_hit *d_ring = nullptr;
-    unsigned long long *d_head = nullptr;
-    uint32_t *d_overflow = nullptr;
-    unsigned long long *d_digest = nullptr;
-    unsigned long long *d_qcount = nullptr;
-    uint64_t drained = 0;
-
-    // stream position
-    bool open = false;
-    uint32_t open_contig = 0;
-    uint64_t open_next = 0;
-    bool any_contig = false;
-    uint32_t last_contig = 0;
-    bool pushed = false;
-
-    uint32_t max_subs = 0;
-    ifa_mode mode = IFA_MODE_BRUTE;
-    ifa_stats stats{};
-
-    // optional per-launch timing of the scan kernels (config.profile)
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
-
-    IndexedState idx;
-};
 
 namespace {
 
@@ -110,7 +43,11 @@ ifa_status fail_cuda(ifa_handle *h, const char *what, cudaError_t e) {
         if (e_ != cudaSuccess) return fail_cuda((h), #call, e_); \
     } while (0)
 
-void encode_entry(const std::string &q, bool rc, uint32_t wmax, uint4 *out, uint32_t *meta) {
+}  // namespace
+
+namespace ifa {
+
+void encode_entry(const std::string &q, bool rc, uint32_t wmax, uint32_t s_e, uint4 *out, uint32_t *meta) {
     const uint32_t L = static_cast<uint32_t>(q.size());
     for (uint32_t j = 0; j < wmax; j++) out[j] = make_uint4(0, 0, 0, 0);
     uint32_t nN = 0;
@@ -128,7 +65,7 @@ void encode_entry(const std::string &q, bool rc, uint32_t wmax, uint4 *out, uint
         }
         out[w].w |= bit;
     }
-    *meta = L | (((L + 31) / 32) << 8) | (nN << 16);
+    *meta = L | (((L + 31) / 32) << 8) | (nN << 16) | ((s_e > 255u ? 255u : s_e) << 24);
 }
 
 ifa_status upload_queries(ifa_handle *h) {
@@ -144,8 +81,8 @@ ifa_status upload_queries(ifa_handle *h) {
     h->qmeta_host.assign(ne, 0);
     for (uint32_t q = 0; q < nq; q++)
         for (uint32_t t = 0; t < 2; t++)
-            encode_entry(h->qs[q], t == 1, w, &words[static_cast<size_t>(2 * q + t) * w],
-                         &h->qmeta_host[2 * q + t]);
+            encode_entry(h->qs[q], t == 1, w, q < h->qs_s.size() ? h->qs_s[q] : 0u,
+                         &words[static_cast<size_t>(2 * q + t) * w], &h->qmeta_host[2 * q + t]);
     cudaFree(h->d_qwords);
     cudaFree(h->d_qmeta);
     h->d_qwords = nullptr;
@@ -169,8 +106,13 @@ ifa_status upload_queries(ifa_handle *h) {
     }
     h->qdirty = false;
     h->idx.invalidate();
+    h->batch.plan_valid = false;
     return IFA_OK;
 }
+
+}  // namespace ifa
+
+namespace {
 
 ifa_status ensure_pieces(ifa_handle *h, int slot, uint32_t n) {
     if (n <= h->pieces_cap[slot]) return IFA_OK;
@@ -348,6 +290,7 @@ void ifa_destroy(ifa_handle *h) {
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
     if (h->stream) cudaStreamSynchronize(h->stream);
     h->idx.release();
+    ifa::batch_release(h);
     for (int i = 0; i < 2; i++) {
         cudaFree(h->d_seg[i]);
         cudaFreeHost(h->h_stage[i]);
@@ -654,6 +597,7 @@ ifa_status ifa_reset_results(ifa_handle *h) {
     if (st != IFA_OK) return st;
     h->stats = ifa_stats{};
     if (h->idx.d_candidates) CK(h, cudaMemset(h->idx.d_candidates, 0, sizeof(unsigned long long)));
+    if (h->batch.d_cand) CK(h, cudaMemset(h->batch.d_cand, 0, sizeof(unsigned long long)));
     return IFA_OK;
 }
 

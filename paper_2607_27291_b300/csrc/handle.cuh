@@ -1,0 +1,95 @@
+// handle.cuh -- the ifa_handle state shared by the C ABI files.
+#pragma once
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "batch_state.cuh"
+#include "ifa_internal.cuh"
+#include "indexed.cuh"
+
+namespace ifa {
+struct Chunk {
+    uint32_t e0, e1, lmin, lmax;
+};
+
+}  // namespace ifa
+
+using ifa::Chunk;
+using ifa::DevPiece;
+using ifa::IndexedState;
+using ifa::BatchState;
+
+struct ifa_handle {
+    ifa_config cfg{};
+    int dev = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    std::string err = "no error";
+
+    // queries
+    std::vector<std::string> qs;
+    uint32_t lmin = 0, lmax = 0, wmax = 1;
+    bool qdirty = true;
+    uint4 *d_qwords = nullptr;
+    uint32_t *d_qmeta = nullptr;
+    std::vector<Chunk> chunks;
+    std::vector<uint32_t> qmeta_host;
+    std::vector<uint4> qwords_host;
+
+    // segment slots
+    uint8_t *d_seg[2] = {nullptr, nullptr};
+    uint8_t *h_stage[2] = {nullptr, nullptr};
+    DevPiece *d_pieces[2] = {nullptr, nullptr};
+    DevPiece *h_pieces[2] = {nullptr, nullptr};
+    uint32_t pieces_cap[2] = {0, 0};
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+    bool slot_used[2] = {false, false};
+    int slot = 0;
+
+    uint8_t *d_halo[2] = {nullptr, nullptr};
+    int halo_cur = 0;
+    uint32_t halo_len = 0;
+
+    uint4 *d_words = nullptr;
+    uint64_t words_cap = 0;
+
+    // results
+    ifa_hit *d_ring = nullptr;
+    unsigned long long *d_head = nullptr;
+    uint32_t *d_overflow = nullptr;
+    unsigned long long *d_digest = nullptr;
+    unsigned long long *d_qcount = nullptr;
+    uint64_t drained = 0;
+
+    // stream position
+    bool open = false;
+    uint32_t open_contig = 0;
+    uint64_t open_next = 0;
+    bool any_contig = false;
+    uint32_t last_contig = 0;
+    bool pushed = false;
+
+    uint32_t max_subs = 0;
+    ifa_mode mode = IFA_MODE_BRUTE;
+    ifa_stats stats{};
+
+    // optional per-launch timing of the scan kernels (config.profile)
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
+
+    IndexedState idx;
+
+    // per-query maxSubs of queries added by ifa_set_add (0 for ifa_load_queries)
+    std::vector<uint32_t> qs_s;
+    BatchState batch;
+};
+
+
+namespace ifa {
+// Encode the handle's queries into the device query table (no-op when clean).
+ifa_status upload_queries(ifa_handle *h);
+// Free the multi-set store and plan.
+void batch_release(ifa_handle *h);
+}  // namespace ifa

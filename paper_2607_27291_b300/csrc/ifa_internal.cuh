@@ -16,8 +16,9 @@
 //   .x hi, .y lo,
 //   .z care mask: 1 where position < L and the query base is A/C/G/T,
 //   .w length mask: 1 where position < L,
-// and a meta word L | W << 8 | nN << 16 (W = words used, nN = query Ns,
-// which always count as mismatches).
+// and a meta word L | W << 8 | nN << 16 | s_e << 24 (W = words used, nN =
+// query Ns, which always count as mismatches, s_e = the entry's own maxSubs,
+// capped at 255, used when a launch asks for per-entry thresholds).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -27,6 +28,13 @@
 namespace ifa {
 
 constexpr int kWarp = 32;
+constexpr uint32_t kSPerEntry = 0xffffffffu;  // launch threshold: use each entry's own s_e
+
+__host__ __device__ inline uint32_t meta_L(uint32_t m) { return m & 0xffu; }
+__host__ __device__ inline uint32_t meta_W(uint32_t m) { return (m >> 8) & 0xffu; }
+__host__ __device__ inline uint32_t meta_nN(uint32_t m) { return (m >> 16) & 0xffu; }
+// maxSubs of an entry under launch threshold s
+__host__ __device__ inline uint32_t entry_s(uint32_t m, uint32_t s) { return s == kSPerEntry ? (m >> 24) : s; }
 
 struct DevPiece {
     uint64_t start;        // first base of the piece in batch coordinates

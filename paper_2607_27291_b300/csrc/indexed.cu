@@ -25,6 +25,7 @@
 
 #include "hits.cuh"
 #include "indexed.cuh"
+#include "seed_scan.cuh"
 
 namespace ifa {
 
@@ -43,116 +44,10 @@ k_seed_scan(Batch b, QueryTable qt, KTablesArg tabs, const uint32_t *__restrict_
     WarpHits wh;
     wh.init(wbuf[warp]);
     unsigned long long ncand = 0;
-
     const uint64_t nblocks = (b.nbases + 31) >> 5;
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kSeedWarps;
-    for (uint64_t blk = static_cast<uint64_t>(blockIdx.x) * kSeedWarps + warp; blk < nblocks; blk += stride) {
-        const uint64_t j = (blk << 5) + lane;
-        const uint4 A = __ldg(b.words + blk), B = __ldg(b.words + blk + 1);
-        const uint32_t hiw = __funnelshift_r(A.x, B.x, lane);
-        const uint32_t low = __funnelshift_r(A.y, B.y, lane);
-        const uint32_t nw = __funnelshift_r(A.z, B.z, lane);
-        const uint32_t bw = __funnelshift_r(A.w, B.w, lane);
-        for (uint32_t ti = 0; ti < tabs.n; ti++) {
-            const KTableDev &T = tabs.t[ti];
-            const uint32_t k = T.k;
-            const uint32_t full = (k >= 32) ? 0xffffffffu : ((1u << k) - 1u);
-            uint32_t beg = 0, end = 0;
-            if (j + k <= b.nbases && (nw & full) == 0u && ((bw >> 1) & (full >> 1)) == 0u) {
-                const uint32_t key = ((hiw & T.care) << k) | (low & T.care);
-                if (T.direct) {
-                    beg = __ldg(T.off + key);
-                    end = __ldg(T.off + key + 1);
-                } else if ((__ldg(T.bits + (key >> 5)) >> (key & 31)) & 1u) {
-                    uint32_t lo = 0, hi = T.nuniq;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (__ldg(T.keys + mid) < key) lo = mid + 1; else hi = mid;
-                    }
-                    if (lo < T.nuniq && __ldg(T.keys + lo) == key) {
-                        beg = __ldg(T.off + lo);
-                        end = __ldg(T.off + lo + 1);
-                    }
-                }
-            }
-            // warp-synchronous walk over each lane's postings so hits can be
-            // compacted by ballot
-            while (__any_sync(0xffffffffu, beg < end)) {
-                bool hit = false;
-                uint32_t id = 0, contig = 0, pos = 0, mm = 0;
-                if (beg < end) {
-                    const uint32_t pv = __ldg(T.post + beg);
-                    beg++;
-                    const uint32_t e = pv >> 8, o = pv & 0xffu;
-                    const uint32_t meta = __ldg(qt.meta + e);
-                    const uint32_t L = meta & 0xffu, W = (meta >> 8) & 0xffu;
-                    if (o <= j) {
-                        const uint64_t p = j - o;
-                        if (p + L <= b.nbases && p + L >= static_cast<uint64_t>(b.halo) + 1) {
-                            ncand++;
-                            const uint64_t w0 = p >> 5;
-                            const uint32_t sh = static_cast<uint32_t>(p & 31);
-                            uint32_t x[WMAX + 1];
-                            uint32_t bnd = 0;
-                            mm = 0;
-                            uint4 cur = __ldg(b.words + w0);
-#pragma unroll
-                            for (int w = 0; w < WMAX; w++) {
-                                x[w] = 0;
-                                if (w < static_cast<int>(W)) {
-                                    const uint4 nx = __ldg(b.words + w0 + w + 1);
-                                    const uint32_t rh = __funnelshift_r(cur.x, nx.x, sh);
-                                    const uint32_t rl = __funnelshift_r(cur.y, nx.y, sh);
-                                    const uint32_t rn = __funnelshift_r(cur.z, nx.z, sh);
-                                    uint32_t rb = __funnelshift_r(cur.w, nx.w, sh);
-                                    if (w == 0) rb &= ~1u;
-                                    const uint4 q = __ldg(qt.words + static_cast<size_t>(e) * WMAX + w);
-                                    x[w] = ((rh ^ q.x) | (rl ^ q.y) | rn) & q.w;
-                                    mm += __popc(x[w]);
-                                    bnd |= rb & q.w;
-                                    cur = nx;
-                                }
-                            }
-                            x[WMAX] = 0;
-                            if (bnd == 0u && mm <= s) {
-                                // error-free k-mer offsets from the mismatch mask
-                                const uint32_t last = L - k;  // largest offset
-                                uint32_t nseed = 0, first = 0xffffffffu;
-#pragma unroll
-                                for (int w = 0; w < WMAX; w++) {
-                                    if (w < static_cast<int>(W) && static_cast<uint32_t>(w) * 32 <= last) {
-                                        uint32_t c = 0;
-                                        for (uint32_t i = 0; i < k; i++)
-                                            if ((T.care >> i) & 1u) c |= __funnelshift_r(x[w], x[w + 1], i);
-                                        uint32_t valid = 0xffffffffu;
-                                        const uint32_t base = static_cast<uint32_t>(w) * 32;
-                                        if (last - base < 31) valid = (2u << (last - base)) - 1u;
-                                        uint32_t S = ~c & valid;
-                                        if (step > 1) {
-                                            uint32_t sm = 0;
-                                            for (uint32_t bi = 0; bi < 32; bi++)
-                                                if ((base + bi) % step == 0) sm |= 1u << bi;
-                                            S &= sm;
-                                        }
-                                        nseed += __popc(S);
-                                        if (first == 0xffffffffu && S) first = base + __ffs(S) - 1;
-                                    }
-                                }
-                                if (first == o && nseed >= __ldg(entry_minhits + e)) {
-                                    hit = true;
-                                    const DevPiece pc = b.pieces[find_piece(b.pieces, b.npieces, p)];
-                                    contig = pc.contig;
-                                    pos = static_cast<uint32_t>(pc.contig_off + (p - pc.start));
-                                    id = e;
-                                }
-                            }
-                        }
-                    }
-                }
-                wh.emit(sink, lane, hit, id >> 1, contig, pos, id & 1u, mm, nullptr);
-            }
-        }
-    }
+    seed::seed_blocks<WMAX>(b, qt, tabs, entry_minhits, step, s, sink, wh,
+                            static_cast<uint64_t>(blockIdx.x) * kSeedWarps + warp, nblocks, stride, lane, ncand);
     wh.finish(sink, lane);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
@@ -293,25 +188,26 @@ ifa_status minhits_device(const uint32_t *L, const uint32_t *subs, const uint32_
     return IFA_OK;
 }
 
-ifa_status indexed_plan(IndexedState &S, const std::vector<std::string> &qs, const ifa_config &cfg,
-                        uint32_t s, cudaStream_t st, std::string &err) {
-    if (S.plan_valid && S.plan_s == s) return IFA_OK;
+ifa_status indexed_plan_q(IndexedState &S, const std::vector<std::string> &qs,
+                          const std::vector<uint32_t> &svec, const std::vector<uint8_t> &include,
+                          const ifa_config &cfg, cudaStream_t st, std::string &err) {
     const uint32_t nq = static_cast<uint32_t>(qs.size());
-    std::vector<uint32_t> lens;
-    for (const auto &q : qs) lens.push_back(static_cast<uint32_t>(q.size()));
-    std::vector<uint32_t> ul = lens;
-    std::sort(ul.begin(), ul.end());
-    ul.erase(std::unique(ul.begin(), ul.end()), ul.end());
+    // MinHits bins: distinct (L, s) of the included queries x listed k
+    std::vector<std::pair<uint32_t, uint32_t>> ls;
+    for (uint32_t q = 0; q < nq; q++)
+        if (include[q]) ls.push_back({static_cast<uint32_t>(qs[q].size()), svec[q]});
+    std::sort(ls.begin(), ls.end());
+    ls.erase(std::unique(ls.begin(), ls.end()), ls.end());
     std::vector<uint32_t> bL, bS, bK;
     uint32_t stride = 2;
-    for (uint32_t L : ul)
+    for (const auto &p : ls)
         for (uint32_t i = 0; i < cfg.n_k; i++) {
             const uint32_t k = cfg.k_list[i];
-            if (k > L || k <= cfg.mask_width) continue;
-            bL.push_back(L);
-            bS.push_back(s);
+            if (k > p.first || k <= cfg.mask_width) continue;
+            bL.push_back(p.first);
+            bS.push_back(p.second);
             bK.push_back(k);
-            stride = std::max(stride, (L - k) / cfg.kmer_step + 2);
+            stride = std::max(stride, (p.first - k) / cfg.kmer_step + 2);
         }
     std::vector<uint32_t> bm(bL.size());
     ifa_status r = minhits_device(bL.data(), bS.data(), bK.data(), static_cast<uint32_t>(bL.size()),
@@ -319,41 +215,49 @@ ifa_status indexed_plan(IndexedState &S, const std::vector<std::string> &qs, con
                                   cfg.minhits_den, cfg.minhits_trials, cfg.minhits_seed, bm.data(), st,
                                   stride, err);
     if (r != IFA_OK) return r;
-    // per length: the longest k with threshold >= 1, else the smallest k clamped to 1
-    std::map<uint32_t, std::pair<int, std::pair<uint32_t, uint32_t>>> choice;  // L -> (status, (k, m))
-    for (uint32_t L : ul) choice[L] = {-1, {0, 0}};
+    // per (L, s): the longest k with threshold >= 1, else the smallest k clamped to 1
+    std::map<std::pair<uint32_t, uint32_t>, std::pair<int, std::pair<uint32_t, uint32_t>>> choice;
+    for (const auto &p : ls) choice[p] = {-1, {0, 0}};
     for (size_t i = 0; i < bL.size(); i++) {
-        auto &c = choice[bL[i]];
+        auto &c = choice[{bL[i], bS[i]}];
         if (bm[i] >= 1 && (c.first != 1 || bK[i] > c.second.first)) c = {1, {bK[i], bm[i]}};
     }
     for (size_t i = 0; i < bL.size(); i++) {
-        auto &c = choice[bL[i]];
+        auto &c = choice[{bL[i], bS[i]}];
         if (c.first == 1) continue;
         if (c.first == -1 || bK[i] < c.second.first) c = {0, {bK[i], 1u}};
     }
     S.plan_k.assign(nq, 0);
     S.plan_minhits.assign(nq, 0);
     S.plan_exhaustive.assign(nq, 0);
+    S.plan_in = include;
     for (uint32_t q = 0; q < nq; q++) {
-        const auto &c = choice[lens[q]];
+        if (!include[q]) continue;
+        const auto &c = choice[{static_cast<uint32_t>(qs[q].size()), svec[q]}];
         S.plan_k[q] = c.second.first;
         S.plan_minhits[q] = c.second.second;
         const bool ex = c.first < 0 || (c.first == 0 && cfg.exhaustive_fallback) || has_n(qs[q]);
         S.plan_exhaustive[q] = ex ? 1 : 0;
     }
     S.plan_valid = true;
-    S.plan_s = s;
     S.tables_valid = false;
     return IFA_OK;
 }
 
-ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
-                           const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
-                           uint32_t wmax, const ifa_config &cfg, uint32_t s, cudaStream_t st,
-                           std::string &err) {
-    ifa_status r = indexed_plan(S, qs, cfg, s, st, err);
+ifa_status indexed_plan(IndexedState &S, const std::vector<std::string> &qs, const ifa_config &cfg,
+                        uint32_t s, cudaStream_t st, std::string &err) {
+    if (S.plan_valid && S.plan_s == s && S.plan_uniform) return IFA_OK;
+    ifa_status r = indexed_plan_q(S, qs, std::vector<uint32_t>(qs.size(), s),
+                                  std::vector<uint8_t>(qs.size(), 1), cfg, st, err);
     if (r != IFA_OK) return r;
-    if (S.tables_valid && S.tables_s == s && S.wmax == wmax) return IFA_OK;
+    S.plan_s = s;
+    S.plan_uniform = true;
+    return IFA_OK;
+}
+
+ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
+                          const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
+                          uint32_t wmax, const ifa_config &cfg, std::string &err) {
     S.free_tables();
     S.wmax = wmax;
     S.step = cfg.kmer_step;
@@ -389,7 +293,7 @@ ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
         const uint32_t care = care_mask(k, cfg.mask_width);
         std::vector<std::pair<uint32_t, uint32_t>> kv;  // (key, posting)
         for (uint32_t q = 0; q < nq; q++) {
-            if (S.plan_exhaustive[q] || S.plan_k[q] != k) continue;
+            if (!S.plan_in[q] || S.plan_exhaustive[q] || S.plan_k[q] != k) continue;
             const uint32_t L = static_cast<uint32_t>(qs[q].size());
             for (uint32_t t = 0; t < 2; t++)
                 for (uint32_t o = 0; o + k <= L; o += cfg.kmer_step)
@@ -444,7 +348,7 @@ ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
     // exhaustive queries: compact table for the brute-force kernel
     std::vector<uint32_t> exq;
     for (uint32_t q = 0; q < nq; q++)
-        if (S.plan_exhaustive[q]) exq.push_back(q);
+        if (S.plan_in[q] && S.plan_exhaustive[q]) exq.push_back(q);
     S.any_exhaustive = !exq.empty();
     if (S.any_exhaustive && e == cudaSuccess) {
         const uint32_t ne = 2 * static_cast<uint32_t>(exq.size());
@@ -482,6 +386,18 @@ ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
         return e == cudaErrorMemoryAllocation ? IFA_ERR_OOM : IFA_ERR_CUDA;
     }
     S.tables_valid = true;
+    return IFA_OK;
+}
+
+ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
+                           const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
+                           uint32_t wmax, const ifa_config &cfg, uint32_t s, cudaStream_t st,
+                           std::string &err) {
+    ifa_status r = indexed_plan(S, qs, cfg, s, st, err);
+    if (r != IFA_OK) return r;
+    if (S.tables_valid && S.tables_s == s && S.wmax == wmax) return IFA_OK;
+    r = indexed_tables(S, qs, qmeta, qwords, wmax, cfg, err);
+    if (r != IFA_OK) return r;
     S.tables_s = s;
     return IFA_OK;
 }

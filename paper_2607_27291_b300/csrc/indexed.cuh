@@ -35,9 +35,11 @@ struct KTablesArg {
 struct IndexedState {
     // plan (per query) for plan_s
     bool plan_valid = false;
+    bool plan_uniform = false;   // plan made for one maxSubs (plan_s) over all queries
     uint32_t plan_s = 0;
     std::vector<uint32_t> plan_k, plan_minhits;
     std::vector<uint8_t> plan_exhaustive;
+    std::vector<uint8_t> plan_in;  // query is part of this plan
 
     // device tables for tables_s
     bool tables_valid = false;
@@ -60,6 +62,7 @@ struct IndexedState {
 
     void invalidate() {
         plan_valid = false;
+        plan_uniform = false;
         tables_valid = false;
     }
     void free_tables();
@@ -74,6 +77,17 @@ ifa_status minhits_device(const uint32_t *L, const uint32_t *subs, const uint32_
 
 ifa_status indexed_plan(IndexedState &S, const std::vector<std::string> &qs, const ifa_config &cfg,
                         uint32_t max_subs, cudaStream_t st, std::string &err);
+
+// Plan for the included queries, each with its own maxSubs.
+ifa_status indexed_plan_q(IndexedState &S, const std::vector<std::string> &qs,
+                          const std::vector<uint32_t> &svec, const std::vector<uint8_t> &include,
+                          const ifa_config &cfg, cudaStream_t st, std::string &err);
+
+// Device tables of the current plan (seeded queries) and the compact table of
+// its exhaustive queries.
+ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
+                          const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
+                          uint32_t wmax, const ifa_config &cfg, std::string &err);
 
 ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
                            const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,

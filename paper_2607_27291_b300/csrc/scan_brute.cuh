@@ -1,0 +1,383 @@
+// scan_brute.cuh -- device code of the brute-force scan, shared by the
+// streaming kernel (scan_brute.cu) and the persistent multi-set kernel
+// (batch.cu).
+//
+//
+// The paper's CPU kernel broadcasts each query base against 32 consecutive
+// reference positions and counts mismatches per lane, stopping early once
+// every lane is over the threshold.  Here a warp owns 128 consecutive
+// windows (four per lane) and compares 32-base words bit-parallel:
+//   x  = ((R_hi ^ Q_hi) | (R_lo ^ Q_lo)) & care        one word, 32 bases
+//   mm = nN + sum over words of popc(x)
+// R_* is the lane's window word, cut from two packed words by a funnel
+// shift; Q_* the query word (reverse complement precomputed) in shared
+// memory.  The packed words of the warp's next block are prefetched into a
+// per-warp shared double buffer with cp.async while the current one is
+// scanned.
+//
+// Early termination, batched: for maxSubs < 32 the first word alone
+// rejects almost every window (E[mm] = 24 of 32 on random sequence), so
+// the hot loop computes only word 0 for 4 entries x 4 windows, packs each
+// entry's four counts into one word whose byte high bits say "over the
+// threshold" (see packed_counts), and one warp vote per 4 entries decides
+// whether the exact path (all words, hit emission) runs for any of them
+// (then a vote per entry picks which).  Entries whose first word is fully
+// counted and that hold no N ("class F") need no care mask, so a window
+// costs 2 LOP3 + 1 POPC on the ALU/POPC pipes plus 1 IMAD on the FMA
+// pipe -- the POPC pipe (16 lanes/clk/SM) is the binding unit.  Other
+// entries ("class M") also AND a care mask and use the threshold
+// maxSubs - nN.
+//
+// Blocks of windows that touch an N, a contig-piece boundary, the batch end
+// or the halo take a generic path that folds in the reference N plane and
+// checks each window stays inside one piece and is owned by this batch.
+#pragma once
+#include "hits.cuh"
+
+namespace ifa {
+namespace brute {
+
+
+constexpr int kScanThreads = 256;
+constexpr int kScanWarps = kScanThreads / kWarp;
+constexpr size_t kScanSmemBudget = 40 * 1024;  // dynamic; + static (hit staging, word staging) < 48 KB
+constexpr int kGroup = 4;                       // entries per warp vote in the hot loop
+constexpr int kWin = 4;                         // windows per lane (32 * kWin per warp step)
+
+// Per-entry shared memory: WMAX uint4 words, a class-M word-0 record, a
+// class-F word-0 record, meta, count, and two 16-bit index slots.
+__host__ __device__ constexpr size_t entry_smem(int wmax) {
+    return wmax * sizeof(uint4) + 2 * sizeof(uint4) + 2 * sizeof(uint32_t) + 2 * sizeof(uint16_t);
+}
+
+struct Smem {
+    uint4 *sq;         // entries x WMAX full words
+    uint4 *sM;         // class M: {hi0, lo0, care0, threshold}
+    uint4 *sF;         // class F: {hi0, lo0, threshold, 0}
+    uint32_t *meta;
+    uint32_t *cnt;
+    uint16_t *fidx;
+    uint16_t *midx;
+};
+
+__device__ inline Smem carve(uint4 *base, uint32_t nent, int wmax) {
+    Smem m;
+    m.sq = base;
+    m.sM = m.sq + static_cast<size_t>(nent) * wmax;
+    m.sF = m.sM + nent;
+    m.meta = reinterpret_cast<uint32_t *>(m.sF + nent);
+    m.cnt = m.meta + nent;
+    m.fidx = reinterpret_cast<uint16_t *>(m.cnt + nent);
+    m.midx = m.fidx + nent;
+    return m;
+}
+
+// Words of the block starting at word 2*? are staged per warp in shared
+// memory; a block is WIN x 32 windows: lane l owns windows p0 + 32 k + l,
+// k < WIN, and window k's word j is cut from staged words k + j, k + j + 1.
+template <int WMAX>
+struct Stage {
+    static constexpr int kWords = kWin + WMAX;  // staged words per block
+};
+
+// Exact evaluation of one entry for the lane's WIN windows of a block without
+// N, piece boundary or ownership limits, then hit emission.
+template <int WMAX>
+__device__ __forceinline__ void exact_fast(const Batch &b, const QueryTable &qt, const Smem &m,
+                                           const uint4 *R, uint32_t e, uint32_t e0, uint64_t p0,
+                                           uint32_t lane, uint32_t s, const HitSink &sink,
+                                           WarpHits &wh, uint32_t &pidx) {
+    const uint32_t meta = m.meta[e];
+    const uint32_t W = meta_W(meta);
+    const uint32_t se = entry_s(meta, s);
+    const uint4 *qw = m.sq + static_cast<size_t>(e) * WMAX;
+    uint32_t mm[kWin];
+#pragma unroll
+    for (int k = 0; k < kWin; k++) mm[k] = meta_nN(meta);
+#pragma unroll
+    for (int j = 0; j < WMAX; j++) {
+        if (j < static_cast<int>(W)) {
+            const uint4 q = qw[j];
+#pragma unroll
+            for (int k = 0; k < kWin; k++) {
+                const uint4 a = R[k + j], c = R[k + j + 1];
+                const uint32_t h = __funnelshift_r(a.x, c.x, lane), l = __funnelshift_r(a.y, c.y, lane);
+                mm[k] += __popc(((h ^ q.x) | (l ^ q.y)) & q.z);
+            }
+        }
+    }
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < kWin; k++) any |= mm[k] <= se;
+    if (!__any_sync(0xffffffffu, any)) return;
+    if (pidx == 0xffffffffu) pidx = find_piece(b.pieces, b.npieces, p0);
+    const DevPiece pc = b.pieces[pidx];
+    const uint32_t id = qt.ids ? qt.ids[e0 + e] : e0 + e;
+    const uint32_t pos0 = static_cast<uint32_t>(pc.contig_off + (p0 + lane - pc.start));
+#pragma unroll
+    for (int k = 0; k < kWin; k++)
+        wh.emit(sink, lane, mm[k] <= se, id >> 1, pc.contig, pos0 + 32 * k, id & 1u, mm[k], m.cnt + e);
+}
+
+// Generic evaluation of every entry for one window per lane (p = p0 + lane)
+// whose block may hold N, piece boundaries, the batch end or the halo.
+template <int WMAX>
+__device__ void generic_window(const Batch &b, const QueryTable &qt, const Smem &m, uint32_t nent,
+                               uint32_t e0, uint64_t p0, uint32_t lane, uint32_t s,
+                               const HitSink &sink, WarpHits &wh) {
+    const uint64_t w0 = p0 >> 5;
+    uint32_t hi[WMAX], lo[WMAX], nw[WMAX], bw[WMAX];
+    uint4 cur = __ldg(b.words + w0);
+#pragma unroll
+    for (int j = 0; j < WMAX; j++) {
+        const uint4 nx = __ldg(b.words + w0 + j + 1);
+        hi[j] = __funnelshift_r(cur.x, nx.x, lane);
+        lo[j] = __funnelshift_r(cur.y, nx.y, lane);
+        nw[j] = __funnelshift_r(cur.z, nx.z, lane);
+        bw[j] = __funnelshift_r(cur.w, nx.w, lane);
+        cur = nx;
+    }
+    bw[0] &= ~1u;  // a piece may start at the window's first base
+    const uint64_t p = p0 + lane;
+    for (uint32_t e = 0; e < nent; e++) {
+        const uint32_t meta = m.meta[e];
+        const uint32_t L = meta_L(meta);
+        const uint32_t W = meta_W(meta);
+        const uint4 *qw = m.sq + static_cast<size_t>(e) * WMAX;
+        uint32_t mm = meta_nN(meta);
+        uint32_t bnd = 0;
+#pragma unroll
+        for (int j = 0; j < WMAX; j++) {
+            if (j < static_cast<int>(W)) {
+                const uint4 q = qw[j];
+                mm += __popc(((hi[j] ^ q.x) | (lo[j] ^ q.y) | nw[j]) & q.z);
+                bnd |= bw[j] & q.w;
+            }
+        }
+        const bool valid = (p + L <= b.nbases) && (p + L >= static_cast<uint64_t>(b.halo) + 1) && bnd == 0u;
+        const bool hit = valid && mm <= entry_s(meta, s);
+        if (__any_sync(0xffffffffu, hit)) {
+            uint32_t contig = 0, pos = 0;
+            if (hit) {
+                const DevPiece pc = b.pieces[find_piece(b.pieces, b.npieces, p)];
+                contig = pc.contig;
+                pos = static_cast<uint32_t>(pc.contig_off + (p - pc.start));
+            }
+            const uint32_t id = qt.ids ? qt.ids[e0 + e] : e0 + e;
+            wh.emit(sink, lane, hit, id >> 1, contig, pos, id & 1u, mm, m.cnt + e);
+        }
+    }
+}
+
+// Byte-lane threshold test.  The four windows' word-0 counts p_k (<= 32)
+// are packed as v = C + p0 + p1 << 8 + p2 << 16 + p3 << 24 with
+// C = 0x80808080 - (T + 1) * 0x01010101 for the entry's threshold T in
+// [-1, 127]: byte k is 128 - (T + 1) + p_k, in [0, 160], so no carry crosses
+// bytes and its high bit is clear exactly when p_k <= T.  The packing runs
+// as IMADs on the FMA pipe (multipliers held in registers), keeping the ALU
+// pipe for the two LOP3 per window.
+__host__ __device__ inline uint32_t byte_bias(int T) {
+    if (T < -1) T = -1;
+    if (T > 127) T = 127;
+    return 0x80808080u - static_cast<uint32_t>(T + 1) * 0x01010101u;
+}
+
+__device__ __forceinline__ uint32_t mad(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// Entry word-0 records: {hi0, lo0, bias, -} (class F) or
+// {hi0, lo0, care0, bias} (class M, MASKED).
+template <bool MASKED>
+__device__ __forceinline__ uint32_t packed_counts(const uint4 &q, const uint32_t *hw, const uint32_t *lw,
+                                                  const uint32_t *mul) {
+    uint32_t p[kWin];
+#pragma unroll
+    for (int w = 0; w < kWin; w++) {
+        uint32_t x = (hw[w] ^ q.x) | (lw[w] ^ q.y);
+        if (MASKED) x &= q.z;
+        p[w] = __popc(x);
+    }
+    uint32_t v = (MASKED ? q.w : q.z) + p[0];
+#pragma unroll
+    for (int w = 1; w < kWin; w++) v = mad(p[w], mul[w], v);
+    return v;
+}
+
+template <int WMAX, bool MASKED>
+__device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt, const Smem &m,
+                                           const uint4 *rec, const uint16_t *idx, uint32_t n,
+                                           const uint32_t *hw, const uint32_t *lw, const uint32_t *mul,
+                                           const uint4 *R, uint32_t e0, uint64_t p0, uint32_t lane,
+                                           uint32_t s, const HitSink &sink, WarpHits &wh, uint32_t &pidx) {
+    constexpr uint32_t kHigh = 0x80808080u;
+    uint32_t k = 0;
+    for (; k + kGroup <= n; k += kGroup) {
+        uint32_t v[kGroup];
+#pragma unroll
+        for (int i = 0; i < kGroup; i++) v[i] = packed_counts<MASKED>(rec[k + i], hw, lw, mul);
+        const uint32_t acc = v[0] & v[1] & v[2] & v[3];
+        if (__any_sync(0xffffffffu, (acc & kHigh) != kHigh)) {
+            // which of the 4 entries fired in any lane; one (not unrolled) copy
+            // of the exact path walks them
+            uint32_t fired = 0;
+#pragma unroll
+            for (int i = 0; i < kGroup; i++) fired |= ((v[i] & kHigh) != kHigh ? 1u : 0u) << i;
+            fired = __reduce_or_sync(0xffffffffu, fired);
+#pragma unroll 1
+            while (fired) {
+                const int i = __ffs(fired) - 1;
+                fired &= fired - 1;
+                exact_fast<WMAX>(b, qt, m, R, idx[k + i], e0, p0, lane, s, sink, wh, pidx);
+            }
+        }
+    }
+    for (; k < n; k++) {
+        const uint32_t v = packed_counts<MASKED>(rec[k], hw, lw, mul);
+        if (__any_sync(0xffffffffu, (v & kHigh) != kHigh))
+            exact_fast<WMAX>(b, qt, m, R, idx[k], e0, p0, lane, s, sink, wh, pidx);
+    }
+}
+
+// Stage the words of block `blk` into `dst` (shared) with cp.async: lane i
+// copies word i (16 bytes).
+template <int NW>
+__device__ __forceinline__ void stage_block(const Batch &b, uint64_t blk, uint4 *dst, uint32_t lane) {
+    if (lane < NW) {
+        const uint4 *src = b.words + blk * kWin + lane;
+        const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + lane));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Load entries [e0, e1) of the table into shared memory and split them into
+// class F and class M (all threads of the CTA; ends with a barrier).
+template <int WMAX>
+__device__ __forceinline__ Smem load_chunk(const QueryTable &qt, uint32_t e0, uint32_t e1, uint32_t s,
+                                           uint4 *smem_base, uint32_t *s_nF, uint32_t *s_nM) {
+    const uint32_t nent = e1 - e0;
+    const Smem m = carve(smem_base, nent, WMAX);
+    for (uint32_t i = threadIdx.x; i < nent * WMAX; i += blockDim.x)
+        m.sq[i] = qt.words[static_cast<size_t>(e0) * WMAX + i];
+    for (uint32_t i = threadIdx.x; i < nent; i += blockDim.x) {
+        m.meta[i] = qt.meta[e0 + i];
+        m.cnt[i] = 0;
+    }
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        // split entries into class F (word 0 fully counted, no N) and class M
+        uint32_t nF = 0, nM = 0;
+        for (uint32_t base = 0; base < nent; base += 32) {
+            const uint32_t e = base + lane;
+            bool isF = false, isM = false;
+            uint4 w0 = make_uint4(0, 0, 0, 0);
+            uint32_t meta = 0;
+            if (e < nent) {
+                meta = m.meta[e];
+                w0 = m.sq[static_cast<size_t>(e) * WMAX];
+                isF = meta_nN(meta) == 0u && w0.z == 0xffffffffu;
+                isM = !isF;
+            }
+            const uint32_t se = entry_s(meta, s);
+            const uint32_t bf = __ballot_sync(0xffffffffu, isF);
+            const uint32_t bm = __ballot_sync(0xffffffffu, isM);
+            const uint32_t below = (1u << lane) - 1u;
+            if (isF) {
+                const uint32_t k = nF + __popc(bf & below);
+                m.sF[k] = make_uint4(w0.x, w0.y, byte_bias(se > 127u ? 127 : static_cast<int>(se)), 0u);
+                m.fidx[k] = static_cast<uint16_t>(e);
+            }
+            if (isM) {
+                const uint32_t k = nM + __popc(bm & below);
+                const uint32_t nN = meta_nN(meta);
+                // threshold for word 0 alone: popc(word 0) <= s - nN is necessary
+                // for a hit; -1 (as int) when the query's Ns alone exceed s
+                const int thr = se >= nN ? static_cast<int>(se - nN > 127u ? 127u : se - nN) : -1;
+                m.sM[k] = make_uint4(w0.x, w0.y, w0.z, byte_bias(thr));
+                m.midx[k] = static_cast<uint16_t>(e);
+            }
+            nF += __popc(bf);
+            nM += __popc(bm);
+        }
+        if (lane == 0) {
+            *s_nF = nF;
+            *s_nM = nM;
+        }
+    }
+    __syncthreads();
+    return m;
+}
+
+// Per-entry counts of the chunk into the per-query counters (all threads,
+// after the last scan of the chunk and a barrier).
+__device__ __forceinline__ void flush_counts(const QueryTable &qt, const Smem &m, uint32_t nent, uint32_t e0,
+                                             const HitSink &sink) {
+    for (uint32_t i = threadIdx.x; i < nent; i += blockDim.x)
+        if (m.cnt[i]) {
+            const uint32_t id = qt.ids ? qt.ids[e0 + i] : e0 + i;
+            atomicAdd(&sink.qcount[id >> 1], static_cast<unsigned long long>(m.cnt[i]));
+            m.cnt[i] = 0;
+        }
+}
+
+// Byte-lane multipliers 1, 2^8, 2^16, 2^24 in registers (opaque to the
+// compiler, so the count packing stays IMAD on the FMA pipe).
+__device__ __forceinline__ void lane_multipliers(uint32_t *mul) {
+#pragma unroll
+    for (int w = 0; w < kWin; w++) asm volatile("mov.u32 %0, %1;" : "=r"(mul[w]) : "r"(1u << (8 * w)));
+}
+
+// Scan blocks blk, blk + stride, ... < blk_end (of 32 * kWin windows) with
+// this warp, staging words through stage[2][NW] (this warp's buffers).
+template <int WMAX>
+__device__ __forceinline__ void scan_blocks(const Batch &b, const QueryTable &qt, const Smem &m, uint32_t nent,
+                                            uint32_t nF, uint32_t nM, uint32_t e0, uint32_t s, uint32_t lmin,
+                                            uint32_t lmax, const HitSink &sink, WarpHits &wh,
+                                            uint4 (*stage)[Stage<WMAX>::kWords], const uint32_t *mul,
+                                            uint64_t blk, uint64_t blk_end, uint64_t stride, uint32_t lane) {
+    constexpr int NW = Stage<WMAX>::kWords;
+    if (blk < blk_end) stage_block<NW>(b, blk, stage[0], lane);
+    for (uint32_t it = 0; blk < blk_end; it++, blk += stride) {
+        const uint64_t nxt = blk + stride;
+        if (nxt < blk_end) stage_block<NW>(b, nxt, stage[(it + 1) & 1], lane);
+        else asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncwarp();
+        const uint4 *R = stage[it & 1];
+        const uint64_t p0 = blk * (32 * kWin);
+        uint32_t flags = R[0].z | (R[0].w & ~1u);
+#pragma unroll
+        for (int i = 1; i < NW; i++) flags |= R[i].z | R[i].w;
+        // a uniform maxSubs >= 32 makes word 0 useless as a filter: scan generically
+        const bool special = (s != kSPerEntry && s >= 32u) || flags != 0u ||
+                             p0 + 32 * kWin - 1 + lmax - 1 >= b.nbases ||
+                             p0 + lmin < static_cast<uint64_t>(b.halo) + 1;
+        if (special) {
+#pragma unroll 1
+            for (int k = 0; k < kWin; k++)
+                generic_window<WMAX>(b, qt, m, nent, e0, p0 + 32 * k, lane, s, sink, wh);
+            __syncwarp();
+            continue;
+        }
+        // word 0 of the lane's windows
+        uint32_t hw[kWin], lw[kWin];
+#pragma unroll
+        for (int k = 0; k < kWin; k++) {
+            hw[k] = __funnelshift_r(R[k].x, R[k + 1].x, lane);
+            lw[k] = __funnelshift_r(R[k].y, R[k + 1].y, lane);
+        }
+        uint32_t pidx = 0xffffffffu;
+        scan_class<WMAX, false>(b, qt, m, m.sF, m.fidx, nF, hw, lw, mul, R, e0, p0, lane, s, sink, wh, pidx);
+        scan_class<WMAX, true>(b, qt, m, m.sM, m.midx, nM, hw, lw, mul, R, e0, p0, lane, s, sink, wh, pidx);
+        __syncwarp();
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+}  // namespace brute
+}  // namespace ifa

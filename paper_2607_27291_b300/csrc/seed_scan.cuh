@@ -1,0 +1,131 @@
+// seed_scan.cuh -- device code of the indexed-mode seed scan, shared by the
+// streaming kernel (indexed.cu) and the persistent multi-set kernel
+// (batch.cu).  See indexed.cu for the method.
+#pragma once
+#include "hits.cuh"
+#include "indexed.cuh"
+
+namespace ifa {
+namespace seed {
+
+// Scan 32-position blocks blk, blk + stride, ... < blk_end with this warp:
+// look every position's k-mer up in each table, verify the window each
+// posting names, and emit it from its first seed when its seed count
+// reaches the entry's threshold.  Adds verified candidates to ncand.
+template <int WMAX>
+__device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt, const KTablesArg &tabs,
+                                            const uint32_t *__restrict__ entry_minhits, uint32_t step,
+                                            uint32_t s, const HitSink &sink, WarpHits &wh, uint64_t blk,
+                                            uint64_t blk_end, uint64_t stride, uint32_t lane,
+                                            unsigned long long &ncand) {
+    for (; blk < blk_end; blk += stride) {
+        const uint64_t j = (blk << 5) + lane;
+        const uint4 A = __ldg(b.words + blk), B = __ldg(b.words + blk + 1);
+        const uint32_t hiw = __funnelshift_r(A.x, B.x, lane);
+        const uint32_t low = __funnelshift_r(A.y, B.y, lane);
+        const uint32_t nw = __funnelshift_r(A.z, B.z, lane);
+        const uint32_t bw = __funnelshift_r(A.w, B.w, lane);
+        for (uint32_t ti = 0; ti < tabs.n; ti++) {
+            const KTableDev &T = tabs.t[ti];
+            const uint32_t k = T.k;
+            const uint32_t full = (k >= 32) ? 0xffffffffu : ((1u << k) - 1u);
+            uint32_t beg = 0, end = 0;
+            if (j + k <= b.nbases && (nw & full) == 0u && ((bw >> 1) & (full >> 1)) == 0u) {
+                const uint32_t key = ((hiw & T.care) << k) | (low & T.care);
+                if (T.direct) {
+                    beg = __ldg(T.off + key);
+                    end = __ldg(T.off + key + 1);
+                } else if ((__ldg(T.bits + (key >> 5)) >> (key & 31)) & 1u) {
+                    uint32_t lo = 0, hi = T.nuniq;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (__ldg(T.keys + mid) < key) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo < T.nuniq && __ldg(T.keys + lo) == key) {
+                        beg = __ldg(T.off + lo);
+                        end = __ldg(T.off + lo + 1);
+                    }
+                }
+            }
+            // warp-synchronous walk over each lane's postings so hits can be
+            // compacted by ballot
+            while (__any_sync(0xffffffffu, beg < end)) {
+                bool hit = false;
+                uint32_t id = 0, contig = 0, pos = 0, mm = 0;
+                if (beg < end) {
+                    const uint32_t pv = __ldg(T.post + beg);
+                    beg++;
+                    const uint32_t e = pv >> 8, o = pv & 0xffu;
+                    const uint32_t meta = __ldg(qt.meta + e);
+                    const uint32_t L = meta_L(meta), W = meta_W(meta);
+                    if (o <= j) {
+                        const uint64_t p = j - o;
+                        if (p + L <= b.nbases && p + L >= static_cast<uint64_t>(b.halo) + 1) {
+                            ncand++;
+                            const uint64_t w0 = p >> 5;
+                            const uint32_t sh = static_cast<uint32_t>(p & 31);
+                            uint32_t x[WMAX + 1];
+                            uint32_t bnd = 0;
+                            mm = 0;
+                            uint4 cur = __ldg(b.words + w0);
+#pragma unroll
+                            for (int w = 0; w < WMAX; w++) {
+                                x[w] = 0;
+                                if (w < static_cast<int>(W)) {
+                                    const uint4 nx = __ldg(b.words + w0 + w + 1);
+                                    const uint32_t rh = __funnelshift_r(cur.x, nx.x, sh);
+                                    const uint32_t rl = __funnelshift_r(cur.y, nx.y, sh);
+                                    const uint32_t rn = __funnelshift_r(cur.z, nx.z, sh);
+                                    uint32_t rb = __funnelshift_r(cur.w, nx.w, sh);
+                                    if (w == 0) rb &= ~1u;
+                                    const uint4 q = __ldg(qt.words + static_cast<size_t>(e) * WMAX + w);
+                                    x[w] = ((rh ^ q.x) | (rl ^ q.y) | rn) & q.w;
+                                    mm += __popc(x[w]);
+                                    bnd |= rb & q.w;
+                                    cur = nx;
+                                }
+                            }
+                            x[WMAX] = 0;
+                            if (bnd == 0u && mm <= entry_s(meta, s)) {
+                                // error-free k-mer offsets from the mismatch mask
+                                const uint32_t last = L - k;  // largest offset
+                                uint32_t nseed = 0, first = 0xffffffffu;
+#pragma unroll
+                                for (int w = 0; w < WMAX; w++) {
+                                    if (w < static_cast<int>(W) && static_cast<uint32_t>(w) * 32 <= last) {
+                                        uint32_t c = 0;
+                                        for (uint32_t i = 0; i < k; i++)
+                                            if ((T.care >> i) & 1u) c |= __funnelshift_r(x[w], x[w + 1], i);
+                                        uint32_t valid = 0xffffffffu;
+                                        const uint32_t base = static_cast<uint32_t>(w) * 32;
+                                        if (last - base < 31) valid = (2u << (last - base)) - 1u;
+                                        uint32_t S = ~c & valid;
+                                        if (step > 1) {
+                                            uint32_t sm = 0;
+                                            for (uint32_t bi = 0; bi < 32; bi++)
+                                                if ((base + bi) % step == 0) sm |= 1u << bi;
+                                            S &= sm;
+                                        }
+                                        nseed += __popc(S);
+                                        if (first == 0xffffffffu && S) first = base + __ffs(S) - 1;
+                                    }
+                                }
+                                if (first == o && nseed >= __ldg(entry_minhits + e)) {
+                                    hit = true;
+                                    const DevPiece pc = b.pieces[find_piece(b.pieces, b.npieces, p)];
+                                    contig = pc.contig;
+                                    pos = static_cast<uint32_t>(pc.contig_off + (p - pc.start));
+                                    id = e;
+                                }
+                            }
+                        }
+                    }
+                }
+                wh.emit(sink, lane, hit, id >> 1, contig, pos, id & 1u, mm, nullptr);
+            }
+        }
+    }
+}
+
+}  // namespace seed
+}  // namespace ifa

@@ -1,0 +1,102 @@
+"""Many query sets against a device-resident reference (batching).
+
+Every set -- brute force, indexed or left to the autotuner, each with its
+own maxSubs -- must report exactly the oracle's hits for its queries, and
+the persistent (graph-replayed) run and the one-set-at-a-time run must agree
+tuple for tuple."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2607_27291_b300 as P
+import synth
+from gpu_helpers import tuples
+
+pytestmark = pytest.mark.gpu
+
+TRIALS = 20_000
+
+
+def _store(h, wl, append_bytes):
+    """Append the reference in chunks of append_bytes (a multiple of 32),
+    cutting contigs across appends."""
+    for a, b, pc in P.segment_pieces(wl.contig_len, append_bytes):
+        P.ifa_ref_append(h, wl.ref[a:b], pc)
+
+
+def _oracle_set(wl, queries, s, mode):
+    if mode == P.IFA_MODE_BRUTE:
+        return oracle.brute(queries, wl.ref, wl.contig_len, s)
+    plan = [oracle.choose_k(len(q), s, trials=TRIALS) for q in queries]
+    exh = [1 if st < 0 else 0 for st, _, _ in plan]
+    return oracle.indexed(queries, wl.ref, wl.contig_len, s, [p[1] for p in plan],
+                          [p[2] for p in plan], exh)
+
+
+def _shift(h, first):
+    h = h.copy()
+    h["query"] += first
+    return h
+
+
+@pytest.mark.parametrize("append_bytes", [1 << 16, 4096])
+def test_sets_match_oracle_and_kinds_agree(append_bytes):
+    wl = synth.small_workload(seed=71, n_queries=2, lmin=18, lmax=50, n_contigs=30, cmin=50,
+                              cmax=8000, plant_ks=[0, 1, 2, 3, 4, 5] * 3)
+    specs = [  # (n queries, maxSubs, mode)
+        (1, 0, P.IFA_MODE_BRUTE), (3, 4, P.IFA_MODE_INDEXED), (7, 2, P.IFA_MODE_AUTO),
+        (2, 6, P.IFA_MODE_BRUTE), (40, 3, P.IFA_MODE_AUTO), (12, 5, P.IFA_MODE_INDEXED),
+        (5, 1, P.IFA_MODE_AUTO),
+    ]
+    sets = []
+    for i, (n, s, mode) in enumerate(specs):
+        qs = synth.random_queries(n, 10 if i % 2 else 18, 50, 100 + i)
+        sets.append((qs, s, mode))
+    # the workload's planted queries go into two of the sets
+    sets[1] = ([wl.queries[0]] + sets[1][0][1:], sets[1][1], sets[1][2])
+    sets[4] = (sets[4][0][:-1] + [wl.queries[1]], sets[4][1], sets[4][2])
+    results = {}
+    for kind in (P.IFA_BATCH_PERSISTENT, P.IFA_BATCH_PER_SET):
+        h = P.ifa_create(hit_capacity=1 << 22, segment_bytes=1 << 20, minhits_trials=TRIALS)
+        try:
+            _store(h, wl, append_bytes)
+            firsts = []
+            for qs, s, mode in sets:
+                sid, first = P.ifa_set_add(h, qs, s, mode)
+                firsts.append(first)
+            res = P.ifa_batch_run(h, kind, len(sets))
+            hits, over = P.ifa_drain_hits(h)
+            assert not over
+            results[kind] = (P.sort_hits(hits), res, firsts)
+            # a second run of the same batch (graph replay) gives the same hits again
+            P.ifa_reset_results(h)
+            P.ifa_batch_run(h, kind, len(sets))
+            again, _ = P.ifa_drain_hits(h)
+            assert tuples(again) == tuples(hits)
+        finally:
+            P.ifa_destroy(h)
+    hp, rp, firsts = results[P.IFA_BATCH_PERSISTENT]
+    hs, rs, _ = results[P.IFA_BATCH_PER_SET]
+    assert tuples(hp) == tuples(hs)
+    assert rp["mode"].tolist() == rs["mode"].tolist()
+    assert rp["hits"].tolist() == rs["hits"].tolist()
+    expect = []
+    for (qs, s, mode), first, ran in zip(sets, firsts, rp["mode"]):
+        assert mode == P.IFA_MODE_AUTO or ran == mode
+        expect.extend(tuples(_shift(_oracle_set(wl, qs, s, int(ran)), first)))
+    assert tuples(hp) == sorted(expect)
+
+
+def test_store_errors():
+    h = P.ifa_create(hit_capacity=1024, segment_bytes=1 << 16)
+    try:
+        ref = np.frombuffer(b"ACGT" * 20, np.uint8).copy()
+        with pytest.raises(P.IfaError) as ei:
+            P.ifa_batch_run(h, P.IFA_BATCH_PERSISTENT, 0)
+        assert ei.value.status == P.IFA_ERR_BAD_STATE
+        P.ifa_ref_append(h, ref[:40], [(0, 0, 0, 40, False)])   # 40: not a multiple of 32
+        with pytest.raises(P.IfaError) as ei:
+            P.ifa_ref_append(h, ref[:32], [(0, 40, 0, 32, True)])
+        assert ei.value.status == P.IFA_ERR_INVALID_ARG
+    finally:
+        P.ifa_destroy(h)
