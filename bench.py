@@ -49,6 +49,14 @@ def parse():
     ap.add_argument("--total", type=float, default=4e9, help="reference bases (default 4 Gbp)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "serving"],
+                    help="sweep: the 4 Gbp maxSubs sweep (default); batched: many query sets "
+                         "in one persistent launch vs one launch per set; serving: Poisson "
+                         "arrivals with continuous batching")
+    ap.add_argument("--sets", type=int, default=256, help="batched: number of query sets")
+    ap.add_argument("--rate", type=float, default=50.0, help="serving: arrivals per second")
+    ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
+    ap.add_argument("--slices", type=int, default=16, help="serving: slices per cycle")
     return ap.parse_args()
 
 
@@ -145,19 +153,27 @@ def measured_peaks():
         return {}
 
 
+def kernel_source_digest():
+    """sha256 (first 16 hex digits) of the scan kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("scan_brute.cu", "scan_brute.cuh", "hits.cuh", "ifa_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2607_27291_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_record():
     """DRAM bytes per scan launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "scan_brute_4gbp_traffic.txt")
-    src = os.path.join(ROOT, "paper_2607_27291_b300", "csrc", "scan_brute.cu")
     try:
         kv = {}
         for line in open(path):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = kernel_source_digest()
         if kv.get("kernel_source_sha256_16") != digest:
             return None
         return float(kv["dram_bytes_per_launch"])
@@ -312,7 +328,8 @@ def run_ours(args, rank, world):
         del ref_dev
         torch.cuda.empty_cache()
         ref_pin = torch.from_numpy(wl.ref).pin_memory()
-        one_pass(SUBS[0], ref_pin, True)  # warm the pinned path
+        for s in SUBS:  # warm the pinned path and size the pinned hit buffer
+            one_pass(s, ref_pin, True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         d2h = 0
@@ -368,8 +385,131 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- many sets
+
+def _store_from_device(P, h, ref_dev, lens):
+    for a, b, pc in P.segment_pieces(lens, 256 << 20):
+        P.ifa_ref_append(h, ref_dev[a:b], pc)
+
+
+def run_batched(args):
+    """Query sets of uneven sizes against a device-resident reference: one
+    persistent graph-replayed launch vs one launch per set."""
+    import torch
+    import paper_2607_27291_b300 as P
+    import synth
+    total = int(args.total if args.total != 4e9 else 16e9)
+    t = time.perf_counter()
+    ref, lens, sets = synth.workload_sets_16gbp(total=total, n_sets=args.sets)
+    t_gen = time.perf_counter() - t
+    ref_dev = torch.from_numpy(ref).cuda()
+    h = P.ifa_create(count_only=1, segment_bytes=256 << 20, minhits_trials=100_000, minhits_seed=1)
+    _store_from_device(P, h, ref_dev, lens)
+    del ref_dev
+    torch.cuda.empty_cache()
+    for qs, s in sets:
+        P.ifa_set_add(h, qs, s, P.IFA_MODE_AUTO)
+    nq = np.array([len(qs) for qs, _ in sets])
+    work = float(nq.sum()) * ref.size          # bp x queries per run
+    t = time.perf_counter()
+    res = P.ifa_batch_run(h, P.IFA_BATCH_PERSISTENT, len(sets))   # calibrates, plans, captures
+    t_plan = time.perf_counter() - t
+    runs = []
+    for _ in range(max(1, args.steps)):
+        P.ifa_reset_results(h)
+        res = P.ifa_batch_run(h, P.IFA_BATCH_PERSISTENT, len(sets))
+        runs.append(float(res["done_ms"].max()))
+    dig_p, cnt_p = P.ifa_get_digest(h, int(nq.sum()))
+    P.ifa_reset_results(h)
+    res_s = P.ifa_batch_run(h, P.IFA_BATCH_PER_SET, len(sets))
+    dig_s, cnt_s = P.ifa_get_digest(h, int(nq.sum()))
+    per_set_ms = float(res_s["done_ms"].max())
+    P.ifa_destroy(h)
+    pers_ms = float(np.median(runs))
+    line = {
+        "workload": "batched", "metric": "aggregate Gbp x queries/s", "unit": "Gbp*queries/s",
+        "value": work / 1e9 / (pers_ms * 1e-3), "per_set_value": work / 1e9 / (per_set_ms * 1e-3),
+        "persistent_ms": pers_ms, "per_set_ms": per_set_ms,
+        "latency_ms": {"persistent": {"p50": pers_ms, "p99": pers_ms},
+                       "per_set": {"p50": float(np.percentile(res_s["done_ms"], 50)),
+                                   "p99": float(np.percentile(res_s["done_ms"], 99))}},
+        "same_results": bool(dig_p == dig_s and (cnt_p == cnt_s).all()),
+        "modes": {"brute_sets": int((res["mode"] == P.IFA_MODE_BRUTE).sum()),
+                  "indexed_sets": int((res["mode"] == P.IFA_MODE_INDEXED).sum())},
+        "hits": int(dig_p[0]),
+        "config": {"reference_bases": int(ref.size), "contigs": int(lens.size), "sets": len(sets),
+                   "queries": int(nq.sum()), "set_sizes": "log-uniform 1-5000",
+                   "lengths": "18-50", "max_subs": "0-12 per set", "gc": "0.30-0.65 per contig",
+                   "generation_s": round(t_gen, 1), "plan_s": round(t_plan, 1)},
+        "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Poisson arrivals of query sets served by continuous batching over a
+    device-resident reference."""
+    import torch
+    import paper_2607_27291_b300 as P
+    import synth
+    total = int(args.total)
+    ref, lens, reqs = synth.workload_serving(total, args.rate, args.duration)
+    ref_dev = torch.from_numpy(ref).cuda()
+    h = P.ifa_create(hit_capacity=1024, segment_bytes=256 << 20, minhits_trials=100_000, minhits_seed=1)
+    _store_from_device(P, h, ref_dev, lens)
+    del ref_dev
+    torch.cuda.empty_cache()
+    # warm the planner's MinHits bins and the kernels with one request
+    P.ifa_serve_start(h, args.slices, 64 << 30, 1 << 20)
+    P.ifa_serve_submit(h, reqs[0][1], reqs[0][2], P.IFA_MODE_AUTO)
+    while P.ifa_serve_step(h)[0]:
+        pass
+    P.ifa_serve_start(h, args.slices, 64 << 30, 1 << 20)
+    ids = []
+    nxt = 0
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt][0] <= now:
+            ids.append(P.ifa_serve_submit(h, reqs[nxt][1], reqs[nxt][2], P.IFA_MODE_AUTO))
+            nxt += 1
+        active, _ = P.ifa_serve_step(h)
+        steps += 1
+        if nxt == len(reqs) and active == 0:
+            infos = [P.ifa_serve_poll(h, r) for r in ids]
+            if all(i["state"] >= 2 for i in infos):
+                break
+        if nxt < len(reqs) and active == 0:
+            time.sleep(max(0.0, min(0.01, reqs[nxt][0] - now)))
+    wall = time.perf_counter() - t0
+    _, qbases = P.ifa_serve_stats(h)
+    lat = np.array([i["done_s"] - i["submit_s"] for i in infos])
+    queue = np.array([i["admit_s"] - i["submit_s"] for i in infos])
+    P.ifa_serve_stop(h)
+    P.ifa_destroy(h)
+    line = {
+        "workload": "serving", "metric": "query-base comparisons/s (nominal) and request latency",
+        "unit": "query-base comparisons/s", "value": qbases / wall,
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "p999": float(np.percentile(lat, 99.9))},
+        "queue_s": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
+        "requests": len(reqs), "wall_s": wall, "steps": steps,
+        "config": {"reference_bases": int(ref.size), "rate_per_s": args.rate,
+                   "duration_s": args.duration, "slices": args.slices,
+                   "set_sizes": "log-uniform 1-2000", "lengths": "18-50", "max_subs": "0-8",
+                   "gc": 0.45, "n_frac": 0.0005, "mode": "auto by query count"},
+        "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     rank, world = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -274,6 +274,59 @@ typedef struct {
  * Errors: BAD_STATE (empty store or no sets), OOM, CUDA. */
 ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per_set);
 
+/* ---- Serving: continuous batching over the store -------------------
+ *
+ * Requests (query sets) arrive at any time.  The store is cut into
+ * n_slices slices scanned cyclically, one per ifa_serve_step: at each slice
+ * boundary the waiting requests that fit the HBM budget are admitted (in
+ * arrival order; one request is always admitted when none is active), then
+ * one persistent launch scans the slice for every active request at once.
+ * A request is complete once every slice has been scanned for it (one full
+ * cycle from its admission); its hits wait in its own device ring until
+ * ifa_serve_drain.  A request's results do not depend on the others
+ * active with it.  Hit query ids are relative to the request. */
+
+typedef struct {
+    uint32_t state;        /* 0 queued, 1 active, 2 complete, 3 drained */
+    uint32_t mode;         /* IFA_MODE_BRUTE or IFA_MODE_INDEXED as run */
+    uint32_t queries;
+    uint32_t slices_done;
+    uint64_t hits;         /* hits found (may exceed the ring) */
+    uint64_t overflowed;   /* 1 when the ring dropped hits */
+    double submit_s;       /* seconds since ifa_serve_start */
+    double admit_s;
+    double done_s;
+    ifa_digest digest;     /* over the request's hits, request-relative ids */
+} ifa_request_info;
+
+/* Start serving over the store: n_slices slices, an HBM budget (bytes) for
+ * admitted requests' rings and plan entries, ring_hits hits per request.
+ * BAD_STATE when the store is empty.  Ends any previous serving session. */
+ifa_status ifa_serve_start(ifa_handle *h, uint32_t n_slices, uint64_t hbm_budget_bytes, uint64_t ring_hits);
+
+/* Queue one request; IFA_MODE_AUTO picks indexed from auto_crossover
+ * queries on (the paper's rule by query count). *request_id may be NULL. */
+ifa_status ifa_serve_submit(ifa_handle *h, const uint8_t *const *seqs, const uint32_t *lens, uint32_t n,
+                            uint32_t max_subs, ifa_mode mode, uint32_t *request_id);
+
+/* Admit what fits, scan the next slice for all active requests, retire
+ * the ones that are complete.  Waits for the slice.  *n_active and
+ * *n_completed (may be NULL) receive the counts after the step. */
+ifa_status ifa_serve_step(ifa_handle *h, uint32_t *n_active, uint32_t *n_completed);
+
+/* State, timing and digest of one request. */
+ifa_status ifa_serve_poll(ifa_handle *h, uint32_t request_id, ifa_request_info *info);
+
+/* Copy a complete request's hits (up to cap) to out and free its ring;
+ * HIT_OVERFLOW (with the data) when its ring dropped hits. */
+ifa_status ifa_serve_drain(ifa_handle *h, uint32_t request_id, ifa_hit *out, uint64_t cap, uint64_t *n_out);
+
+/* Slices scanned and nominal query-base comparisons done so far. */
+ifa_status ifa_serve_stats(ifa_handle *h, uint64_t *slices_run, double *query_bases);
+
+/* End serving and free every request's ring. */
+ifa_status ifa_serve_stop(ifa_handle *h);
+
 /* Brute-force scan of one reference chunk that allocates no memory.
  *
  * The paper has no counterpart: this entry point exists for callers that

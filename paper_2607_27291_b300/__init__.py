@@ -90,6 +90,14 @@ _SYMBOLS = {
     "ifa_set_add": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.c_uint32,
                               C.c_uint32, C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "ifa_batch_run": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "ifa_serve_start": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint64, C.c_uint64]),
+    "ifa_serve_submit": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.c_uint32,
+                                   C.c_uint32, C.c_int, C.POINTER(C.c_uint32)]),
+    "ifa_serve_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+    "ifa_serve_poll": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p]),
+    "ifa_serve_drain": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64)]),
+    "ifa_serve_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
+    "ifa_serve_stop": (C.c_int, [C.c_void_p]),
     "ifa_scan_brute_noalloc": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
                                          C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32,
                                          C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p,
@@ -340,6 +348,61 @@ def ifa_batch_run(h, kind: int, n_sets: int) -> np.ndarray:
     out = np.zeros(max(1, n_sets), SET_RESULT_DTYPE)
     _check(lib().ifa_batch_run(h, int(kind), out.ctypes.data), h)
     return out[:n_sets]
+
+
+class ifa_request_info(C.Structure):
+    _fields_ = [("state", C.c_uint32), ("mode", C.c_uint32), ("queries", C.c_uint32),
+                ("slices_done", C.c_uint32), ("hits", C.c_uint64), ("overflowed", C.c_uint64),
+                ("submit_s", C.c_double), ("admit_s", C.c_double), ("done_s", C.c_double),
+                ("digest", ifa_digest)]
+
+
+def ifa_serve_start(h, n_slices: int, hbm_budget_bytes: int, ring_hits: int) -> None:
+    _check(lib().ifa_serve_start(h, n_slices, hbm_budget_bytes, ring_hits), h)
+
+
+def ifa_serve_submit(h, queries: Sequence[bytes], max_subs: int, mode: int = IFA_MODE_AUTO) -> int:
+    n = len(queries)
+    bufs = [C.create_string_buffer(bytes(q), len(q)) for q in queries]
+    ptrs = (C.c_void_p * max(1, n))(*[C.cast(b, C.c_void_p) for b in bufs])
+    lens = (C.c_uint32 * max(1, n))(*[len(q) for q in queries])
+    rid = C.c_uint32()
+    _check(lib().ifa_serve_submit(h, ptrs, lens, n, int(max_subs), int(mode), C.byref(rid)), h)
+    return rid.value
+
+
+def ifa_serve_step(h) -> Tuple[int, int]:
+    a = C.c_uint32()
+    d = C.c_uint32()
+    _check(lib().ifa_serve_step(h, C.byref(a), C.byref(d)), h)
+    return a.value, d.value
+
+
+def ifa_serve_poll(h, rid: int) -> dict:
+    info = ifa_request_info()
+    _check(lib().ifa_serve_poll(h, rid, C.byref(info)), h)
+    out = {f: getattr(info, f) for f, _ in ifa_request_info._fields_ if f != "digest"}
+    out["digest"] = (int(info.digest.count), int(info.digest.sum), int(info.digest.xr))
+    return out
+
+
+def ifa_serve_drain(h, rid: int, cap: int) -> Tuple[np.ndarray, bool]:
+    out = np.zeros(max(1, cap), HIT_DTYPE)
+    n = C.c_uint64()
+    st = _check(lib().ifa_serve_drain(h, rid, out.ctypes.data, cap, C.byref(n)), h,
+                allow=(IFA_OK, IFA_ERR_HIT_OVERFLOW))
+    return out[:n.value], st == IFA_ERR_HIT_OVERFLOW
+
+
+def ifa_serve_stats(h) -> Tuple[int, float]:
+    n = C.c_uint64()
+    qb = C.c_double()
+    _check(lib().ifa_serve_stats(h, C.byref(n), C.byref(qb)), h)
+    return n.value, qb.value
+
+
+def ifa_serve_stop(h) -> None:
+    _check(lib().ifa_serve_stop(h), h)
 
 
 def ifa_scan_brute_noalloc(device: int, queries: Sequence[bytes], ref_ptr: int, length: int,

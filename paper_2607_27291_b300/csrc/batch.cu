@@ -76,8 +76,6 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
     int loaded = -1;
     Smem m{};
     uint32_t nent = 0, e0 = 0, lmin = 0, lmax = 0;
-    const uint64_t nbblk = (b.nbases + 32 * kWin - 1) / (32 * kWin);
-    const uint64_t nsblk = (b.nbases + 31) >> 5;
     const uint32_t n_seed = w.n_items - w.n_brute_items;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(w.queue, 1u);
@@ -85,8 +83,8 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
         const uint32_t item = s_item;
         if (item >= w.n_items) break;
         if (item < n_seed) {
-            const uint64_t lo = static_cast<uint64_t>(item) * w.tile_sblocks;
-            const uint64_t hi = lo + w.tile_sblocks < nsblk ? lo + w.tile_sblocks : nsblk;
+            const uint64_t lo = w.s_block0 + static_cast<uint64_t>(item) * w.tile_sblocks;
+            const uint64_t hi = lo + w.tile_sblocks < w.s_block_end ? lo + w.tile_sblocks : w.s_block_end;
             seed::seed_blocks<WMAX>(b, ft, w.tabs, w.emh, w.step, kSPerEntry, sink, wh, lo + warp, hi,
                                     kBWarps, lane, ncand);
         } else {
@@ -105,8 +103,8 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
                 nent = e1 - e0;
                 loaded = static_cast<int>(chunk);
             }
-            const uint64_t lo = static_cast<uint64_t>(tile) * w.tile_bblocks;
-            const uint64_t hi = lo + w.tile_bblocks < nbblk ? lo + w.tile_bblocks : nbblk;
+            const uint64_t lo = w.b_block0 + static_cast<uint64_t>(tile) * w.tile_bblocks;
+            const uint64_t hi = lo + w.tile_bblocks < w.b_block_end ? lo + w.tile_bblocks : w.b_block_end;
             scan_blocks<WMAX>(b, bt, m, nent, s_nF, s_nM, e0, kSPerEntry, lmin, lmax, sink, wh, stage[warp], mul,
                               lo + warp, hi, kBWarps, lane);
         }
@@ -152,6 +150,19 @@ int batch_grid(uint32_t wmax) {
     if (e != cudaSuccess || per < 1) per = 1;
     return sms * per;
 }
+
+}  // namespace
+
+namespace ifa {
+cudaError_t launch_batch_kernel(uint32_t wmax, const Batch &b, const BatchWork &w, const QueryTable &bt,
+                                const QueryTable &ft, const HitSink &sink, int grid, size_t smem,
+                                cudaStream_t st) {
+    return launch_batch(wmax, b, w, bt, ft, sink, grid, smem, st);
+}
+int batch_kernel_grid(uint32_t wmax) { return batch_grid(wmax); }
+}  // namespace ifa
+
+namespace {
 
 Batch store_batch(const BatchState &B) {
     Batch b;
@@ -405,6 +416,10 @@ ifa_status build_plan(ifa_handle *h) {
     // tiles: about 16 items per CTA slot over all chunks, at least 32 blocks per tile
     const uint64_t want_b = static_cast<uint64_t>(16) * B.grid;
     const uint64_t tiles_per_chunk = W.nchunks ? std::max<uint64_t>(1, want_b / W.nchunks) : 1;
+    W.b_block0 = 0;
+    W.b_block_end = nbblk;
+    W.s_block0 = 0;
+    W.s_block_end = nsblk;
     W.tile_bblocks = std::max<uint64_t>(32, (nbblk + tiles_per_chunk - 1) / tiles_per_chunk);
     W.n_btiles = static_cast<uint32_t>((nbblk + W.tile_bblocks - 1) / W.tile_bblocks);
     W.tile_sblocks = std::max<uint64_t>(64, (nsblk + 8 * B.grid - 1) / (8 * B.grid));

@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <memory>
+#include <string>
 #include <vector>
 
 #include "ifa_internal.cuh"
@@ -31,7 +32,9 @@ struct BatchWork {
     uint32_t step;
     const uint4 *qwords;
     const uint32_t *qmeta;
-    // tiles
+    // tiles over block ranges [b_block0, b_block_end) and [s_block0, s_block_end)
+    uint64_t b_block0, b_block_end;  // blocks of 128 windows
+    uint64_t s_block0, s_block_end;  // blocks of 32 positions
     uint64_t tile_bblocks;   // brute tile, in blocks of 128 windows
     uint64_t tile_sblocks;   // seed tile, in blocks of 32 positions
     uint32_t n_btiles, n_stiles;
@@ -80,6 +83,55 @@ struct BatchState {
     double brute_entry_bases_per_s = 0;  // entry x base evaluations per second
     double seed_pos_per_s = 0;           // positions x tables per second
     double cand_per_s = 0;               // verified candidates per second
+};
+
+}  // namespace ifa
+
+namespace ifa {
+
+// One served request (a query set) and its device hit ring.
+struct Request {
+    std::vector<std::string> qs;
+    uint32_t s = 0;
+    ifa_mode mode = IFA_MODE_BRUTE;  // as run (AUTO resolved at submission)
+    int state = 0;                   // 0 queued, 1 active, 2 done, 3 drained
+    double t_submit = 0, t_admit = 0, t_done = 0;  // seconds since ifa_serve_start
+    uint32_t slices_done = 0;
+    ifa_hit *d_ring = nullptr;
+    unsigned long long *d_counters = nullptr;  // head, overflow, count, sum, xor
+    uint64_t cap = 0;
+    uint64_t bytes = 0;                        // charged to the budget
+    unsigned long long final_counters[5] = {0, 0, 0, 0, 0};
+};
+
+// Continuous-batching serving over the reference store.
+struct ServeState {
+    bool on = false;
+    uint32_t n_slices = 1;
+    uint64_t budget = 0, used = 0;
+    uint64_t ring_cap = 0;
+    double t0 = 0;
+    std::vector<Request> reqs;
+    std::vector<uint32_t> pending;   // FIFO of request ids
+    std::vector<uint32_t> active;    // request ids being scanned
+    uint32_t slice = 0;
+    bool dirty = true;
+    // plan of the active set
+    std::vector<void *> allocs;
+    uint32_t wmax = 1;
+    uint32_t nq = 0;
+    QueryTable ft{};
+    QueryTable bt{};
+    uint32_t b_entries = 0;
+    std::vector<uint32_t> chunk_e0;
+    IndexedState merged;
+    BatchWork work{};
+    HitSink sink{};
+    int grid = 0;
+    unsigned int *d_queue = nullptr;
+    unsigned long long *d_cand = nullptr;
+    uint64_t slices_run = 0;
+    double scanned_query_bases = 0;   // nominal comparisons done by completed slices
 };
 
 }  // namespace ifa

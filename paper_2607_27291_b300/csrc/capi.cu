@@ -290,6 +290,7 @@ void ifa_destroy(ifa_handle *h) {
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
     if (h->stream) cudaStreamSynchronize(h->stream);
     h->idx.release();
+    ifa::serve_release(h);
     ifa::batch_release(h);
     for (int i = 0; i < 2; i++) {
         cudaFree(h->d_seg[i]);

@@ -84,6 +84,7 @@ struct ifa_handle {
     // per-query maxSubs of queries added by ifa_set_add (0 for ifa_load_queries)
     std::vector<uint32_t> qs_s;
     BatchState batch;
+    ifa::ServeState serve;
 };
 
 
@@ -92,4 +93,12 @@ namespace ifa {
 ifa_status upload_queries(ifa_handle *h);
 // Free the multi-set store and plan.
 void batch_release(ifa_handle *h);
+// The persistent multi-set kernel (batch.cu), for the serving loop.
+cudaError_t launch_batch_kernel(uint32_t wmax, const Batch &b, const BatchWork &w, const QueryTable &bt,
+                                const QueryTable &ft, const HitSink &sink, int grid, size_t smem,
+                                cudaStream_t st);
+int batch_kernel_grid(uint32_t wmax);
+void encode_entry(const std::string &q, bool rc, uint32_t wmax, uint32_t s_e, uint4 *out, uint32_t *meta);
+// Free the serving state.
+void serve_release(ifa_handle *h);
 }  // namespace ifa

@@ -52,6 +52,33 @@ struct WarpHits {
         const uint32_t ballot = __ballot_sync(0xffffffffu, hit);
         if (ballot == 0) return;
         const uint32_t cnt = __popc(ballot);
+        if (s.q2r) {
+            // per-request rings: each hit goes straight to its request's ring
+            if (hit) {
+                const RingDesc R = s.rings[s.q2r[q]];
+                const uint32_t rq = q - R.qfirst;
+                const uint64_t v = hit_digest_item(rq, contig, pos, strand, mm);
+                atomicAdd(&R.counters[2], 1ull);
+                atomicAdd(&R.counters[3], static_cast<unsigned long long>(v));
+                atomicXor(&R.counters[4], static_cast<unsigned long long>(v));
+                const unsigned long long idx = atomicAdd(&R.counters[0], 1ull);
+                if (idx < R.cap) {
+                    ifa_hit h;
+                    h.query = rq;
+                    h.contig = contig;
+                    h.pos = pos;
+                    h.strand = static_cast<uint8_t>(strand);
+                    h.mismatches = static_cast<uint8_t>(mm > 255 ? 255 : mm);
+                    h.reserved = 0;
+                    R.ring[idx] = h;
+                } else {
+                    R.counters[1] = 1ull;
+                }
+                if (!entry_count) atomicAdd(&s.qcount[q], 1ull);
+            }
+            if (entry_count && lane == static_cast<uint32_t>(__ffs(ballot) - 1)) atomicAdd(entry_count, cnt);
+            return;
+        }
         if (hit) {
             const uint64_t v = hit_digest_item(q, contig, pos, strand, mm);
             dcount += 1;

@@ -43,6 +43,16 @@ struct DevPiece {
     uint32_t pad;
 };
 
+// One request's own hit ring (serving): counters = {head, overflow, digest
+// count, digest sum, digest xor}; hits carry query ids relative to qfirst.
+struct RingDesc {
+    ifa_hit *ring;
+    unsigned long long *counters;
+    unsigned long long cap;
+    uint32_t qfirst;
+    uint32_t pad;
+};
+
 struct HitSink {
     ifa_hit *ring;                 // hit buffer (may be null in count-only mode)
     unsigned long long *head;      // total hits claimed (can exceed capacity)
@@ -51,6 +61,9 @@ struct HitSink {
     unsigned long long *qcount;    // per query
     uint32_t *overflow;            // set to 1 when a hit is dropped
     int count_only;
+    // serving: query -> request slot and the slots' rings (null: one shared ring)
+    const uint32_t *q2r = nullptr;
+    const RingDesc *rings = nullptr;
 };
 
 struct QueryTable {

@@ -22,6 +22,8 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 
 #include "hits.cuh"
 #include "indexed.cuh"
@@ -152,10 +154,62 @@ uint64_t IndexedState::candidates_host(cudaStream_t st) const {
     return v;
 }
 
+namespace {
+
+// Thresholds are a pure function of the bin and the Monte Carlo settings, so
+// they are remembered for the life of the process (query sets that come and
+// go reuse the same bins).
+struct BinKey {
+    uint32_t L, s, k, step, mask, clips, num, den, trials;
+    uint64_t seed;
+    bool operator<(const BinKey &o) const {
+        return std::tie(L, s, k, step, mask, clips, num, den, trials, seed) <
+               std::tie(o.L, o.s, o.k, o.step, o.mask, o.clips, o.num, o.den, o.trials, o.seed);
+    }
+};
+std::mutex g_bin_mutex;
+std::map<BinKey, uint32_t> g_bin_cache;
+
+}  // namespace
+
 ifa_status minhits_device(const uint32_t *L, const uint32_t *subs, const uint32_t *k, uint32_t n,
                           uint32_t step, uint32_t mask_w, uint32_t max_clips, uint32_t num, uint32_t den,
                           uint32_t trials, uint64_t seed, uint32_t *out, cudaStream_t st,
                           uint32_t stride, std::string &err) {
+    if (n == 0) return IFA_OK;
+    // answer remembered bins, compute the rest on the device
+    std::vector<uint32_t> mL, mS, mK, where;
+    {
+        std::lock_guard<std::mutex> lock(g_bin_mutex);
+        for (uint32_t i = 0; i < n; i++) {
+            auto it = g_bin_cache.find(BinKey{L[i], subs[i], k[i], step, mask_w, max_clips, num, den, trials, seed});
+            if (it != g_bin_cache.end()) {
+                out[i] = it->second;
+            } else {
+                mL.push_back(L[i]);
+                mS.push_back(subs[i]);
+                mK.push_back(k[i]);
+                where.push_back(i);
+            }
+        }
+    }
+    if (mL.empty()) return IFA_OK;
+    std::vector<uint32_t> mo(mL.size());
+    ifa_status r = minhits_compute(mL.data(), mS.data(), mK.data(), static_cast<uint32_t>(mL.size()), step, mask_w,
+                                   max_clips, num, den, trials, seed, mo.data(), st, stride, err);
+    if (r != IFA_OK) return r;
+    std::lock_guard<std::mutex> lock(g_bin_mutex);
+    for (size_t j = 0; j < mL.size(); j++) {
+        out[where[j]] = mo[j];
+        g_bin_cache[BinKey{mL[j], mS[j], mK[j], step, mask_w, max_clips, num, den, trials, seed}] = mo[j];
+    }
+    return IFA_OK;
+}
+
+ifa_status minhits_compute(const uint32_t *L, const uint32_t *subs, const uint32_t *k, uint32_t n,
+                           uint32_t step, uint32_t mask_w, uint32_t max_clips, uint32_t num, uint32_t den,
+                           uint32_t trials, uint64_t seed, uint32_t *out, cudaStream_t st,
+                           uint32_t stride, std::string &err) {
     if (n == 0) return IFA_OK;
     uint32_t *dL = nullptr, *dS = nullptr, *dK = nullptr, *dH = nullptr, *dO = nullptr;
     const size_t nb = static_cast<size_t>(n) * sizeof(uint32_t);

@@ -70,6 +70,11 @@ struct IndexedState {
     uint64_t candidates_host(cudaStream_t st) const;
 };
 
+// MinHits thresholds on the device (remembered per bin for the process).
+ifa_status minhits_compute(const uint32_t *L, const uint32_t *subs, const uint32_t *k, uint32_t n,
+                           uint32_t step, uint32_t mask_w, uint32_t max_clips, uint32_t num,
+                           uint32_t den, uint32_t trials, uint64_t seed, uint32_t *out,
+                           cudaStream_t st, uint32_t hist_stride, std::string &err);
 ifa_status minhits_device(const uint32_t *L, const uint32_t *subs, const uint32_t *k, uint32_t n,
                           uint32_t step, uint32_t mask_w, uint32_t max_clips, uint32_t num,
                           uint32_t den, uint32_t trials, uint64_t seed, uint32_t *out,

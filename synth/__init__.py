@@ -381,3 +381,78 @@ def _plant_queries(ref, starts, lens, queries, qids, k, seed, occ) -> List[Plant
             out.append(Plant(qi, ci, p, t, k_eff))
             break
     return out
+
+
+# ------------------------------------------------- many sets / serving inputs
+
+def per_contig_reference(lens: np.ndarray, gc_lo: float, gc_hi: float, seed: int,
+                         n_frac: float = 0.0, threads: Optional[int] = None):
+    """Reference whose contig i has its own GC drawn uniform in [gc_lo, gc_hi]
+    (a fixed GC when gc_lo == gc_hi); each contig comes from its own
+    generator, so contigs can be regenerated alone.  Returns (ref, gc)."""
+    rng = _rng(seed, _S_GC)
+    gc = rng.uniform(gc_lo, gc_hi, size=len(lens)) if gc_hi > gc_lo else np.full(len(lens), gc_lo)
+    starts = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    ref = np.empty(int(starts[-1]), dtype=np.uint8)
+
+    def fill(i):
+        r = _rng(seed, _S_BASES, 1_000_000 + i).random(int(lens[i]), dtype=np.float32)
+        g = gc[i]
+        code = (r >= np.float32((1 - g) / 2)).astype(np.uint8)
+        code += r >= np.float32(0.5)
+        code += r >= np.float32((1 + g) / 2)
+        ref[starts[i]:starts[i + 1]] = _ACGT[code]
+
+    threads = threads or min(32, os.cpu_count() or 1)
+    with _cf.ThreadPoolExecutor(threads) as ex:
+        list(ex.map(fill, range(len(lens))))
+    if n_frac > 0:
+        add_n_runs(ref, n_frac, seed, _Occupied())
+    return ref, gc
+
+
+def log_uniform_int(rng, lo: int, hi: int, size: int) -> np.ndarray:
+    return np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1), size=size))).astype(np.int64)
+
+
+def query_sets(n_sets: int, size_lo: int, size_hi: int, lmin: int, lmax: int, smax: int,
+               seed: int):
+    """n_sets sets of uniform-ACGT queries: sizes log-uniform in
+    [size_lo, size_hi], lengths uniform in [lmin, lmax], each set's maxSubs
+    uniform in {0..smax}.  Returns [(queries, max_subs)]."""
+    rng = _rng(seed, _S_QUERIES, 7)
+    sizes = log_uniform_int(rng, size_lo, size_hi, n_sets)
+    subs = rng.integers(0, smax + 1, size=n_sets)
+    out = []
+    for i in range(n_sets):
+        out.append((random_queries(int(sizes[i]), lmin, lmax, seed * 100_000 + i), int(subs[i])))
+    return out
+
+
+def workload_sets_16gbp(total: int = 16_000_000_000, n_sets: int = 256):
+    """Query sets of log-uniform sizes 1-5000, lengths 18-50 bp, maxSubs
+    0-12, against a reference of log-uniform contigs 1 kbp - 10 Mbp with
+    per-contig GC uniform in [0.30, 0.65].  Returns (ref, lens, sets)."""
+    seed = 4
+    lens = contig_lengths(total, 1000, 10_000_000, "loguniform", seed)
+    ref, _ = per_contig_reference(lens, 0.30, 0.65, seed)
+    return ref, lens, query_sets(n_sets, 1, 5000, 18, 50, 12, seed)
+
+
+def workload_serving(total: int, rate: float, duration: float, seed: int = 5):
+    """Poisson arrivals (mean `rate` per second over `duration` seconds) of
+    query sets of log-uniform sizes 1-2000, lengths 18-50 bp, maxSubs 0-8,
+    against a reference (GC 45%, 0.05% N, log-uniform contigs 1 kbp -
+    10 Mbp).  Returns (ref, lens, [(arrival_s, queries, max_subs)])."""
+    lens = contig_lengths(total, 1000, 10_000_000, "loguniform", seed)
+    ref, _ = per_contig_reference(lens, 0.45, 0.45, seed, n_frac=0.0005)
+    rng = _rng(seed, _S_QUERIES, 8)
+    t = 0.0
+    arrivals = []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            break
+        arrivals.append(t)
+    sets = query_sets(len(arrivals), 1, 2000, 18, 50, 8, seed)
+    return ref, lens, [(a, qs, s) for a, (qs, s) in zip(arrivals, sets)]

@@ -55,15 +55,18 @@ def test_sets_match_oracle_and_kinds_agree(append_bytes):
     # the workload's planted queries go into two of the sets
     sets[1] = ([wl.queries[0]] + sets[1][0][1:], sets[1][1], sets[1][2])
     sets[4] = (sets[4][0][:-1] + [wl.queries[1]], sets[4][1], sets[4][2])
+    # both kinds on one handle: the autotuner's choices (from measured rates)
+    # are made once and shared
     results = {}
-    for kind in (P.IFA_BATCH_PERSISTENT, P.IFA_BATCH_PER_SET):
-        h = P.ifa_create(hit_capacity=1 << 22, segment_bytes=1 << 20, minhits_trials=TRIALS)
-        try:
-            _store(h, wl, append_bytes)
-            firsts = []
-            for qs, s, mode in sets:
-                sid, first = P.ifa_set_add(h, qs, s, mode)
-                firsts.append(first)
+    h = P.ifa_create(hit_capacity=1 << 22, segment_bytes=1 << 20, minhits_trials=TRIALS)
+    try:
+        _store(h, wl, append_bytes)
+        firsts = []
+        for qs, s, mode in sets:
+            sid, first = P.ifa_set_add(h, qs, s, mode)
+            firsts.append(first)
+        for kind in (P.IFA_BATCH_PERSISTENT, P.IFA_BATCH_PER_SET):
+            P.ifa_reset_results(h)
             res = P.ifa_batch_run(h, kind, len(sets))
             hits, over = P.ifa_drain_hits(h)
             assert not over
@@ -73,8 +76,8 @@ def test_sets_match_oracle_and_kinds_agree(append_bytes):
             P.ifa_batch_run(h, kind, len(sets))
             again, _ = P.ifa_drain_hits(h)
             assert tuples(again) == tuples(hits)
-        finally:
-            P.ifa_destroy(h)
+    finally:
+        P.ifa_destroy(h)
     hp, rp, firsts = results[P.IFA_BATCH_PERSISTENT]
     hs, rs, _ = results[P.IFA_BATCH_PER_SET]
     assert tuples(hp) == tuples(hs)
