@@ -85,9 +85,16 @@ def allmax(x, world):
     return float(t.item())
 
 
-def make_workload(total):
+def shard_seed(rank):
+    """Reference seed of a rank's shard: rank 0 scans the 4 Gbp reference of
+    the single-GPU run, rank r > 0 a reference drawn from its own seed (weak
+    scaling: the N ranks together scan N independent shards)."""
+    return 2 + 1000 * rank
+
+
+def make_workload(total, rank=0):
     import synth
-    return synth.workload_4gbp(total=int(total))
+    return synth.workload_4gbp(total=int(total), seed=shard_seed(rank))
 
 
 def nominal_work(wl, contig_sel=None):
@@ -241,7 +248,7 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     t_gen = time.perf_counter()
-    wl = make_workload(args.total)
+    wl = make_workload(args.total, rank)
     t_gen = time.perf_counter() - t_gen
     segs = list(P.segment_pieces(wl.contig_len, SEG))
     ref_dev = torch.from_numpy(wl.ref).to(f"cuda:{dev}")
@@ -452,7 +459,7 @@ def run_serving(args):
     import torch
     import paper_2607_27291_b300 as P
     import synth
-    total = int(args.total)
+    total = int(args.total if args.total != 4e9 else 1e9)
     ref, lens, reqs = synth.workload_serving(total, args.rate, args.duration)
     ref_dev = torch.from_numpy(ref).cuda()
     h = P.ifa_create(hit_capacity=1024, segment_bytes=256 << 20, minhits_trials=100_000, minhits_seed=1)

@@ -58,10 +58,31 @@ def lib():
                                           C.c_uint32, C.c_uint32, C.c_uint32]
         L.oracle_revcomp.restype = None
         L.oracle_revcomp.argtypes = [u8p, C.c_uint32, u8p]
+        L.oracle_minhits_quantile.restype = C.c_uint32
+        L.oracle_minhits_quantile.argtypes = [u64p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64]
         L.oracle_kmer_count.restype = C.c_uint32
         L.oracle_kmer_count.argtypes = [C.c_uint32] * 3
         _lib = L
     return _lib
+
+
+class use_library:
+    """Context manager: route every oracle call to another build of the same
+    C source (the pin tests use it to check that planted mistakes fail)."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib, LIB_PATH
+        self.saved, self._orig = _lib, LIB_PATH
+        _lib, LIB_PATH = None, self.path
+        lib()
+        return self
+
+    def __exit__(self, *a):
+        global _lib, LIB_PATH
+        _lib, LIB_PATH = self.saved, self._orig
 
 
 def _ptr(a: np.ndarray, ct):
@@ -174,6 +195,12 @@ def choose_k(L: int, subs: int, klist=(8, 9, 10, 12, 14), step: int = 1, mask_w:
     st = lib().oracle_choose_k(L, subs, _ptr(kl, C.c_uint32), kl.size, step, mask_w, max_clips,
                                num, den, trials, seed, _ptr(ko, C.c_uint32), _ptr(mo, C.c_uint32))
     return int(st), int(ko[0]), int(mo[0])
+
+
+def minhits_quantile(hist, num: int, den: int) -> int:
+    h = np.ascontiguousarray(hist, dtype=np.uint64)
+    return int(lib().oracle_minhits_quantile(_ptr(h, C.c_uint64), h.size - 1, num, den,
+                                             int(h.sum())))
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

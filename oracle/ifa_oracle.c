@@ -343,6 +343,26 @@ uint32_t oracle_kmer_count(uint32_t L, uint32_t k, uint32_t step)
 }
 
 /*
+ * The threshold a survivor histogram h[0..K] of `trials` trials gives: the
+ * largest m such that at least num/den of the trials kept m or more
+ * error-free k-mers, i.e. #{trials with >= m} * den >= num * trials
+ * (Methods, indexed mode: the count needed to find an alignment "with a
+ * user-defined probability").  m = 0 always qualifies.
+ */
+uint32_t oracle_minhits_quantile(const uint64_t *h, uint32_t K, uint32_t num, uint32_t den,
+                                 uint64_t trials)
+{
+    unsigned __int128 need = (unsigned __int128)num * trials;
+    uint64_t tail = 0;
+    for (int64_t m = K; m >= 0; m--) {
+        tail += h[m];
+        if ((unsigned __int128)tail * den >= need)
+            return (uint32_t)m;
+    }
+    return 0;
+}
+
+/*
  * MinHitsCalculator (Methods, indexed mode): the minimum number of seed
  * hits that an alignment with `subs` substitutions still shows with
  * probability >= num/den, for a query of length L, seed length k, offset
@@ -408,16 +428,7 @@ uint32_t oracle_minhits(uint32_t L, uint32_t subs, uint32_t k, uint32_t step, ui
         }
         h[surv]++;
     }
-    uint32_t best = 0;
-    unsigned __int128 need = (unsigned __int128)num * trials;
-    uint64_t tail = 0;
-    for (int64_t m = K; m >= 0; m--) {
-        tail += h[m];
-        if ((unsigned __int128)tail * den >= need) {
-            best = (uint32_t)m;
-            break;
-        }
-    }
+    uint32_t best = oracle_minhits_quantile(h, K, num, den, trials);
     if (hist)
         memcpy(hist, h, (K + 1) * sizeof(uint64_t));
     free(h);

@@ -47,17 +47,40 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                     }
                 }
             }
-            // warp-synchronous walk over each lane's postings so hits can be
-            // compacted by ballot
-            while (__any_sync(0xffffffffu, beg < end)) {
+            // The warp's postings, flattened: lane l owns [exc_l, exc_l + cnt_l)
+            // of the warp's total; each round every lane verifies one posting
+            // (its owner found by a 5-step search over the lanes' offsets), so
+            // lanes stay busy however unevenly the k-mers hit, and the warp
+            // stays converged for ballot compaction of the hits.
+            const uint32_t cnt = end - beg;
+            uint32_t inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= static_cast<uint32_t>(o)) inc += v;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+            const uint32_t exc = inc - cnt;
+            for (uint32_t base = 0; base < total; base += 32) {
+                const uint32_t f = base + lane;
+                // owner: the largest lane whose first flat index is <= f
+                uint32_t own = 0;
+#pragma unroll
+                for (int stp = 16; stp > 0; stp >>= 1) {
+                    const uint32_t c = own + stp;
+                    if (__shfl_sync(0xffffffffu, exc, c) <= f) own = c;
+                }
+                const uint32_t own_beg = __shfl_sync(0xffffffffu, beg, own);
+                const uint32_t own_exc = __shfl_sync(0xffffffffu, exc, own);
                 bool hit = false;
                 uint32_t id = 0, contig = 0, pos = 0, mm = 0;
-                if (beg < end) {
-                    const uint32_t pv = __ldg(T.post + beg);
-                    beg++;
+                if (f < total) {
+                    const uint64_t j = (blk << 5) + own;
+                    const uint32_t pv = __ldg(T.post + own_beg + (f - own_exc));
                     const uint32_t e = pv >> 8, o = pv & 0xffu;
                     const uint32_t meta = __ldg(qt.meta + e);
                     const uint32_t L = meta_L(meta), W = meta_W(meta);
+                    const uint32_t se = entry_s(meta, s);
                     if (o <= j) {
                         const uint64_t p = j - o;
                         if (p + L <= b.nbases && p + L >= static_cast<uint64_t>(b.halo) + 1) {
@@ -83,10 +106,11 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                                     mm += __popc(x[w]);
                                     bnd |= rb & q.w;
                                     cur = nx;
+                                    if (mm > se) break;  // over maxSubs already
                                 }
                             }
                             x[WMAX] = 0;
-                            if (bnd == 0u && mm <= entry_s(meta, s)) {
+                            if (bnd == 0u && mm <= se) {
                                 // error-free k-mer offsets from the mismatch mask
                                 const uint32_t last = L - k;  // largest offset
                                 uint32_t nseed = 0, first = 0xffffffffu;

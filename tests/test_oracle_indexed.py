@@ -103,6 +103,16 @@ def test_minhits_matches_exact_enumeration(L, s, k, step, mask_w, num, den):
         assert m == m_exact
 
 
+def test_quantile_rule_on_hand_histograms():
+    # "found with probability P": a threshold met by exactly P of the trials counts
+    assert oracle.minhits_quantile([50, 50], 1, 2) == 1
+    assert oracle.minhits_quantile([51, 49], 1, 2) == 0
+    assert oracle.minhits_quantile([0, 1, 998, 1], 999, 1000) == 2
+    assert oracle.minhits_quantile([0, 2, 997, 1], 999, 1000) == 1
+    assert oracle.minhits_quantile([0, 0, 0, 10], 999, 1000) == 3
+    assert oracle.minhits_quantile([10, 0, 0, 0], 1, 1000) == 0
+
+
 @pytest.mark.parametrize("L,k,step", [(20, 8, 1), (33, 14, 1), (40, 10, 3)])
 def test_minhits_closed_forms(L, k, step):
     K = len(range(0, L - k + 1, step))
@@ -193,6 +203,15 @@ def test_minhits_one_equals_text_seed_test(wl_idx, k, step, mask_w):
         if _text_seeded(qq, wl.contig(h[1]), h[2], k, step, mask_w) >= 1:
             expect.append(h)
     assert got == expect
+
+
+def test_n_is_never_part_of_a_seed():
+    # an N opposite an N is still a mismatch: no k-mer holding it is a seed
+    ctg = np.frombuffer(b"ACGTNACGTA", np.uint8).copy()
+    assert oracle.window_seeds(b"ACGTNACGTA", 0, ctg, 0, 10) == 0
+    assert oracle.window_seeds(b"ACGTNACGTA", 0, ctg, 0, 4) == 3      # ACGT, ACGT, CGTA
+    assert oracle.window_seeds(b"ACGTNACGTA", 0, ctg, 0, 5) == 1      # ACGTA only
+    assert oracle.window_mismatches(b"ACGTNACGTA", 0, ctg, 0) == 1
 
 
 def test_indexed_subset_and_degenerate_cases(wl_idx):
