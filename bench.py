@@ -490,7 +490,8 @@ def run_serving(args):
         if nxt < len(reqs) and active == 0:
             time.sleep(max(0.0, min(0.01, reqs[nxt][0] - now)))
     wall = time.perf_counter() - t0
-    _, qbases = P.ifa_serve_stats(h)
+    sst = P.ifa_serve_stats(h)
+    qbases = sst["query_bases"]
     lat = np.array([i["done_s"] - i["submit_s"] for i in infos])
     queue = np.array([i["admit_s"] - i["submit_s"] for i in infos])
     P.ifa_serve_stop(h)
@@ -502,6 +503,7 @@ def run_serving(args):
                       "p999": float(np.percentile(lat, 99.9))},
         "queue_s": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
         "requests": len(reqs), "wall_s": wall, "steps": steps,
+        "host_plan_s": sst["plan_s"], "device_scan_s": sst["scan_s"],
         "config": {"reference_bases": int(ref.size), "rate_per_s": args.rate,
                    "duration_s": args.duration, "slices": args.slices,
                    "set_sizes": "log-uniform 1-2000", "lengths": "18-50", "max_subs": "0-8",

@@ -321,8 +321,11 @@ ifa_status ifa_serve_poll(ifa_handle *h, uint32_t request_id, ifa_request_info *
  * HIT_OVERFLOW (with the data) when its ring dropped hits. */
 ifa_status ifa_serve_drain(ifa_handle *h, uint32_t request_id, ifa_hit *out, uint64_t cap, uint64_t *n_out);
 
-/* Slices scanned and nominal query-base comparisons done so far. */
-ifa_status ifa_serve_stats(ifa_handle *h, uint64_t *slices_run, double *query_bases);
+/* Slices scanned, nominal query-base comparisons done, host seconds spent
+ * building plans and seconds spent waiting for slices, since
+ * ifa_serve_start.  Any pointer may be NULL. */
+ifa_status ifa_serve_stats(ifa_handle *h, uint64_t *slices_run, double *query_bases, double *plan_seconds,
+                           double *scan_seconds);
 
 /* End serving and free every request's ring. */
 ifa_status ifa_serve_stop(ifa_handle *h);

@@ -15,7 +15,8 @@ from typing import Iterable, List, Optional, Sequence, Tuple
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libifa.so")
+# IFA_LIB selects another build of the library (tuning experiments)
+LIB_PATH = os.environ.get("IFA_LIB") or os.path.join(_HERE, "libifa.so")
 
 IFA_OK = 0
 IFA_ERR_INVALID_ARG = 1
@@ -96,7 +97,8 @@ _SYMBOLS = {
     "ifa_serve_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "ifa_serve_poll": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p]),
     "ifa_serve_drain": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64)]),
-    "ifa_serve_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
+    "ifa_serve_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "ifa_serve_stop": (C.c_int, [C.c_void_p]),
     "ifa_scan_brute_noalloc": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
                                          C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32,
@@ -394,11 +396,13 @@ def ifa_serve_drain(h, rid: int, cap: int) -> Tuple[np.ndarray, bool]:
     return out[:n.value], st == IFA_ERR_HIT_OVERFLOW
 
 
-def ifa_serve_stats(h) -> Tuple[int, float]:
+def ifa_serve_stats(h) -> dict:
     n = C.c_uint64()
     qb = C.c_double()
-    _check(lib().ifa_serve_stats(h, C.byref(n), C.byref(qb)), h)
-    return n.value, qb.value
+    ps = C.c_double()
+    ss = C.c_double()
+    _check(lib().ifa_serve_stats(h, C.byref(n), C.byref(qb), C.byref(ps), C.byref(ss)), h)
+    return {"slices": n.value, "query_bases": qb.value, "plan_s": ps.value, "scan_s": ss.value}
 
 
 def ifa_serve_stop(h) -> None:

@@ -57,7 +57,7 @@ ifa_status bfail(ifa_handle *h, ifa_status st, const std::string &msg) {
 // Items [0, n_items - n_brute_items) are seed tiles, the rest brute-force
 // (chunk, tile) items in chunk-major order, so a CTA reloads its shared
 // query chunk rarely.
-template <int WMAX>
+template <int WMAX, bool MULTI>
 __global__ void __launch_bounds__(kBThreads)
 k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
     using namespace brute;
@@ -68,7 +68,7 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
     __shared__ uint32_t s_nF, s_nM, s_item;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
-    WarpHits wh;
+    WarpHitsT<MULTI> wh;
     wh.init(wbuf[warp]);
     uint32_t mul[kWin];
     lane_multipliers(mul);
@@ -120,7 +120,10 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
 template <int WMAX>
 cudaError_t launch_batch_t(const Batch &b, const BatchWork &w, const QueryTable &bt, const QueryTable &ft,
                            const HitSink &sink, int grid, size_t smem, cudaStream_t st) {
-    k_batch<WMAX><<<grid, kBThreads, smem, st>>>(b, w, bt, ft, sink);
+    if (sink.q2r)
+        k_batch<WMAX, true><<<grid, kBThreads, smem, st>>>(b, w, bt, ft, sink);
+    else
+        k_batch<WMAX, false><<<grid, kBThreads, smem, st>>>(b, w, bt, ft, sink);
     return cudaGetLastError();
 }
 
@@ -142,10 +145,10 @@ int batch_grid(uint32_t wmax) {
     const size_t smem = brute::kScanSmemBudget;
     cudaError_t e = cudaSuccess;
     switch (wmax) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<1>, kBThreads, smem); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<2>, kBThreads, smem); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<4>, kBThreads, smem); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<8>, kBThreads, smem); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<1, true>, kBThreads, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<2, true>, kBThreads, smem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<4, true>, kBThreads, smem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<8, true>, kBThreads, smem); break;
     }
     if (e != cudaSuccess || per < 1) per = 1;
     return sms * per;

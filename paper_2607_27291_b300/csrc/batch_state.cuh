@@ -132,6 +132,7 @@ struct ServeState {
     unsigned long long *d_cand = nullptr;
     uint64_t slices_run = 0;
     double scanned_query_bases = 0;   // nominal comparisons done by completed slices
+    double plan_s = 0, scan_s = 0;    // host time building plans, time waiting for slices
 };
 
 }  // namespace ifa

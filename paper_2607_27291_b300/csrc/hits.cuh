@@ -13,7 +13,11 @@
 
 namespace ifa {
 
-struct WarpHits {
+// MULTI: hits go to per-request rings (serving); otherwise to the shared
+// hit buffer with warp staging.  A compile-time choice, so the streaming and
+// batch kernels carry no serving code.
+template <bool MULTI>
+struct WarpHitsT {
     ifa_hit *buf;          // this warp's 32 staged hits (shared memory)
     uint32_t n;            // staged count (warp-uniform)
     unsigned long long dcount, dsum, dxor;  // this lane's digest terms
@@ -52,8 +56,8 @@ struct WarpHits {
         const uint32_t ballot = __ballot_sync(0xffffffffu, hit);
         if (ballot == 0) return;
         const uint32_t cnt = __popc(ballot);
-        if (s.q2r) {
-            // per-request rings: each hit goes straight to its request's ring
+        if constexpr (MULTI) {
+            // each hit goes straight to its request's own ring and digest
             if (hit) {
                 const RingDesc R = s.rings[s.q2r[q]];
                 const uint32_t rq = q - R.qfirst;
@@ -122,5 +126,7 @@ struct WarpHits {
         }
     }
 };
+
+using WarpHits = WarpHitsT<false>;
 
 }  // namespace ifa

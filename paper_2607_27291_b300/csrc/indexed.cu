@@ -345,28 +345,29 @@ ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
     for (size_t ti = 0; ti < ks.size() && e == cudaSuccess; ti++) {
         const uint32_t k = ks[ti];
         const uint32_t care = care_mask(k, cfg.mask_width);
-        std::vector<std::pair<uint32_t, uint32_t>> kv;  // (key, posting)
+        std::vector<uint32_t> kk, pv;  // (key, posting) pairs
         for (uint32_t q = 0; q < nq; q++) {
             if (!S.plan_in[q] || S.plan_exhaustive[q] || S.plan_k[q] != k) continue;
             const uint32_t L = static_cast<uint32_t>(qs[q].size());
             for (uint32_t t = 0; t < 2; t++)
-                for (uint32_t o = 0; o + k <= L; o += cfg.kmer_step)
-                    kv.push_back({query_key(qs[q], t == 1, o, k, care), ((2 * q + t) << 8) | o});
+                for (uint32_t o = 0; o + k <= L; o += cfg.kmer_step) {
+                    kk.push_back(query_key(qs[q], t == 1, o, k, care));
+                    pv.push_back(((2 * q + t) << 8) | o);
+                }
         }
-        std::sort(kv.begin(), kv.end());
+        const size_t np = kk.size();
         KTableDev &T = S.targ.t[ti];
         T.k = k;
         T.care = care;
-        std::vector<uint32_t> post(kv.size());
-        for (size_t i = 0; i < kv.size(); i++) post[i] = kv[i].second;
-        uint32_t *dpost = static_cast<uint32_t *>(dalloc(post.size() * sizeof(uint32_t)));
-        if (dpost) ck(cudaMemcpy(dpost, post.data(), post.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-        T.post = dpost;
+        std::vector<uint32_t> post(np);
         if (k <= kDirectMaxK) {
+            // counting sort straight into the direct-address offsets
             const size_t nkeys = size_t(1) << (2 * k);
             std::vector<uint32_t> off(nkeys + 1, 0);
-            for (const auto &p : kv) off[p.first + 1]++;
+            for (size_t i = 0; i < np; i++) off[kk[i] + 1]++;
             for (size_t i = 0; i < nkeys; i++) off[i + 1] += off[i];
+            std::vector<uint32_t> cur(off.begin(), off.end() - 1);
+            for (size_t i = 0; i < np; i++) post[cur[kk[i]]++] = pv[i];
             uint32_t *doff = static_cast<uint32_t *>(dalloc(off.size() * sizeof(uint32_t)));
             if (doff) ck(cudaMemcpy(doff, off.data(), off.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
             T.direct = 1;
@@ -375,17 +376,33 @@ ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
             T.bits = nullptr;
             T.nuniq = 0;
         } else {
+            // two 16-bit LSD radix passes over (key, posting), then distinct keys
+            std::vector<uint32_t> k2(np), p2(np);
+            for (int pass = 0; pass < 2; pass++) {
+                const int sh = 16 * pass;
+                std::vector<uint32_t> cnt(65537, 0);
+                for (size_t i = 0; i < np; i++) cnt[((kk[i] >> sh) & 0xffffu) + 1]++;
+                for (size_t i = 0; i < 65536; i++) cnt[i + 1] += cnt[i];
+                for (size_t i = 0; i < np; i++) {
+                    const uint32_t d = cnt[(kk[i] >> sh) & 0xffffu]++;
+                    k2[d] = kk[i];
+                    p2[d] = pv[i];
+                }
+                kk.swap(k2);
+                pv.swap(p2);
+            }
+            post = pv;
             std::vector<uint32_t> keys, off;
-            for (size_t i = 0; i < kv.size(); i++) {
-                if (i == 0 || kv[i].first != kv[i - 1].first) {
-                    keys.push_back(kv[i].first);
+            for (size_t i = 0; i < np; i++) {
+                if (i == 0 || kk[i] != kk[i - 1]) {
+                    keys.push_back(kk[i]);
                     off.push_back(static_cast<uint32_t>(i));
                 }
             }
-            off.push_back(static_cast<uint32_t>(kv.size()));
+            off.push_back(static_cast<uint32_t>(np));
             const size_t nbits = size_t(1) << (2 * k);
             std::vector<uint32_t> bits(nbits / 32, 0);
-            for (uint32_t kk : keys) bits[kk >> 5] |= 1u << (kk & 31);
+            for (uint32_t key : keys) bits[key >> 5] |= 1u << (key & 31);
             uint32_t *dk = static_cast<uint32_t *>(dalloc(keys.size() * sizeof(uint32_t)));
             uint32_t *doff = static_cast<uint32_t *>(dalloc(off.size() * sizeof(uint32_t)));
             uint32_t *db = static_cast<uint32_t *>(dalloc(bits.size() * sizeof(uint32_t)));
@@ -398,6 +415,9 @@ ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
             T.bits = db;
             T.nuniq = static_cast<uint32_t>(keys.size());
         }
+        uint32_t *dpost = static_cast<uint32_t *>(dalloc(post.size() * sizeof(uint32_t)));
+        if (dpost && np) ck(cudaMemcpy(dpost, post.data(), post.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        T.post = dpost;
     }
     // exhaustive queries: compact table for the brute-force kernel
     std::vector<uint32_t> exq;

@@ -37,8 +37,17 @@ namespace {
 
 using namespace brute;
 
+// Resident CTAs per SM the register allocation must allow: 4 (64 registers)
+// fits queries up to 128 bases without spilling; the 256-base build needs 96
+// registers and gets 2.
+#ifndef IFA_SCAN_MIN_CTAS
+#define IFA_SCAN_MIN_CTAS 4
+#endif
 template <int WMAX>
-__global__ void __launch_bounds__(kScanThreads)
+constexpr int kScanMinCtas = WMAX <= 4 ? IFA_SCAN_MIN_CTAS : (IFA_SCAN_MIN_CTAS > 2 ? 2 : IFA_SCAN_MIN_CTAS);
+
+template <int WMAX>
+__global__ void __launch_bounds__(kScanThreads, kScanMinCtas<WMAX>)
 k_scan_brute(Batch b, QueryTable qt, uint32_t e0, uint32_t e1, uint32_t s, uint32_t lmin,
              uint32_t lmax, HitSink sink) {
     constexpr int NW = Stage<WMAX>::kWords;

@@ -81,21 +81,25 @@ struct Stage {
 };
 
 // Exact evaluation of one entry for the lane's WIN windows of a block without
-// N, piece boundary or ownership limits, then hit emission.
-template <int WMAX>
+// N, piece boundary or ownership limits, then hit emission.  The word-0
+// counts come from the packed word v of the hot loop (byte k of v minus
+// byte k of the entry's bias is window k's word-0 count), so only words
+// 1.. are computed here.
+template <int WMAX, class WH>
 __device__ __forceinline__ void exact_fast(const Batch &b, const QueryTable &qt, const Smem &m,
                                            const uint4 *R, uint32_t e, uint32_t e0, uint64_t p0,
                                            uint32_t lane, uint32_t s, const HitSink &sink,
-                                           WarpHits &wh, uint32_t &pidx) {
+                                           WH &wh, uint32_t &pidx, uint32_t v, uint32_t bias) {
     const uint32_t meta = m.meta[e];
     const uint32_t W = meta_W(meta);
     const uint32_t se = entry_s(meta, s);
     const uint4 *qw = m.sq + static_cast<size_t>(e) * WMAX;
     uint32_t mm[kWin];
 #pragma unroll
-    for (int k = 0; k < kWin; k++) mm[k] = meta_nN(meta);
+    for (int k = 0; k < kWin; k++)
+        mm[k] = meta_nN(meta) + (((v >> (8 * k)) & 0xffu) - ((bias >> (8 * k)) & 0xffu));
 #pragma unroll
-    for (int j = 0; j < WMAX; j++) {
+    for (int j = 1; j < WMAX; j++) {
         if (j < static_cast<int>(W)) {
             const uint4 q = qw[j];
 #pragma unroll
@@ -121,10 +125,10 @@ __device__ __forceinline__ void exact_fast(const Batch &b, const QueryTable &qt,
 
 // Generic evaluation of every entry for one window per lane (p = p0 + lane)
 // whose block may hold N, piece boundaries, the batch end or the halo.
-template <int WMAX>
+template <int WMAX, class WH>
 __device__ void generic_window(const Batch &b, const QueryTable &qt, const Smem &m, uint32_t nent,
                                uint32_t e0, uint64_t p0, uint32_t lane, uint32_t s,
-                               const HitSink &sink, WarpHits &wh) {
+                               const HitSink &sink, WH &wh) {
     const uint64_t w0 = p0 >> 5;
     uint32_t hi[WMAX], lo[WMAX], nw[WMAX], bw[WMAX];
     uint4 cur = __ldg(b.words + w0);
@@ -206,12 +210,12 @@ __device__ __forceinline__ uint32_t packed_counts(const uint4 &q, const uint32_t
     return v;
 }
 
-template <int WMAX, bool MASKED>
+template <int WMAX, bool MASKED, class WH>
 __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt, const Smem &m,
                                            const uint4 *rec, const uint16_t *idx, uint32_t n,
                                            const uint32_t *hw, const uint32_t *lw, const uint32_t *mul,
                                            const uint4 *R, uint32_t e0, uint64_t p0, uint32_t lane,
-                                           uint32_t s, const HitSink &sink, WarpHits &wh, uint32_t &pidx) {
+                                           uint32_t s, const HitSink &sink, WH &wh, uint32_t &pidx) {
     constexpr uint32_t kHigh = 0x80808080u;
     uint32_t k = 0;
     for (; k + kGroup <= n; k += kGroup) {
@@ -230,14 +234,19 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
             while (fired) {
                 const int i = __ffs(fired) - 1;
                 fired &= fired - 1;
-                exact_fast<WMAX>(b, qt, m, R, idx[k + i], e0, p0, lane, s, sink, wh, pidx);
+                // v[i] by a select chain (no local array); the bias from the record
+                const uint32_t vi = i == 0 ? v[0] : i == 1 ? v[1] : i == 2 ? v[2] : v[3];
+                const uint4 q = rec[k + i];
+                exact_fast<WMAX>(b, qt, m, R, idx[k + i], e0, p0, lane, s, sink, wh, pidx, vi,
+                                 MASKED ? q.w : q.z);
             }
         }
     }
     for (; k < n; k++) {
-        const uint32_t v = packed_counts<MASKED>(rec[k], hw, lw, mul);
+        const uint4 q = rec[k];
+        const uint32_t v = packed_counts<MASKED>(q, hw, lw, mul);
         if (__any_sync(0xffffffffu, (v & kHigh) != kHigh))
-            exact_fast<WMAX>(b, qt, m, R, idx[k], e0, p0, lane, s, sink, wh, pidx);
+            exact_fast<WMAX>(b, qt, m, R, idx[k], e0, p0, lane, s, sink, wh, pidx, v, MASKED ? q.w : q.z);
     }
 }
 
@@ -334,10 +343,10 @@ __device__ __forceinline__ void lane_multipliers(uint32_t *mul) {
 
 // Scan blocks blk, blk + stride, ... < blk_end (of 32 * kWin windows) with
 // this warp, staging words through stage[2][NW] (this warp's buffers).
-template <int WMAX>
+template <int WMAX, class WH>
 __device__ __forceinline__ void scan_blocks(const Batch &b, const QueryTable &qt, const Smem &m, uint32_t nent,
                                             uint32_t nF, uint32_t nM, uint32_t e0, uint32_t s, uint32_t lmin,
-                                            uint32_t lmax, const HitSink &sink, WarpHits &wh,
+                                            uint32_t lmax, const HitSink &sink, WH &wh,
                                             uint4 (*stage)[Stage<WMAX>::kWords], const uint32_t *mul,
                                             uint64_t blk, uint64_t blk_end, uint64_t stride, uint32_t lane) {
     constexpr int NW = Stage<WMAX>::kWords;

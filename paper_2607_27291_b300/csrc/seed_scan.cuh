@@ -12,10 +12,10 @@ namespace seed {
 // look every position's k-mer up in each table, verify the window each
 // posting names, and emit it from its first seed when its seed count
 // reaches the entry's threshold.  Adds verified candidates to ncand.
-template <int WMAX>
+template <int WMAX, class WH>
 __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt, const KTablesArg &tabs,
                                             const uint32_t *__restrict__ entry_minhits, uint32_t step,
-                                            uint32_t s, const HitSink &sink, WarpHits &wh, uint64_t blk,
+                                            uint32_t s, const HitSink &sink, WH &wh, uint64_t blk,
                                             uint64_t blk_end, uint64_t stride, uint32_t lane,
                                             unsigned long long &ncand) {
     for (; blk < blk_end; blk += stride) {

@@ -256,6 +256,8 @@ ifa_status ifa_serve_start(ifa_handle *h, uint32_t n_slices, uint64_t hbm_budget
     S.dirty = true;
     S.slices_run = 0;
     S.scanned_query_bases = 0;
+    S.plan_s = 0;
+    S.scan_s = 0;
     SCK(h, cudaMalloc(&S.d_queue, sizeof(unsigned int)));
     SCK(h, cudaMalloc(&S.d_cand, sizeof(unsigned long long)));
     SCK(h, cudaMemset(S.d_cand, 0, sizeof(unsigned long long)));
@@ -324,7 +326,9 @@ ifa_status ifa_serve_step(ifa_handle *h, uint32_t *n_active, uint32_t *n_complet
     uint32_t done = 0;
     if (!S.active.empty()) {
         if (S.dirty) {
+            const double t0 = now_s();
             const ifa_status st = build_serve_plan(h);
+            S.plan_s += now_s() - t0;
             if (st != IFA_OK) return st;
         }
         // this slice's block ranges and tiles
@@ -354,9 +358,11 @@ ifa_status ifa_serve_step(ifa_handle *h, uint32_t *n_active, uint32_t *n_complet
         b.halo = 0;
         b.pieces = B.d_pieces;
         b.npieces = B.d_pieces_n;
+        const double t1 = now_s();
         SCK(h, cudaMemsetAsync(S.d_queue, 0, sizeof(unsigned int), h->stream));
         SCK(h, launch_batch_kernel(S.wmax, b, w, S.bt, S.ft, S.sink, S.grid, brute::kScanSmemBudget, h->stream));
         SCK(h, cudaStreamSynchronize(h->stream));
+        S.scan_s += now_s() - t1;
         h->stats.kernel_launches += 1;
         S.slices_run++;
         const double slice_bases = static_cast<double>(ns) * 32.0;
@@ -424,10 +430,13 @@ ifa_status ifa_serve_drain(ifa_handle *h, uint32_t id, ifa_hit *out, uint64_t ca
     return r.final_counters[1] ? IFA_ERR_HIT_OVERFLOW : IFA_OK;
 }
 
-ifa_status ifa_serve_stats(ifa_handle *h, uint64_t *slices_run, double *query_bases) {
+ifa_status ifa_serve_stats(ifa_handle *h, uint64_t *slices_run, double *query_bases, double *plan_seconds,
+                           double *scan_seconds) {
     if (!h) return IFA_ERR_INVALID_ARG;
     if (slices_run) *slices_run = h->serve.slices_run;
     if (query_bases) *query_bases = h->serve.scanned_query_bases;
+    if (plan_seconds) *plan_seconds = h->serve.plan_s;
+    if (scan_seconds) *scan_seconds = h->serve.scan_s;
     return IFA_OK;
 }
 
