@@ -253,7 +253,9 @@ def run_ours(args, rank, world):
     segs = list(P.segment_pieces(wl.contig_len, SEG))
     ref_dev = torch.from_numpy(wl.ref).to(f"cuda:{dev}")
     stream = torch.cuda.Stream(device=dev)
-    hcap = 1 << 28
+    # hit buffer sized to the reference: the 4 Gbp sweep's maxSubs-16 pass emits
+    # about 8.3e7 hits, a 256 Mbp profiling case about 5e6
+    hcap = min(1 << 28, max(1 << 22, int(args.total) // 16))
     h = P.ifa_create(device=dev, hit_capacity=hcap, segment_bytes=SEG, profile=1)
     P.ifa_set_stream(h, stream)
     P.ifa_load_queries(h, wl.queries)

@@ -372,8 +372,52 @@ ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *const *queries,
                                   uint64_t *counters_device, uint64_t *per_query_counts_device,
                                   void *stream);
 
+/* ---- SAM text (Methods, "Output Format"; host-side, needs no device) ----
+ *
+ * The paper writes headerless SAM records as the stream goes, because the
+ * full contig list is only known at the end, and a separate header file
+ * (its outh= flag) to be concatenated in front.  The primary alignment of a
+ * query is the first valid one in reference order (Results, accuracy
+ * validation).
+ *
+ * Readings where the paper is silent: FLAG is 16 for strand '-' plus 256
+ * for a secondary record; POS is pos + 1; MAPQ is 255 (not available);
+ * CIGAR is "<L>M" (no clipping); RNEXT/PNEXT/TLEN are * 0 0; SEQ is the
+ * query on the reference's forward strand (the reverse complement for
+ * '-'), upper case, every non-ACGT byte written as N; QUAL is *; the one
+ * tag is NM:i:<mismatches>. */
+typedef struct {
+    const uint8_t *const *query_seqs;   /* n_queries ASCII queries, as loaded */
+    const uint32_t *query_lens;
+    const char *const *query_names;     /* n_queries NUL-terminated names, or NULL: "q<id>" */
+    uint32_t n_queries;
+    const char *const *contig_names;    /* indexed by contig id, or NULL: "c<id>" */
+    uint32_t n_contig_names;            /* entries of contig_names (ids beyond get "c<id>") */
+} ifa_sam_info;
+
+/* SAM records for n hits, one line each, no header.  hits (host) is sorted
+ * in place into reference order (contig id, pos, strand, query,
+ * mismatches).  primary_seen (host, n_queries bytes, zeroed by the caller
+ * once per pass over the reference) marks queries whose primary was already
+ * written: a hit is primary when its query's byte is 0, which this call then
+ * sets.  Calls must follow the stream order (drain after ifa_flush).
+ * out (host, cap bytes) receives the text, not NUL-terminated; *n_out is
+ * its length.  If cap is too small nothing is written, primary_seen is not
+ * changed, *n_out is the length needed and the status is
+ * IFA_ERR_INVALID_ARG.  A hit naming a query >= n_queries or a strand
+ * other than 0/1 is IFA_ERR_INVALID_ARG, before anything is written. */
+ifa_status ifa_sam_records(ifa_hit *hits, uint64_t n, const ifa_sam_info *info, uint8_t *primary_seen,
+                           char *out, uint64_t cap, uint64_t *n_out);
+
+/* The separate SAM header: "@HD VN:1.6 SO:unsorted" and one "@SQ SN LN"
+ * line per contig, tab-separated, in the order given.  contig_ids[i] names
+ * contig i ("c<id>") when contig_names is NULL.  Buffer rules as for
+ * ifa_sam_records. */
+ifa_status ifa_sam_header(const char *const *contig_names, const uint32_t *contig_ids,
+                          const uint64_t *contig_lens, uint32_t n, char *out, uint64_t cap, uint64_t *n_out);
+
 /* Human-readable description of the last failure on h (or of the last
- * failed ifa_create/ifa_minhits/ifa_scan_brute_noalloc when h is NULL).
+ * failed ifa_create/ifa_minhits/ifa_scan_brute_noalloc/ifa_sam_* when h is NULL).
  * Never NULL. */
 const char *ifa_last_error(const ifa_handle *h);
 

@@ -57,6 +57,12 @@ class ifa_stats(C.Structure):
                 ("scan_launches", C.c_uint64), ("scan_ns", C.c_uint64)]
 
 
+class ifa_sam_info(C.Structure):
+    _fields_ = [("query_seqs", C.POINTER(C.c_void_p)), ("query_lens", C.POINTER(C.c_uint32)),
+                ("query_names", C.POINTER(C.c_char_p)), ("n_queries", C.c_uint32),
+                ("contig_names", C.POINTER(C.c_char_p)), ("n_contig_names", C.c_uint32)]
+
+
 class IfaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("ifa status %d: %s" % (status, msg))
@@ -104,6 +110,10 @@ _SYMBOLS = {
                                          C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32,
                                          C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p,
                                          C.c_void_p]),
+    "ifa_sam_records": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(ifa_sam_info), C.c_void_p,
+                                  C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64)]),
+    "ifa_sam_header": (C.c_int, [C.POINTER(C.c_char_p), C.c_void_p, C.c_void_p, C.c_uint32,
+                                 C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64)]),
 }
 
 
@@ -425,6 +435,69 @@ def ifa_scan_brute_noalloc(device: int, queries: Sequence[bytes], ref_ptr: int, 
                                         hit_capacity, C.c_void_p(counters_ptr),
                                         C.c_void_p(per_query_counts_ptr or None),
                                         C.c_void_p(sptr or None)))
+
+
+def _names(names, n):
+    if names is None:
+        return None
+    arr = (C.c_char_p * max(1, n))()
+    for i, x in enumerate(names):
+        arr[i] = x.encode() if isinstance(x, str) else x
+    return arr
+
+
+def ifa_sam_records(hits: np.ndarray, queries: Sequence[bytes], primary_seen: np.ndarray,
+                    query_names=None, contig_names=None) -> bytes:
+    """Headerless SAM records for `hits` (sorted in place into reference
+    order); `primary_seen` (uint8, one per query) carries the primary flags
+    across calls of one pass over the reference."""
+    hits = np.ascontiguousarray(hits, dtype=HIT_DTYPE)
+    if primary_seen.dtype != np.uint8 or primary_seen.size != len(queries) or \
+            not primary_seen.flags.c_contiguous:
+        raise ValueError("primary_seen must be a contiguous uint8 array, one byte per query")
+    nq = len(queries)
+    bufs = [C.create_string_buffer(bytes(q), max(1, len(q))) for q in queries]
+    info = ifa_sam_info()
+    seqs = (C.c_void_p * max(1, nq))(*[C.cast(b, C.c_void_p) for b in bufs])
+    lens = (C.c_uint32 * max(1, nq))(*[len(q) for q in queries])
+    info.query_seqs = C.cast(seqs, C.POINTER(C.c_void_p))
+    info.query_lens = C.cast(lens, C.POINTER(C.c_uint32))
+    qn = _names(query_names, nq)
+    info.query_names = C.cast(qn, C.POINTER(C.c_char_p)) if qn is not None else None
+    info.n_queries = nq
+    cn = _names(contig_names, len(contig_names) if contig_names is not None else 0)
+    info.contig_names = C.cast(cn, C.POINTER(C.c_char_p)) if cn is not None else None
+    info.n_contig_names = len(contig_names) if contig_names is not None else 0
+    need = C.c_uint64()
+    cap = max(1, hits.size) * 128
+    while True:
+        out = C.create_string_buffer(cap)
+        st = lib().ifa_sam_records(hits.ctypes.data, hits.size, C.byref(info), primary_seen.ctypes.data,
+                                   out, cap, C.byref(need))
+        if st == IFA_ERR_INVALID_ARG and need.value > cap:
+            cap = need.value
+            continue
+        _check(st)
+        return out.raw[:need.value]
+
+
+def ifa_sam_header(contig_lens, contig_ids=None, contig_names=None) -> bytes:
+    """The separate SAM header (@HD, then one @SQ per contig)."""
+    lens = np.ascontiguousarray(contig_lens, dtype=np.uint64)
+    n = lens.size
+    ids = None if contig_ids is None else np.ascontiguousarray(contig_ids, dtype=np.uint32)
+    cn = _names(contig_names, n)
+    need = C.c_uint64()
+    cap = 64 + 64 * n
+    while True:
+        out = C.create_string_buffer(cap)
+        st = lib().ifa_sam_header(cn, ids.ctypes.data if ids is not None else None, lens.ctypes.data, n,
+                                  out, cap, C.byref(need))
+        if st == IFA_ERR_INVALID_ARG and need.value > cap:
+            cap = need.value
+            continue
+        _check(st)
+        return out.raw[:need.value]
 
 
 def ifa_last_error(h=None) -> str:

@@ -1,0 +1,93 @@
+"""SAM text (Methods, "Output Format"): the oracle against a hand-written
+example, then the library's host-side formatter against the oracle.  No GPU:
+the formatter is host code and the hits come from the CPU oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.sam as osam
+import paper_2607_27291_b300 as P
+import synth
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "sam_example.json")))
+
+
+def _queries():
+    return [q.encode() for q in GOLDEN["queries"]]
+
+
+def _hit_array(tuples):
+    a = np.zeros(len(tuples), dtype=P.HIT_DTYPE)
+    for i, (q, c, p, t, m) in enumerate(tuples):
+        a[i] = (q, c, p, t, m, 0)
+    return a
+
+
+def test_oracle_matches_hand_written_records():
+    seen = [False] * len(GOLDEN["queries"])
+    text = osam.sam_records([tuple(h) for h in GOLDEN["hits"]], _queries(), seen)
+    assert text == "".join(r + "\n" for r in GOLDEN["records"])
+    assert seen == [True, True]
+
+
+def test_oracle_names_and_header():
+    seen = [False, False]
+    names = {int(k): v for k, v in GOLDEN["contig_names"].items()}
+    text = osam.sam_records([tuple(h) for h in GOLDEN["hits"]], _queries(), seen,
+                            query_names=GOLDEN["query_names"], contig_names=names)
+    assert text.splitlines()[0] == GOLDEN["named_first_record"]
+    assert osam.sam_header([tuple(c) for c in GOLDEN["header_contigs"]]) == GOLDEN["header"]
+
+
+def test_library_matches_hand_written_records():
+    seen = np.zeros(2, dtype=np.uint8)
+    text = P.ifa_sam_records(_hit_array(GOLDEN["hits"]), _queries(), seen)
+    assert text.decode() == "".join(r + "\n" for r in GOLDEN["records"])
+    assert seen.tolist() == [1, 1]
+    names = [None] * 6
+    for k, v in GOLDEN["contig_names"].items():
+        names[int(k)] = v
+    seen[:] = 0
+    text = P.ifa_sam_records(_hit_array(GOLDEN["hits"]), _queries(), seen,
+                             query_names=GOLDEN["query_names"], contig_names=names)
+    assert text.decode().splitlines()[0] == GOLDEN["named_first_record"]
+    hdr = P.ifa_sam_header([c[1] for c in GOLDEN["header_contigs"]],
+                           contig_names=[c[0] for c in GOLDEN["header_contigs"]])
+    assert hdr.decode() == GOLDEN["header"]
+    assert P.ifa_sam_header([1000, 250], contig_ids=[3, 5]).decode() == \
+        "@HD\tVN:1.6\tSO:unsorted\n@SQ\tSN:c3\tLN:1000\n@SQ\tSN:c5\tLN:250\n"
+
+
+def test_library_matches_oracle_across_calls():
+    """Hits of a small brute-force oracle run, formatted in two calls (two
+    halves of the reference in stream order) with the primary flags carried
+    over: the concatenated text equals one oracle call."""
+    wl = synth.small_workload(seed=3)
+    hits = oracle.brute(wl.queries, wl.ref, wl.contig_len, 3)
+    assert hits.size > 20
+    tuples = [tuple(int(x) for x in (h["query"], h["contig"], h["pos"], h["strand"], h["mismatches"]))
+              for h in hits]
+    seen_o = [False] * len(wl.queries)
+    expect = osam.sam_records(tuples, wl.queries, seen_o)
+    split = int(np.median(hits["contig"]))
+    first = hits[hits["contig"] < split]
+    second = hits[hits["contig"] >= split]
+    seen = np.zeros(len(wl.queries), dtype=np.uint8)
+    got = P.ifa_sam_records(first.copy(), wl.queries, seen) + P.ifa_sam_records(second.copy(), wl.queries, seen)
+    assert got.decode() == expect
+    assert seen.astype(bool).tolist() == seen_o
+
+
+def test_library_rejects_bad_hits_and_keeps_flags():
+    seen = np.zeros(2, dtype=np.uint8)
+    bad = _hit_array([[0, 1, 2, 0, 0], [7, 1, 2, 0, 0]])
+    with pytest.raises(P.IfaError):
+        P.ifa_sam_records(bad, _queries(), seen)
+    assert seen.tolist() == [0, 0]
+    bad = _hit_array([[0, 1, 2, 2, 0]])
+    with pytest.raises(P.IfaError):
+        P.ifa_sam_records(bad, _queries(), seen)
+    assert P.ifa_sam_records(_hit_array([]), _queries(), seen) == b""
