@@ -106,7 +106,7 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
             const uint64_t lo = w.b_block0 + static_cast<uint64_t>(tile) * w.tile_bblocks;
             const uint64_t hi = lo + w.tile_bblocks < w.b_block_end ? lo + w.tile_bblocks : w.b_block_end;
             scan_blocks<WMAX>(b, bt, m, nent, s_nF, s_nM, e0, kSPerEntry, lmin, lmax, sink, wh, stage[warp], mul,
-                              lo + warp, hi, kBWarps, lane);
+                              lo, hi, warp, kBWarps, lane);
         }
         __syncthreads();
     }

@@ -5,9 +5,14 @@
 //  - a warp stages its hits in a private 32-entry shared-memory buffer
 //    (slots assigned by ballot rank) and claims global slots with one
 //    atomicAdd per 32 hits;
-//  - each lane keeps its own digest terms (count, sum, xor) in registers,
-//    reduced over the warp once at the end of the kernel;
+//  - the digest terms (count, sum, xor) are taken when a full or final
+//    buffer is flushed, one staged hit per lane, so the hash runs with the
+//    warp converged rather than once per hitting lane in divergent code;
+//    each lane keeps its terms in registers, reduced over the warp once at
+//    the end of the kernel;
 //  - per-entry counts go to a per-CTA shared array, flushed once.
+// The staging runs in count-only mode too (it feeds the digest); only the
+// global writes are skipped there.
 #pragma once
 #include "ifa_internal.cuh"
 
@@ -31,6 +36,18 @@ struct WarpHitsT {
     __device__ void flush(const HitSink &s, uint32_t lane) {
         __syncwarp();
         if (n == 0) return;
+        if (lane < n) {
+            const ifa_hit h = buf[lane];
+            const uint64_t v = hit_digest_item(h.query, h.contig, h.pos, h.strand, h.mismatches);
+            dcount += 1;
+            dsum += v;
+            dxor ^= v;
+        }
+        if (s.count_only) {
+            n = 0;
+            __syncwarp();
+            return;
+        }
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(s.head, static_cast<unsigned long long>(n));
         base = __shfl_sync(0xffffffffu, base, 0);
@@ -83,16 +100,9 @@ struct WarpHitsT {
             if (entry_count && lane == static_cast<uint32_t>(__ffs(ballot) - 1)) atomicAdd(entry_count, cnt);
             return;
         }
-        if (hit) {
-            const uint64_t v = hit_digest_item(q, contig, pos, strand, mm);
-            dcount += 1;
-            dsum += v;
-            dxor ^= v;
-            if (!entry_count) atomicAdd(&s.qcount[q], 1ull);
-        }
+        if (hit && !entry_count) atomicAdd(&s.qcount[q], 1ull);
         if (entry_count && lane == static_cast<uint32_t>(__ffs(ballot) - 1))
             atomicAdd(entry_count, cnt);
-        if (s.count_only) return;
         if (n + cnt > 32) flush(s, lane);
         if (hit) {
             const uint32_t r = __popc(ballot & ((1u << lane) - 1u));
@@ -111,7 +121,7 @@ struct WarpHitsT {
 
     // End of kernel: flush staged hits and fold the digest terms of the warp.
     __device__ void finish(const HitSink &s, uint32_t lane) {
-        if (!s.count_only) flush(s, lane);
+        flush(s, lane);
         unsigned long long c = dcount, su = dsum, x = dxor;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

@@ -23,6 +23,28 @@ __device__ __forceinline__ void pack_byte(uint32_t c, uint32_t bit, uint32_t &hi
     nn |= (ok ^ 1u) << bit;
 }
 
+// Bits 0, 8, 16, 24 of m gathered into bits 24..27 by one multiply: the
+// partial products of 2^24, 2^17, 2^10, 2^3 land on distinct bits, so no
+// carries occur and bits 24..27 hold exactly the four selected bits.
+__device__ __forceinline__ uint32_t gather_nibble(uint32_t m) { return (m * 0x01020408u) >> 24; }
+
+// Four ASCII bytes (byte j of u = base j) -> bits 0..3 of the hi, lo and N
+// planes.  The 2-bit code is (byte >> 1) & 3 (A 0, C 1, T 2, G 3); a byte is
+// a base exactly when, with the case bit set, it equals the lower-case
+// letter its code bits name, tested for all four bytes at once with an
+// exact zero-byte test.  Code bits of non-bases are cleared by the caller.
+__device__ __forceinline__ void pack4(uint32_t u, uint32_t &h4, uint32_t &l4, uint32_t &n4) {
+    const uint32_t l = (u >> 1) & 0x01010101u;
+    const uint32_t h = (u >> 2) & 0x01010101u;
+    // per byte 0x61 + 2 l + 19 h - 15 l h: 'a' 'c' 't' 'g' for codes 0..3 (no carries)
+    const uint32_t letter = 0x61616161u + 2u * l + 19u * h - 15u * (l & h);
+    const uint32_t x = (u | 0x20202020u) ^ letter;
+    const uint32_t nz = (((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x) & 0x80808080u;  // high bit: byte != 0
+    l4 = gather_nibble(l);
+    h4 = gather_nibble(h);
+    n4 = gather_nibble(nz >> 7);
+}
+
 // Word w of the batch.  Words below H/32 hold the halo region: 'N' padding
 // up to H - hlen, then the hlen halo bases.  Word H/32 + i holds segment
 // bytes [32 i, 32 i + 32), read as two 16-byte vectors when the segment is
@@ -48,9 +70,15 @@ k_pack(const uint8_t *__restrict__ halo, uint32_t hlen, uint32_t H, const uint8_
             const uint4 a = __ldg(v), c = __ldg(v + 1);
             const uint32_t u[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
 #pragma unroll
-            for (int j = 0; j < 8; j++)
-#pragma unroll
-                for (int b = 0; b < 4; b++) pack_byte((u[j] >> (8 * b)) & 0xffu, j * 4 + b, hi, lo, nn);
+            for (int j = 0; j < 8; j++) {
+                uint32_t h4, l4, n4;
+                pack4(u[j], h4, l4, n4);
+                hi |= h4 << (4 * j);
+                lo |= l4 << (4 * j);
+                nn |= n4 << (4 * j);
+            }
+            hi &= ~nn;
+            lo &= ~nn;
         } else {
             for (uint32_t b = 0; b < 32; b++)
                 pack_byte(o + b < slen ? seg[o + b] : 'N', b, hi, lo, nn);

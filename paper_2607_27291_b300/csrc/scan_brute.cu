@@ -64,9 +64,8 @@ k_scan_brute(Batch b, QueryTable qt, uint32_t e0, uint32_t e1, uint32_t s, uint3
     uint32_t mul[kWin];
     lane_multipliers(mul);
     const uint64_t nblk = (b.nbases + 32 * kWin - 1) / (32 * kWin);
-    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kScanWarps;
-    scan_blocks<WMAX>(b, qt, m, nent, s_nF, s_nM, e0, s, lmin, lmax, sink, wh, stage[warp], mul,
-                      static_cast<uint64_t>(blockIdx.x) * kScanWarps + warp, nblk, stride, lane);
+    scan_blocks<WMAX>(b, qt, m, nent, s_nF, s_nM, e0, s, lmin, lmax, sink, wh, stage[warp], mul, 0, nblk,
+                      blockIdx.x * kScanWarps + warp, gridDim.x * kScanWarps, lane);
     wh.finish(sink, lane);
     __syncthreads();
     flush_counts(qt, m, nent, e0, sink);

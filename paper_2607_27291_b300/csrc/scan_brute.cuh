@@ -80,48 +80,26 @@ struct Stage {
     static constexpr int kWords = kWin + WMAX;  // staged words per block
 };
 
-// Exact evaluation of one entry for the lane's WIN windows of a block without
-// N, piece boundary or ownership limits, then hit emission.  The word-0
-// counts come from the packed word v of the hot loop (byte k of v minus
-// byte k of the entry's bias is window k's word-0 count), so only words
-// 1.. are computed here.
-template <int WMAX, class WH>
-__device__ __forceinline__ void exact_fast(const Batch &b, const QueryTable &qt, const Smem &m,
-                                           const uint4 *R, uint32_t e, uint32_t e0, uint64_t p0,
-                                           uint32_t lane, uint32_t s, const HitSink &sink,
-                                           WH &wh, uint32_t &pidx, uint32_t v, uint32_t bias) {
-    const uint32_t meta = m.meta[e];
-    const uint32_t W = meta_W(meta);
-    const uint32_t se = entry_s(meta, s);
-    const uint4 *qw = m.sq + static_cast<size_t>(e) * WMAX;
-    uint32_t mm[kWin];
-#pragma unroll
-    for (int k = 0; k < kWin; k++)
-        mm[k] = meta_nN(meta) + (((v >> (8 * k)) & 0xffu) - ((bias >> (8 * k)) & 0xffu));
-#pragma unroll
-    for (int j = 1; j < WMAX; j++) {
-        if (j < static_cast<int>(W)) {
-            const uint4 q = qw[j];
-#pragma unroll
-            for (int k = 0; k < kWin; k++) {
-                const uint4 a = R[k + j], c = R[k + j + 1];
-                const uint32_t h = __funnelshift_r(a.x, c.x, lane), l = __funnelshift_r(a.y, c.y, lane);
-                mm[k] += __popc(((h ^ q.x) | (l ^ q.y)) & q.z);
-            }
+// Piece lookup for the blocks a warp visits, in increasing position: the
+// piece found last stays valid until the next piece's start, and a later
+// lookup searches only the pieces from it on.
+struct PieceCursor {
+    uint32_t idx = 0;   // piece of the last lookup
+    uint64_t next = 0;  // start of piece idx + 1 (~0 past the last); 0 before any lookup
+
+    __device__ __forceinline__ uint32_t find(const Batch &b, uint64_t p) {
+        if (p < next) return idx;
+        // the answer is in [idx, npieces) once a lookup was made (p only grows)
+        uint32_t lo = next == 0 ? 0u : idx, hi = b.npieces;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (b.pieces[mid].start <= p) lo = mid; else hi = mid;
         }
+        idx = lo;
+        next = idx + 1 < b.npieces ? b.pieces[idx + 1].start : ~0ull;
+        return idx;
     }
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < kWin; k++) any |= mm[k] <= se;
-    if (!__any_sync(0xffffffffu, any)) return;
-    if (pidx == 0xffffffffu) pidx = find_piece(b.pieces, b.npieces, p0);
-    const DevPiece pc = b.pieces[pidx];
-    const uint32_t id = qt.ids ? qt.ids[e0 + e] : e0 + e;
-    const uint32_t pos0 = static_cast<uint32_t>(pc.contig_off + (p0 + lane - pc.start));
-#pragma unroll
-    for (int k = 0; k < kWin; k++)
-        wh.emit(sink, lane, mm[k] <= se, id >> 1, pc.contig, pos0 + 32 * k, id & 1u, mm[k], m.cnt + e);
-}
+};
 
 // Generic evaluation of every entry for one window per lane (p = p0 + lane)
 // whose block may hold N, piece boundaries, the batch end or the halo.
@@ -192,6 +170,66 @@ __device__ __forceinline__ uint32_t mad(uint32_t a, uint32_t b, uint32_t c) {
     return d;
 }
 
+// Exact evaluation of one entry for the lane's kWin windows of a block
+// without N, piece boundary or ownership limits, then hit emission.  Counts
+// stay packed one byte per window: d = v - bias holds the word-0 counts
+// (see packed_counts), the entry's Ns are added to every byte, and words
+// 1.. are added by IMAD.  Word j of window k is word 0 of window k + j, so
+// it is taken from the hot loop's registers where k + j < kWin and cut from
+// the staged words otherwise.  No byte can carry: a window's count is at
+// most its query length (<= 255).
+template <int WMAX, class WH>
+__device__ __forceinline__ void exact_fast(const Batch &b, const QueryTable &qt, const Smem &m,
+                                           const uint4 *R, const uint32_t *hw, const uint32_t *lw,
+                                           const uint32_t *mul, uint32_t e, uint32_t e0, uint64_t p0,
+                                           uint32_t lane, uint32_t s, const HitSink &sink,
+                                           WH &wh, PieceCursor &pcur, uint32_t v, uint32_t bias) {
+    const uint32_t meta = m.meta[e];
+    const uint32_t W = meta_W(meta);
+    const uint32_t se = entry_s(meta, s);
+    const uint4 *qw = m.sq + static_cast<size_t>(e) * WMAX;
+    uint32_t d = v - bias + meta_nN(meta) * 0x01010101u;
+#pragma unroll
+    for (int j = 1; j < WMAX; j++) {
+        if (j < static_cast<int>(W)) {
+            const uint4 q = qw[j];
+#pragma unroll
+            for (int k = 0; k < kWin; k++) {
+                uint32_t h, l;
+                if (k + j < kWin) {
+                    h = hw[k + j];
+                    l = lw[k + j];
+                } else {
+                    const uint4 a = R[k + j], c = R[k + j + 1];
+                    h = __funnelshift_r(a.x, c.x, lane);
+                    l = __funnelshift_r(a.y, c.y, lane);
+                }
+                d = mad(__popc(((h ^ q.x) | (l ^ q.y)) & q.z), mul[k], d);
+            }
+        }
+    }
+    // byte k of hm has its high bit set when window k hits (count <= se)
+    uint32_t hm;
+    if constexpr (WMAX <= 4) {
+        // counts <= 128 (queries up to 128 bases), so for se <= 127 the
+        // byte-lane test of packed_counts applies (128 - (se + 1) + count
+        // stays below 256); se >= 128 passes every window
+        hm = se >= 128u ? 0x80808080u : ~(d + byte_bias(static_cast<int>(se))) & 0x80808080u;
+    } else {
+        hm = 0;
+#pragma unroll
+        for (int k = 0; k < kWin; k++) hm |= (((d >> (8 * k)) & 0xffu) <= se ? 0x80u : 0u) << (8 * k);
+    }
+    if (!__any_sync(0xffffffffu, hm != 0u)) return;
+    const DevPiece pc = b.pieces[pcur.find(b, p0)];
+    const uint32_t id = qt.ids ? qt.ids[e0 + e] : e0 + e;
+    const uint32_t pos0 = static_cast<uint32_t>(pc.contig_off + (p0 + lane - pc.start));
+#pragma unroll
+    for (int k = 0; k < kWin; k++)
+        wh.emit(sink, lane, (hm >> (8 * k + 7)) & 1u, id >> 1, pc.contig, pos0 + 32 * k, id & 1u,
+                (d >> (8 * k)) & 0xffu, m.cnt + e);
+}
+
 // Entry word-0 records: {hi0, lo0, bias, -} (class F) or
 // {hi0, lo0, care0, bias} (class M, MASKED).
 template <bool MASKED>
@@ -215,7 +253,7 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
                                            const uint4 *rec, const uint16_t *idx, uint32_t n,
                                            const uint32_t *hw, const uint32_t *lw, const uint32_t *mul,
                                            const uint4 *R, uint32_t e0, uint64_t p0, uint32_t lane,
-                                           uint32_t s, const HitSink &sink, WH &wh, uint32_t &pidx) {
+                                           uint32_t s, const HitSink &sink, WH &wh, PieceCursor &pcur) {
     constexpr uint32_t kHigh = 0x80808080u;
     uint32_t k = 0;
     for (; k + kGroup <= n; k += kGroup) {
@@ -237,7 +275,7 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
                 // v[i] by a select chain (no local array); the bias from the record
                 const uint32_t vi = i == 0 ? v[0] : i == 1 ? v[1] : i == 2 ? v[2] : v[3];
                 const uint4 q = rec[k + i];
-                exact_fast<WMAX>(b, qt, m, R, idx[k + i], e0, p0, lane, s, sink, wh, pidx, vi,
+                exact_fast<WMAX>(b, qt, m, R, hw, lw, mul, idx[k + i], e0, p0, lane, s, sink, wh, pcur, vi,
                                  MASKED ? q.w : q.z);
             }
         }
@@ -246,7 +284,8 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
         const uint4 q = rec[k];
         const uint32_t v = packed_counts<MASKED>(q, hw, lw, mul);
         if (__any_sync(0xffffffffu, (v & kHigh) != kHigh))
-            exact_fast<WMAX>(b, qt, m, R, idx[k], e0, p0, lane, s, sink, wh, pidx, v, MASKED ? q.w : q.z);
+            exact_fast<WMAX>(b, qt, m, R, hw, lw, mul, idx[k], e0, p0, lane, s, sink, wh, pcur, v,
+                             MASKED ? q.w : q.z);
     }
 }
 
@@ -341,18 +380,34 @@ __device__ __forceinline__ void lane_multipliers(uint32_t *mul) {
     for (int w = 0; w < kWin; w++) asm volatile("mov.u32 %0, %1;" : "=r"(mul[w]) : "r"(1u << (8 * w)));
 }
 
-// Scan blocks blk, blk + stride, ... < blk_end (of 32 * kWin windows) with
-// this warp, staging words through stage[2][NW] (this warp's buffers).
+// Blocks (of 32 * kWin windows) are dealt to the nw warps of a range in
+// chunks of kChunk consecutive blocks, round robin: warp w scans blocks
+// base + w * kChunk + j * nw * kChunk + i (i < kChunk) below blk_end.  The
+// warps together sweep the range front to back, so their reads share DRAM
+// pages, while each warp still moves forward through the pieces.  Words are
+// staged through stage[2][NW] (this warp's buffers), one block ahead.
+#ifndef IFA_SCAN_CHUNK
+#define IFA_SCAN_CHUNK 1  // measured on B300: 1 beats 4, 8 and 32 at maxSubs 4 and 16
+#endif
+constexpr uint32_t kChunk = IFA_SCAN_CHUNK;
 template <int WMAX, class WH>
 __device__ __forceinline__ void scan_blocks(const Batch &b, const QueryTable &qt, const Smem &m, uint32_t nent,
                                             uint32_t nF, uint32_t nM, uint32_t e0, uint32_t s, uint32_t lmin,
                                             uint32_t lmax, const HitSink &sink, WH &wh,
                                             uint4 (*stage)[Stage<WMAX>::kWords], const uint32_t *mul,
-                                            uint64_t blk, uint64_t blk_end, uint64_t stride, uint32_t lane) {
+                                            uint64_t base, uint64_t blk_end, uint32_t w, uint32_t nw,
+                                            uint32_t lane) {
     constexpr int NW = Stage<WMAX>::kWords;
+    PieceCursor pcur;
+    const uint64_t jump = static_cast<uint64_t>(nw - 1) * kChunk;
+    uint64_t blk = base + static_cast<uint64_t>(w) * kChunk;
+    uint32_t in_chunk = 0;
+    uint64_t nxt = blk;
     if (blk < blk_end) stage_block<NW>(b, blk, stage[0], lane);
-    for (uint32_t it = 0; blk < blk_end; it++, blk += stride) {
-        const uint64_t nxt = blk + stride;
+    for (uint32_t it = 0; blk < blk_end; it++, blk = nxt) {
+        const bool chunk_end = in_chunk + 1 == kChunk;
+        nxt = chunk_end ? blk + 1 + jump : blk + 1;
+        in_chunk = chunk_end ? 0u : in_chunk + 1;
         if (nxt < blk_end) stage_block<NW>(b, nxt, stage[(it + 1) & 1], lane);
         else asm volatile("cp.async.commit_group;\n" ::: "memory");
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
@@ -380,9 +435,8 @@ __device__ __forceinline__ void scan_blocks(const Batch &b, const QueryTable &qt
             hw[k] = __funnelshift_r(R[k].x, R[k + 1].x, lane);
             lw[k] = __funnelshift_r(R[k].y, R[k + 1].y, lane);
         }
-        uint32_t pidx = 0xffffffffu;
-        scan_class<WMAX, false>(b, qt, m, m.sF, m.fidx, nF, hw, lw, mul, R, e0, p0, lane, s, sink, wh, pidx);
-        scan_class<WMAX, true>(b, qt, m, m.sM, m.midx, nM, hw, lw, mul, R, e0, p0, lane, s, sink, wh, pidx);
+        scan_class<WMAX, false>(b, qt, m, m.sF, m.fidx, nF, hw, lw, mul, R, e0, p0, lane, s, sink, wh, pcur);
+        scan_class<WMAX, true>(b, qt, m, m.sM, m.midx, nM, hw, lw, mul, R, e0, p0, lane, s, sink, wh, pcur);
         __syncwarp();
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");

@@ -103,3 +103,34 @@ def test_store_errors():
         assert ei.value.status == P.IFA_ERR_INVALID_ARG
     finally:
         P.ifa_destroy(h)
+
+
+def test_per_set_subs_at_query_length():
+    """Per-set maxSubs at and above the query length on the fast path: a
+    128-base query against a poly-A contig mismatches every base of every
+    window (count 128), so maxSubs 128 keeps every window and 127 none;
+    other sets mix 100-128 bp queries with maxSubs 60 and 200."""
+    import types
+    rng = np.random.default_rng(5)
+    contig0 = np.full(3000, ord("A"), np.uint8)
+    contig1 = np.frombuffer(bytes(rng.choice(list(b"ACGT"), 2000).astype(np.uint8)), np.uint8)
+    wl = types.SimpleNamespace(ref=np.concatenate([contig0, contig1]),
+                               contig_len=np.array([3000, 2000], np.int64))
+    specs = [([b"C" * 128], 128), ([b"C" * 128], 127), ([b"G" * 100 + b"T" * 28], 200),
+             (synth.random_queries(3, 100, 128, 9), 60), (synth.random_queries(2, 120, 128, 10), 128)]
+    h = P.ifa_create(hit_capacity=1 << 20, segment_bytes=1 << 16)
+    try:
+        _store(h, wl, 1 << 12)
+        firsts = [P.ifa_set_add(h, qs, s, P.IFA_MODE_BRUTE)[1] for qs, s in specs]
+        P.ifa_batch_run(h, P.IFA_BATCH_PERSISTENT, len(specs))
+        hits, over = P.ifa_drain_hits(h)
+        assert not over
+    finally:
+        P.ifa_destroy(h)
+    expect = []
+    for (qs, s), first in zip(specs, firsts):
+        expect.extend(tuples(_shift(oracle.brute(qs, wl.ref, wl.contig_len, s), first)))
+    # maxSubs = L keeps every window of both contigs; 127 drops the poly-A contig
+    assert len([x for x in expect if x[0] == firsts[0]]) == 2 * (3000 - 127) + 2 * (2000 - 127)
+    assert not [x for x in expect if x[0] == firsts[1] and x[1] == 0]
+    assert tuples(P.sort_hits(hits)) == sorted(expect)
