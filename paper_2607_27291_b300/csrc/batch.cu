@@ -377,7 +377,7 @@ ifa_status build_plan(ifa_handle *h) {
         for (uint32_t q = 0; q < nq; q++) seeded[q] = idx_in[q] && !plan_all.plan_exhaustive[q];
         st = indexed_plan_q(B.merged, h->qs, svec, seeded, h->cfg, h->stream, h->err);
         if (st != IFA_OK) return st;
-        st = indexed_tables(B.merged, h->qs, h->qmeta_host, h->qwords_host, wmax, h->cfg, h->err);
+        st = indexed_tables(B.merged, h->qs, h->qmeta_host, h->qwords_host, wmax, h->cfg, h->stream, h->err);
         if (st != IFA_OK) return st;
     }
     // per-set tables for the per-set baseline
@@ -390,7 +390,7 @@ ifa_status build_plan(ifa_handle *h) {
         if (std::none_of(mine.begin(), mine.end(), [](uint8_t x) { return x != 0; })) continue;
         st = indexed_plan_q(*B.per_set.back(), h->qs, svec, mine, h->cfg, h->stream, h->err);
         if (st != IFA_OK) return st;
-        st = indexed_tables(*B.per_set.back(), h->qs, h->qmeta_host, h->qwords_host, wmax, h->cfg, h->err);
+        st = indexed_tables(*B.per_set.back(), h->qs, h->qmeta_host, h->qwords_host, wmax, h->cfg, h->stream, h->err);
         if (st != IFA_OK) return st;
         cudaMalloc(&B.per_set.back()->d_candidates, sizeof(unsigned long long));
     }
@@ -494,7 +494,7 @@ ifa_status calibrate(ifa_handle *h) {
     if (pick < nq && e == cudaSuccess) {
         in[pick] = 1;
         st = indexed_plan_q(one, h->qs, svec, in, h->cfg, h->stream, h->err);
-        if (st == IFA_OK) st = indexed_tables(one, h->qs, h->qmeta_host, h->qwords_host, h->wmax, h->cfg, h->err);
+        if (st == IFA_OK) st = indexed_tables(one, h->qs, h->qmeta_host, h->qwords_host, h->wmax, h->cfg, h->stream, h->err);
         if (st == IFA_OK && one.targ.n) {
             cudaMalloc(&one.d_candidates, sizeof(unsigned long long));
             cudaMemset(one.d_candidates, 0, sizeof(unsigned long long));
@@ -517,7 +517,7 @@ ifa_status calibrate(ifa_handle *h) {
             c8.minhits_num = 1;
             c8.minhits_den = 1;  // deterministic bound: no Monte Carlo
             st = indexed_plan_q(dense, h->qs, svec, all, c8, h->stream, h->err);
-            if (st == IFA_OK) st = indexed_tables(dense, h->qs, h->qmeta_host, h->qwords_host, h->wmax, c8, h->err);
+            if (st == IFA_OK) st = indexed_tables(dense, h->qs, h->qmeta_host, h->qwords_host, h->wmax, c8, h->stream, h->err);
             if (st == IFA_OK && dense.targ.n) {
                 cudaMalloc(&dense.d_candidates, sizeof(unsigned long long));
                 cudaMemset(dense.d_candidates, 0, sizeof(unsigned long long));

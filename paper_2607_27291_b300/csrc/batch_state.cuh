@@ -117,7 +117,7 @@ struct ServeState {
     uint32_t slice = 0;
     bool dirty = true;
     // plan of the active set
-    std::vector<void *> allocs;
+    DevBufs pool;
     uint32_t wmax = 1;
     uint32_t nq = 0;
     QueryTable ft{};

@@ -23,6 +23,9 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <utility>
+#include <vector>
+
 #include "ifa.h"
 
 namespace ifa {
@@ -51,6 +54,36 @@ struct RingDesc {
     unsigned long long cap;
     uint32_t qfirst;
     uint32_t pad;
+};
+
+// Grow-only device buffers addressed by slot, kept across rebuilds of a
+// plan so that a rebuild allocates nothing once sizes have settled.  Reuse
+// is ordered by the stream the plan's work runs on; growing frees the old
+// buffer (cudaFree waits for the device).
+struct DevBufs {
+    std::vector<std::pair<void *, size_t>> b;
+
+    void *get(size_t slot, size_t bytes, cudaError_t &e) {
+        if (e != cudaSuccess) return nullptr;
+        if (b.size() <= slot) b.resize(slot + 1, {nullptr, 0});
+        auto &x = b[slot];
+        if (x.second < bytes || !x.first) {
+            const bool grew = x.first != nullptr;
+            cudaFree(x.first);
+            x = {nullptr, 0};
+            // exact on first use; a quarter of headroom once a slot has had to grow
+            size_t want = grew ? bytes + bytes / 4 : bytes;
+            if (want < 256) want = 256;
+            e = cudaMalloc(&x.first, want);
+            if (e != cudaSuccess) return nullptr;
+            x.second = want;
+        }
+        return x.first;
+    }
+    void release() {
+        for (auto &x : b) cudaFree(x.first);
+        b.clear();
+    }
 };
 
 struct HitSink {

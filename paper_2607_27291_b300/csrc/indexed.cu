@@ -123,14 +123,9 @@ cudaError_t launch_seed_scan(const Batch &b, const QueryTable &qt, const KTables
 }
 
 void IndexedState::free_tables() {
-    for (void *p : allocs) cudaFree(p);
-    allocs.clear();
+    // the buffers stay for the next build; only the plan's view is dropped
     targ = KTablesArg{};
-    cudaFree(d_entry_minhits);
     d_entry_minhits = nullptr;
-    cudaFree(d_ex_words);
-    cudaFree(d_ex_meta);
-    cudaFree(d_ex_ids);
     d_ex_words = nullptr;
     d_ex_meta = nullptr;
     d_ex_ids = nullptr;
@@ -142,6 +137,7 @@ void IndexedState::free_tables() {
 
 void IndexedState::release() {
     free_tables();
+    bufs.release();
     cudaFree(d_candidates);
     d_candidates = nullptr;
 }
@@ -311,7 +307,8 @@ ifa_status indexed_plan(IndexedState &S, const std::vector<std::string> &qs, con
 
 ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
                           const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
-                          uint32_t wmax, const ifa_config &cfg, std::string &err) {
+                          uint32_t wmax, const ifa_config &cfg, cudaStream_t st, std::string &err) {
+    enum : size_t { kWords, kEmh, kEnts, kFirst, kKeys, kPv, kSums, kExWords, kExMeta, kExIds, kTab0 };
     S.free_tables();
     S.wmax = wmax;
     S.step = cfg.kmer_step;
@@ -319,105 +316,79 @@ ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
     auto ck = [&](cudaError_t x) {
         if (e == cudaSuccess && x != cudaSuccess) e = x;
     };
-    auto dalloc = [&](size_t bytes) -> void * {
-        void *p = nullptr;
-        ck(cudaMalloc(&p, bytes ? bytes : 4));
-        if (p) S.allocs.push_back(p);
-        return p;
+    // host -> device on st; pageable sources are staged by the driver before
+    // the call returns, so the host vectors may go right after
+    auto put = [&](void *d, const void *h, size_t bytes) {
+        if (e == cudaSuccess && bytes) ck(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st));
     };
     const uint32_t nq = static_cast<uint32_t>(qs.size());
     if (!S.d_candidates) {
         ck(cudaMalloc(&S.d_candidates, sizeof(unsigned long long)));
-        ck(cudaMemset(S.d_candidates, 0, sizeof(unsigned long long)));
+        ck(cudaMemsetAsync(S.d_candidates, 0, sizeof(unsigned long long), st));
     }
     // per-entry thresholds
-    std::vector<uint32_t> emh(2 * nq);
+    std::vector<uint32_t> emh(2 * static_cast<size_t>(nq));
     for (uint32_t q = 0; q < nq; q++) emh[2 * q] = emh[2 * q + 1] = S.plan_minhits[q];
-    ck(cudaMalloc(&S.d_entry_minhits, emh.size() * sizeof(uint32_t)));
-    ck(cudaMemcpy(S.d_entry_minhits, emh.data(), emh.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    S.d_entry_minhits = static_cast<uint32_t *>(S.bufs.get(kEmh, emh.size() * sizeof(uint32_t), e));
+    put(S.d_entry_minhits, emh.data(), emh.size() * sizeof(uint32_t));
     // tables per distinct k among seeded queries
     std::vector<uint32_t> ks;
     for (uint32_t q = 0; q < nq; q++)
-        if (!S.plan_exhaustive[q]) ks.push_back(S.plan_k[q]);
+        if (S.plan_in[q] && !S.plan_exhaustive[q]) ks.push_back(S.plan_k[q]);
     std::sort(ks.begin(), ks.end());
     ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
-    S.targ.n = static_cast<uint32_t>(ks.size());
-    for (size_t ti = 0; ti < ks.size() && e == cudaSuccess; ti++) {
-        const uint32_t k = ks[ti];
-        const uint32_t care = care_mask(k, cfg.mask_width);
-        std::vector<uint32_t> kk, pv;  // (key, posting) pairs
-        for (uint32_t q = 0; q < nq; q++) {
-            if (!S.plan_in[q] || S.plan_exhaustive[q] || S.plan_k[q] != k) continue;
-            const uint32_t L = static_cast<uint32_t>(qs[q].size());
-            for (uint32_t t = 0; t < 2; t++)
-                for (uint32_t o = 0; o + k <= L; o += cfg.kmer_step) {
-                    kk.push_back(query_key(qs[q], t == 1, o, k, care));
-                    pv.push_back(((2 * q + t) << 8) | o);
-                }
-        }
-        const size_t np = kk.size();
-        KTableDev &T = S.targ.t[ti];
-        T.k = k;
-        T.care = care;
-        std::vector<uint32_t> post(np);
-        if (k <= kDirectMaxK) {
-            // counting sort straight into the direct-address offsets
-            const size_t nkeys = size_t(1) << (2 * k);
-            std::vector<uint32_t> off(nkeys + 1, 0);
-            for (size_t i = 0; i < np; i++) off[kk[i] + 1]++;
-            for (size_t i = 0; i < nkeys; i++) off[i + 1] += off[i];
-            std::vector<uint32_t> cur(off.begin(), off.end() - 1);
-            for (size_t i = 0; i < np; i++) post[cur[kk[i]]++] = pv[i];
-            uint32_t *doff = static_cast<uint32_t *>(dalloc(off.size() * sizeof(uint32_t)));
-            if (doff) ck(cudaMemcpy(doff, off.data(), off.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-            T.direct = 1;
-            T.off = doff;
-            T.keys = nullptr;
-            T.bits = nullptr;
-            T.nuniq = 0;
-        } else {
-            // two 16-bit LSD radix passes over (key, posting), then distinct keys
-            std::vector<uint32_t> k2(np), p2(np);
-            for (int pass = 0; pass < 2; pass++) {
-                const int sh = 16 * pass;
-                std::vector<uint32_t> cnt(65537, 0);
-                for (size_t i = 0; i < np; i++) cnt[((kk[i] >> sh) & 0xffffu) + 1]++;
-                for (size_t i = 0; i < 65536; i++) cnt[i + 1] += cnt[i];
-                for (size_t i = 0; i < np; i++) {
-                    const uint32_t d = cnt[(kk[i] >> sh) & 0xffffu]++;
-                    k2[d] = kk[i];
-                    p2[d] = pv[i];
-                }
-                kk.swap(k2);
-                pv.swap(p2);
-            }
-            post = pv;
-            std::vector<uint32_t> keys, off;
-            for (size_t i = 0; i < np; i++) {
-                if (i == 0 || kk[i] != kk[i - 1]) {
-                    keys.push_back(kk[i]);
-                    off.push_back(static_cast<uint32_t>(i));
+    if (!ks.empty()) {
+        const uint4 *d_words = static_cast<const uint4 *>(S.bufs.get(kWords, qwords.size() * sizeof(uint4), e));
+        put(const_cast<uint4 *>(d_words), qwords.data(), qwords.size() * sizeof(uint4));
+        S.targ.n = static_cast<uint32_t>(ks.size());
+        for (size_t ti = 0; ti < ks.size() && e == cudaSuccess; ti++) {
+            const uint32_t k = ks[ti];
+            const uint32_t care = care_mask(k, cfg.mask_width);
+            // entries of this table and their first posting
+            std::vector<uint32_t> ents, first{0};
+            for (uint32_t q = 0; q < nq; q++) {
+                if (!S.plan_in[q] || S.plan_exhaustive[q] || S.plan_k[q] != k) continue;
+                const uint32_t L = static_cast<uint32_t>(qs[q].size());
+                const uint32_t n_off = L >= k ? (L - k) / cfg.kmer_step + 1 : 0;
+                for (uint32_t t = 0; t < 2; t++) {
+                    ents.push_back(2 * q + t);
+                    first.push_back(first.back() + n_off);
                 }
             }
-            off.push_back(static_cast<uint32_t>(np));
-            const size_t nbits = size_t(1) << (2 * k);
-            std::vector<uint32_t> bits(nbits / 32, 0);
-            for (uint32_t key : keys) bits[key >> 5] |= 1u << (key & 31);
-            uint32_t *dk = static_cast<uint32_t *>(dalloc(keys.size() * sizeof(uint32_t)));
-            uint32_t *doff = static_cast<uint32_t *>(dalloc(off.size() * sizeof(uint32_t)));
-            uint32_t *db = static_cast<uint32_t *>(dalloc(bits.size() * sizeof(uint32_t)));
-            if (dk && !keys.empty()) ck(cudaMemcpy(dk, keys.data(), keys.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-            if (doff) ck(cudaMemcpy(doff, off.data(), off.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-            if (db) ck(cudaMemcpy(db, bits.data(), bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-            T.direct = 0;
-            T.off = doff;
-            T.keys = dk;
-            T.bits = db;
-            T.nuniq = static_cast<uint32_t>(keys.size());
+            const uint32_t np = first.back();
+            const bool direct = k <= kDirectMaxK;
+            const uint64_t nkeys = 1ull << (2 * k);
+            const uint64_t noff = direct ? nkeys + 3 : static_cast<uint64_t>(np) + 3;
+            const uint64_t nbw = direct ? 0 : nkeys / 32;
+            uint32_t *d_ents = static_cast<uint32_t *>(S.bufs.get(kEnts, ents.size() * sizeof(uint32_t), e));
+            uint32_t *d_first = static_cast<uint32_t *>(S.bufs.get(kFirst, first.size() * sizeof(uint32_t), e));
+            uint32_t *d_keys = static_cast<uint32_t *>(S.bufs.get(kKeys, std::max<size_t>(np, 1) * sizeof(uint32_t), e));
+            uint32_t *d_pv = static_cast<uint32_t *>(S.bufs.get(kPv, std::max<size_t>(np, 1) * sizeof(uint32_t), e));
+            uint32_t *d_sums = static_cast<uint32_t *>(
+                S.bufs.get(kSums, device_scan_sums_words(std::max(noff, nbw)) * sizeof(uint32_t), e));
+            uint32_t *d_off = static_cast<uint32_t *>(S.bufs.get(kTab0 + 4 * ti, noff * sizeof(uint32_t), e));
+            uint32_t *d_bits = direct ? nullptr
+                                      : static_cast<uint32_t *>(S.bufs.get(kTab0 + 4 * ti + 1, nbw * sizeof(uint32_t), e));
+            uint32_t *d_rank = direct ? nullptr
+                                      : static_cast<uint32_t *>(S.bufs.get(kTab0 + 4 * ti + 2, nbw * sizeof(uint32_t), e));
+            uint32_t *d_post = static_cast<uint32_t *>(
+                S.bufs.get(kTab0 + 4 * ti + 3, std::max<size_t>(np, 1) * sizeof(uint32_t), e));
+            put(d_ents, ents.data(), ents.size() * sizeof(uint32_t));
+            put(d_first, first.data(), first.size() * sizeof(uint32_t));
+            if (e == cudaSuccess)
+                ck(launch_postings(d_words, wmax, d_ents, d_first, static_cast<uint32_t>(ents.size()), k, care,
+                                   cfg.kmer_step, d_keys, d_pv, st));
+            if (e == cudaSuccess) ck(build_table(k, direct, d_keys, d_pv, np, d_off, d_bits, d_rank, d_post, d_sums, st));
+            KTableDev &T = S.targ.t[ti];
+            T.k = k;
+            T.care = care;
+            T.direct = direct ? 1u : 0u;
+            T.pad = 0;
+            T.off = d_off ? d_off + 2 : nullptr;
+            T.rank = d_rank;
+            T.bits = d_bits;
+            T.post = d_post;
         }
-        uint32_t *dpost = static_cast<uint32_t *>(dalloc(post.size() * sizeof(uint32_t)));
-        if (dpost && np) ck(cudaMemcpy(dpost, post.data(), post.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-        T.post = dpost;
     }
     // exhaustive queries: compact table for the brute-force kernel
     std::vector<uint32_t> exq;
@@ -429,20 +400,18 @@ ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
         std::vector<uint32_t> ids(ne), meta(ne);
         std::vector<uint4> words(static_cast<size_t>(ne) * wmax);
         S.ex_entries = ne;
-        ck(cudaMalloc(&S.d_ex_words, static_cast<size_t>(ne) * wmax * sizeof(uint4)));
-        ck(cudaMalloc(&S.d_ex_meta, ne * sizeof(uint32_t)));
-        ck(cudaMalloc(&S.d_ex_ids, ne * sizeof(uint32_t)));
+        S.d_ex_words = static_cast<uint4 *>(S.bufs.get(kExWords, words.size() * sizeof(uint4), e));
+        S.d_ex_meta = static_cast<uint32_t *>(S.bufs.get(kExMeta, ne * sizeof(uint32_t), e));
+        S.d_ex_ids = static_cast<uint32_t *>(S.bufs.get(kExIds, ne * sizeof(uint32_t), e));
         for (uint32_t i = 0; i < ne; i++) {
             const uint32_t src = 2 * exq[i / 2] + (i & 1);
             ids[i] = src;
             meta[i] = qmeta[src];
             for (uint32_t w = 0; w < wmax; w++) words[static_cast<size_t>(i) * wmax + w] = qwords[static_cast<size_t>(src) * wmax + w];
         }
-        if (e == cudaSuccess) {
-            ck(cudaMemcpy(S.d_ex_words, words.data(), words.size() * sizeof(uint4), cudaMemcpyHostToDevice));
-            ck(cudaMemcpy(S.d_ex_meta, meta.data(), ne * sizeof(uint32_t), cudaMemcpyHostToDevice));
-            ck(cudaMemcpy(S.d_ex_ids, ids.data(), ne * sizeof(uint32_t), cudaMemcpyHostToDevice));
-        }
+        put(S.d_ex_words, words.data(), words.size() * sizeof(uint4));
+        put(S.d_ex_meta, meta.data(), ne * sizeof(uint32_t));
+        put(S.d_ex_ids, ids.data(), ne * sizeof(uint32_t));
         uint32_t cap = scan_brute_chunk_entries(wmax) & ~1u;
         if (cap < 2) cap = 2;
         for (uint32_t e0 = 0; e0 < ne; e0 += cap) {
@@ -470,7 +439,7 @@ ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
     ifa_status r = indexed_plan(S, qs, cfg, s, st, err);
     if (r != IFA_OK) return r;
     if (S.tables_valid && S.tables_s == s && S.wmax == wmax) return IFA_OK;
-    r = indexed_tables(S, qs, qmeta, qwords, wmax, cfg, err);
+    r = indexed_tables(S, qs, qmeta, qwords, wmax, cfg, st, err);
     if (r != IFA_OK) return r;
     S.tables_s = s;
     return IFA_OK;

@@ -15,15 +15,17 @@ constexpr uint32_t kDirectMaxK = 12;   // k <= 12: direct-address offsets (4^k +
 
 // One seed length's query k-mer table.  Keys are "planar": the k hi-plane
 // bits of the k-mer above its k lo-plane bits (masked positions zeroed), an
-// injective code of the unmasked bases.  Postings are (entry << 8 | offset).
+// injective code of the unmasked bases.  Postings are (entry << 8 | offset);
+// the postings of a key are post[off[x] .. off[x + 1]) with x the key
+// (direct) or the key's rank among the present keys (ranked).
 struct KTableDev {
     uint32_t k;
     uint32_t care;         // k-bit mask of the positions that count
     uint32_t direct;       // 1: off[] indexed by key
-    uint32_t nuniq;        // hashed: number of distinct keys
-    const uint32_t *off;   // direct: 4^k + 1; hashed: nuniq + 1
-    const uint32_t *keys;  // hashed: sorted distinct keys
-    const uint32_t *bits;  // hashed: presence bitmap of 4^k bits
+    uint32_t pad;
+    const uint32_t *off;   // direct: 4^k + 1 words; ranked: present keys + 1
+    const uint32_t *rank;  // ranked: keys present before each bitmap word
+    const uint32_t *bits;  // ranked: presence bitmap of 4^k bits
     const uint32_t *post;  // postings grouped by key
 };
 
@@ -41,11 +43,12 @@ struct IndexedState {
     std::vector<uint8_t> plan_exhaustive;
     std::vector<uint8_t> plan_in;  // query is part of this plan
 
-    // device tables for tables_s
+    // device tables for tables_s, in grow-only buffers kept across rebuilds
+    // (slot -> (pointer, bytes)); released by release()
     bool tables_valid = false;
     uint32_t tables_s = 0;
     KTablesArg targ{};
-    std::vector<void *> allocs;
+    DevBufs bufs;
     uint32_t *d_entry_minhits = nullptr;
     unsigned long long *d_candidates = nullptr;
     uint32_t wmax = 1;
@@ -89,10 +92,21 @@ ifa_status indexed_plan_q(IndexedState &S, const std::vector<std::string> &qs,
                           const ifa_config &cfg, cudaStream_t st, std::string &err);
 
 // Device tables of the current plan (seeded queries) and the compact table of
-// its exhaustive queries.
+// its exhaustive queries, built on stream st (ordered before later work on
+// st; the host does not wait).
 ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
                           const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
-                          uint32_t wmax, const ifa_config &cfg, std::string &err);
+                          uint32_t wmax, const ifa_config &cfg, cudaStream_t st, std::string &err);
+
+// Device table construction (ktables.cu).
+uint64_t device_scan_sums_words(uint64_t n);
+cudaError_t device_scan(const uint32_t *in, uint32_t *out, uint64_t n, bool popc, bool exclusive,
+                        uint32_t *sums, cudaStream_t st);
+cudaError_t launch_postings(const uint4 *words, uint32_t wmax, const uint32_t *ents, const uint32_t *first,
+                            uint32_t nents, uint32_t k, uint32_t care, uint32_t step, uint32_t *keys,
+                            uint32_t *pv, cudaStream_t st);
+cudaError_t build_table(uint32_t k, bool direct, uint32_t *keys, const uint32_t *pv, uint32_t np, uint32_t *off,
+                        uint32_t *bits, uint32_t *rank, uint32_t *post, uint32_t *sums, cudaStream_t st);
 
 ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
                            const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,

@@ -35,15 +35,14 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                 if (T.direct) {
                     beg = __ldg(T.off + key);
                     end = __ldg(T.off + key + 1);
-                } else if ((__ldg(T.bits + (key >> 5)) >> (key & 31)) & 1u) {
-                    uint32_t lo = 0, hi = T.nuniq;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (__ldg(T.keys + mid) < key) lo = mid + 1; else hi = mid;
-                    }
-                    if (lo < T.nuniq && __ldg(T.keys + lo) == key) {
-                        beg = __ldg(T.off + lo);
-                        end = __ldg(T.off + lo + 1);
+                } else {
+                    // ranked: bitmap word and the rank of its first bit, then
+                    // the key's rank among the present keys
+                    const uint32_t w = key >> 5, bw = __ldg(T.bits + w);
+                    if ((bw >> (key & 31u)) & 1u) {
+                        const uint32_t r = __ldg(T.rank + w) + __popc(bw & ((1u << (key & 31u)) - 1u));
+                        beg = __ldg(T.off + r);
+                        end = __ldg(T.off + r + 1);
                     }
                 }
             }

@@ -42,27 +42,23 @@ ifa_status sfail(ifa_handle *h, ifa_status st, const std::string &msg) {
                          std::string(#call) + ": " + cudaGetErrorString(e_));              \
     } while (0)
 
-void free_serve_plan(ServeState &S) {
-    for (void *p : S.allocs) cudaFree(p);
-    S.allocs.clear();
-    S.merged.release();
-}
+// The plan's device arrays live in S.pool (grow-only, one slot per array)
+// and the merged k-mer tables in S.merged's own buffers, so a rebuild at a
+// slice boundary allocates nothing once sizes have settled.
+enum PlanSlot : size_t { kPWords, kPMeta, kPBw, kPBm, kPIds, kPC0, kPC1, kPCl, kPCh, kPQ2r, kPRings, kPQc };
+
+void free_serve_plan(ServeState &S) { S.merged.free_tables(); }
 
 template <typename T>
-T *salloc(ServeState &S, size_t n, cudaError_t &e) {
-    void *p = nullptr;
-    const cudaError_t r = cudaMalloc(&p, std::max<size_t>(1, n) * sizeof(T));
-    if (r != cudaSuccess) {
-        if (e == cudaSuccess) e = r;
-        return nullptr;
-    }
-    S.allocs.push_back(p);
-    return static_cast<T *>(p);
+T *salloc(ServeState &S, PlanSlot slot, size_t n, cudaError_t &e) {
+    return static_cast<T *>(S.pool.get(slot, std::max<size_t>(1, n) * sizeof(T), e));
 }
 
+// Stream-ordered upload (pageable source: staged before the call returns).
 template <typename T>
-void sput(T *d, const std::vector<T> &v, cudaError_t &e) {
-    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+void sput(T *d, const std::vector<T> &v, cudaStream_t st, cudaError_t &e) {
+    if (e == cudaSuccess && !v.empty())
+        e = cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
 }
 
 // Bytes a request is charged against the HBM budget: its ring and counters
@@ -114,7 +110,7 @@ ifa_status build_serve_plan(ifa_handle *h) {
     }
     if (std::any_of(seeded.begin(), seeded.end(), [](uint8_t x) { return x != 0; })) {
         st = indexed_plan_q(S.merged, aq, as, seeded, h->cfg, h->stream, h->err);
-        if (st == IFA_OK) st = indexed_tables(S.merged, aq, meta, words, wmax, h->cfg, h->err);
+        if (st == IFA_OK) st = indexed_tables(S.merged, aq, meta, words, wmax, h->cfg, h->stream, h->err);
         if (st != IFA_OK) return st;
     }
     // compact brute table (brute requests and exhaustive indexed queries)
@@ -156,28 +152,29 @@ ifa_status build_serve_plan(ifa_handle *h) {
         rings[slot].pad = 0;
     }
     cudaError_t e = cudaSuccess;
-    uint4 *d_words = salloc<uint4>(S, words.size(), e);
-    uint32_t *d_meta = salloc<uint32_t>(S, meta.size(), e);
-    uint4 *d_bw = salloc<uint4>(S, bw.size(), e);
-    uint32_t *d_bm = salloc<uint32_t>(S, bm.size(), e);
-    uint32_t *d_ids = salloc<uint32_t>(S, ids.size(), e);
-    uint32_t *d_c0 = salloc<uint32_t>(S, c0.size(), e), *d_c1 = salloc<uint32_t>(S, c1.size(), e);
-    uint32_t *d_cl = salloc<uint32_t>(S, cl.size(), e), *d_ch = salloc<uint32_t>(S, ch.size(), e);
-    uint32_t *d_q2r = salloc<uint32_t>(S, q2r.size(), e);
-    RingDesc *d_rings = salloc<RingDesc>(S, rings.size(), e);
-    unsigned long long *d_qc = salloc<unsigned long long>(S, nq, e);
-    sput(d_words, words, e);
-    sput(d_meta, meta, e);
-    sput(d_bw, bw, e);
-    sput(d_bm, bm, e);
-    sput(d_ids, ids, e);
-    sput(d_c0, c0, e);
-    sput(d_c1, c1, e);
-    sput(d_cl, cl, e);
-    sput(d_ch, ch, e);
-    sput(d_q2r, q2r, e);
-    sput(d_rings, rings, e);
-    if (e == cudaSuccess) e = cudaMemset(d_qc, 0, std::max<size_t>(1, nq) * sizeof(unsigned long long));
+    const cudaStream_t st_ = h->stream;
+    uint4 *d_words = salloc<uint4>(S, kPWords, words.size(), e);
+    uint32_t *d_meta = salloc<uint32_t>(S, kPMeta, meta.size(), e);
+    uint4 *d_bw = salloc<uint4>(S, kPBw, bw.size(), e);
+    uint32_t *d_bm = salloc<uint32_t>(S, kPBm, bm.size(), e);
+    uint32_t *d_ids = salloc<uint32_t>(S, kPIds, ids.size(), e);
+    uint32_t *d_c0 = salloc<uint32_t>(S, kPC0, c0.size(), e), *d_c1 = salloc<uint32_t>(S, kPC1, c1.size(), e);
+    uint32_t *d_cl = salloc<uint32_t>(S, kPCl, cl.size(), e), *d_ch = salloc<uint32_t>(S, kPCh, ch.size(), e);
+    uint32_t *d_q2r = salloc<uint32_t>(S, kPQ2r, q2r.size(), e);
+    RingDesc *d_rings = salloc<RingDesc>(S, kPRings, rings.size(), e);
+    unsigned long long *d_qc = salloc<unsigned long long>(S, kPQc, nq, e);
+    sput(d_words, words, st_, e);
+    sput(d_meta, meta, st_, e);
+    sput(d_bw, bw, st_, e);
+    sput(d_bm, bm, st_, e);
+    sput(d_ids, ids, st_, e);
+    sput(d_c0, c0, st_, e);
+    sput(d_c1, c1, st_, e);
+    sput(d_cl, cl, st_, e);
+    sput(d_ch, ch, st_, e);
+    sput(d_q2r, q2r, st_, e);
+    sput(d_rings, rings, st_, e);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_qc, 0, std::max<size_t>(1, nq) * sizeof(unsigned long long), st_);
     if (e != cudaSuccess) return sfail(h, IFA_ERR_CUDA, std::string("serve plan: ") + cudaGetErrorString(e));
     S.ft = QueryTable{d_words, d_meta, nullptr, 2 * nq, wmax};
     S.bt = QueryTable{d_bw, d_bm, d_ids, static_cast<uint32_t>(ids.size()), wmax};
@@ -220,6 +217,8 @@ namespace ifa {
 void serve_release(ifa_handle *h) {
     ServeState &S = h->serve;
     free_serve_plan(S);
+    S.merged.release();
+    S.pool.release();
     for (Request &r : S.reqs) {
         cudaFree(r.d_ring);
         cudaFree(r.d_counters);

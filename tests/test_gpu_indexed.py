@@ -79,7 +79,8 @@ def test_indexed_matches_oracle(s, seg_bytes):
     assert set(tuples(got)) <= brute
 
 
-@pytest.mark.parametrize("step,mask_w,klist", [(2, 0, (8, 10)), (1, 2, (9, 11)), (3, 1, (6, 7))])
+@pytest.mark.parametrize("step,mask_w,klist", [(2, 0, (8, 10)), (1, 2, (9, 11)), (3, 1, (6, 7)),
+                                                (1, 0, (13, 15)), (2, 1, (14, 16))])
 def test_indexed_step_and_mask(step, mask_w, klist):
     wl = synth.small_workload(seed=43, n_queries=8, lmin=14, lmax=40, n_contigs=10, cmin=100,
                               cmax=3000, plant_ks=[0, 1, 2, 3] * 4)
