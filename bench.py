@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--rate", type=float, default=50.0, help="serving: arrivals per second")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
     ap.add_argument("--slices", type=int, default=16, help="serving: slices per cycle")
+    ap.add_argument("--no-solo", action="store_true", help="serving: skip the one-request-at-a-time baseline")
+    ap.add_argument("--solo-max-s", type=float, default=180.0,
+                    help="serving: wall-time cap of the one-request-at-a-time baseline")
     return ap.parse_args()
 
 
@@ -455,9 +458,67 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_trace(P, h, reqs, slices, budget, max_wall):
+    """Replay the arrival trace through the serving loop; budget = HBM bytes
+    for admission (1 admits one request at a time).  Stops early after
+    max_wall seconds, leaving later requests unfinished."""
+    P.ifa_serve_start(h, slices, budget, 1 << 20)
+    ids = []
+    open_ids = []   # submitted, not yet drained
+    nxt = 0
+    t0 = time.perf_counter()
+    steps = 0
+    cut = False
+    drained_hits = 0
+    while True:
+        now = time.perf_counter() - t0
+        if now > max_wall:
+            cut = True
+            break
+        while nxt < len(reqs) and reqs[nxt][0] <= now:
+            rid = P.ifa_serve_submit(h, reqs[nxt][1], reqs[nxt][2], P.IFA_MODE_AUTO)
+            ids.append(rid)
+            open_ids.append(rid)
+            nxt += 1
+        active, completed = P.ifa_serve_step(h)
+        steps += 1
+        if completed:
+            # the client collects finished requests' hits (frees their rings)
+            still = []
+            for rid in open_ids:
+                info = P.ifa_serve_poll(h, rid)
+                if info["state"] == 2:
+                    got, _ = P.ifa_serve_drain(h, rid, min(int(info["hits"]), 1 << 20))
+                    drained_hits += got.size
+                else:
+                    still.append(rid)
+            open_ids = still
+        if nxt == len(reqs) and active == 0 and not open_ids:
+            break
+        if nxt < len(reqs) and active == 0:
+            time.sleep(max(0.0, min(0.01, reqs[nxt][0] - now)))
+    wall = time.perf_counter() - t0
+    infos = [P.ifa_serve_poll(h, r) for r in ids]
+    sst = P.ifa_serve_stats(h)
+    P.ifa_serve_stop(h)
+    done = [i for i in infos if i["state"] >= 2]
+    # unfinished requests count with their latency so far (a lower bound)
+    lat = np.array([i["done_s"] - i["submit_s"] for i in done] +
+                   [wall - i["submit_s"] for i in infos if i["state"] < 2] +
+                   [wall - r[0] for r in reqs[nxt:]])
+    queue = np.array([i["admit_s"] - i["submit_s"] for i in done]) if done else np.zeros(1)
+    return {"value": sst["query_bases"] / wall, "hits_drained": drained_hits,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "p999": float(np.percentile(lat, 99.9))},
+            "queue_s": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
+            "completed": len(done), "requests": len(reqs), "wall_s": wall, "steps": steps,
+            "stopped_at_wall_limit": cut, "host_plan_s": sst["plan_s"], "device_scan_s": sst["scan_s"]}
+
+
 def run_serving(args):
     """Poisson arrivals of query sets served by continuous batching over a
-    device-resident reference."""
+    device-resident reference, and the same trace served one request at a
+    time (admission limited to one active request) as the baseline."""
     import torch
     import paper_2607_27291_b300 as P
     import synth
@@ -473,43 +534,23 @@ def run_serving(args):
     P.ifa_serve_submit(h, reqs[0][1], reqs[0][2], P.IFA_MODE_AUTO)
     while P.ifa_serve_step(h)[0]:
         pass
-    P.ifa_serve_start(h, args.slices, 64 << 30, 1 << 20)
-    ids = []
-    nxt = 0
-    t0 = time.perf_counter()
-    steps = 0
-    while True:
-        now = time.perf_counter() - t0
-        while nxt < len(reqs) and reqs[nxt][0] <= now:
-            ids.append(P.ifa_serve_submit(h, reqs[nxt][1], reqs[nxt][2], P.IFA_MODE_AUTO))
-            nxt += 1
-        active, _ = P.ifa_serve_step(h)
-        steps += 1
-        if nxt == len(reqs) and active == 0:
-            infos = [P.ifa_serve_poll(h, r) for r in ids]
-            if all(i["state"] >= 2 for i in infos):
-                break
-        if nxt < len(reqs) and active == 0:
-            time.sleep(max(0.0, min(0.01, reqs[nxt][0] - now)))
-    wall = time.perf_counter() - t0
-    sst = P.ifa_serve_stats(h)
-    qbases = sst["query_bases"]
-    lat = np.array([i["done_s"] - i["submit_s"] for i in infos])
-    queue = np.array([i["admit_s"] - i["submit_s"] for i in infos])
-    P.ifa_serve_stop(h)
+    cb = serve_trace(P, h, reqs, args.slices, 64 << 30, float("inf"))
+    solo = None
+    if not args.no_solo:
+        solo = serve_trace(P, h, reqs, args.slices, 1, args.solo_max_s)
     P.ifa_destroy(h)
     line = {
         "workload": "serving", "metric": "query-base comparisons/s (nominal) and request latency",
-        "unit": "query-base comparisons/s", "value": qbases / wall,
-        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                      "p999": float(np.percentile(lat, 99.9))},
-        "queue_s": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
-        "requests": len(reqs), "wall_s": wall, "steps": steps,
-        "host_plan_s": sst["plan_s"], "device_scan_s": sst["scan_s"],
+        "unit": "query-base comparisons/s", "value": cb["value"],
+        "latency_s": cb["latency_s"], "queue_s": cb["queue_s"], "requests": len(reqs),
+        "wall_s": cb["wall_s"], "steps": cb["steps"],
+        "host_plan_s": cb["host_plan_s"], "device_scan_s": cb["device_scan_s"],
+        "one_request_at_a_time": solo,
         "config": {"reference_bases": int(ref.size), "rate_per_s": args.rate,
                    "duration_s": args.duration, "slices": args.slices,
                    "set_sizes": "log-uniform 1-2000", "lengths": "18-50", "max_subs": "0-8",
-                   "gc": 0.45, "n_frac": 0.0005, "mode": "auto by query count"},
+                   "gc": 0.45, "n_frac": 0.0005, "mode": "auto by query count",
+                   "admission": "HBM budget 64 GiB (continuous batching); baseline: one active request"},
         "data": "synthetic",
     }
     print(json.dumps(line), flush=True)
