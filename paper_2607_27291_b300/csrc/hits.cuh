@@ -18,9 +18,21 @@
 
 namespace ifa {
 
+// Windows per brute-force block (32 lanes x 4 windows); an event's block
+// index times this is the block's first window.
+constexpr uint32_t kEventBlock = 128;
+
 // MULTI: hits go to per-request rings (serving); otherwise to the shared
 // hit buffer with warp staging.  A compile-time choice, so the streaming and
 // batch kernels carry no serving code.
+//
+// Two ways in, sharing the warp's 32-slot buffer (never mixed: a brute-force
+// block range starts by flushing hits and ends by flushing events):
+//  - emit(): one hit per lane (seed scan), staged as ifa_hit;
+//  - event(): the brute-force scan's (entry, lane, block) with a byte mask of
+//    its hitting windows and their mismatch counts, staged as 16 bytes.  The
+//    flush expands events into hits with the warp converged: piece lookup,
+//    query id, digest, one slot claim per flush.
 template <bool MULTI>
 struct WarpHitsT {
     ifa_hit *buf;          // this warp's 32 staged hits (shared memory)
@@ -76,25 +88,7 @@ struct WarpHitsT {
         if constexpr (MULTI) {
             // each hit goes straight to its request's own ring and digest
             if (hit) {
-                const RingDesc R = s.rings[s.q2r[q]];
-                const uint32_t rq = q - R.qfirst;
-                const uint64_t v = hit_digest_item(rq, contig, pos, strand, mm);
-                atomicAdd(&R.counters[2], 1ull);
-                atomicAdd(&R.counters[3], static_cast<unsigned long long>(v));
-                atomicXor(&R.counters[4], static_cast<unsigned long long>(v));
-                const unsigned long long idx = atomicAdd(&R.counters[0], 1ull);
-                if (idx < R.cap) {
-                    ifa_hit h;
-                    h.query = rq;
-                    h.contig = contig;
-                    h.pos = pos;
-                    h.strand = static_cast<uint8_t>(strand);
-                    h.mismatches = static_cast<uint8_t>(mm > 255 ? 255 : mm);
-                    h.reserved = 0;
-                    R.ring[idx] = h;
-                } else {
-                    R.counters[1] = 1ull;
-                }
+                ring_put(s, q, contig, pos, strand, mm);
                 if (!entry_count) atomicAdd(&s.qcount[q], 1ull);
             }
             if (entry_count && lane == static_cast<uint32_t>(__ffs(ballot) - 1)) atomicAdd(entry_count, cnt);
@@ -116,6 +110,119 @@ struct WarpHitsT {
             buf[n + r] = h;
         }
         n += cnt;
+        __syncwarp();
+    }
+
+    // One hit to a request's own ring and digest (serving).
+    __device__ static void ring_put(const HitSink &s, uint32_t q, uint32_t contig, uint32_t pos, uint32_t strand,
+                                    uint32_t mm) {
+        const RingDesc R = s.rings[s.q2r[q]];
+        const uint32_t rq = q - R.qfirst;
+        const uint64_t v = hit_digest_item(rq, contig, pos, strand, mm);
+        atomicAdd(&R.counters[2], 1ull);
+        atomicAdd(&R.counters[3], static_cast<unsigned long long>(v));
+        atomicXor(&R.counters[4], static_cast<unsigned long long>(v));
+        const unsigned long long idx = atomicAdd(&R.counters[0], 1ull);
+        if (idx < R.cap) {
+            ifa_hit h;
+            h.query = rq;
+            h.contig = contig;
+            h.pos = pos;
+            h.strand = static_cast<uint8_t>(strand);
+            h.mismatches = static_cast<uint8_t>(mm > 255 ? 255 : mm);
+            h.reserved = 0;
+            R.ring[idx] = h;
+        } else {
+            R.counters[1] = 1ull;
+        }
+    }
+
+    // Stage one event per lane with has != 0: chunk-local entry e (< 2^16),
+    // block index blk, hm = high bit of byte k set when window k of the lane
+    // hits, d = byte k the window's mismatch count.
+    __device__ void event(const Batch &b, const uint32_t *ids, uint32_t e0, uint32_t *cnt, const HitSink &s,
+                          uint32_t lane, bool has, uint32_t e, uint32_t d, uint32_t blk, uint32_t hm) {
+        const uint32_t ballot = __ballot_sync(0xffffffffu, has);
+        if (ballot == 0) return;
+        const uint32_t c = __popc(ballot);
+        if (n + c > 32) flush_events(b, ids, e0, cnt, s, lane);
+        if (has) {
+            const uint32_t r = __popc(ballot & ((1u << lane) - 1u));
+            reinterpret_cast<uint4 *>(buf)[n + r] = make_uint4(e | (lane << 16), d, blk, hm);
+        }
+        n += c;
+        __syncwarp();
+    }
+
+    // Expand the staged events into hits (all lanes; lane i takes event i).
+    __device__ void flush_events(const Batch &b, const uint32_t *ids, uint32_t e0, uint32_t *cnt,
+                                 const HitSink &s, uint32_t lane) {
+        __syncwarp();
+        if (n == 0) return;
+        uint4 ev = make_uint4(0u, 0u, 0u, 0u);
+        if (lane < n) ev = reinterpret_cast<const uint4 *>(buf)[lane];
+        n = 0;
+        __syncwarp();
+        uint32_t hm = ev.w & 0x80808080u;
+        const uint32_t nh = __popc(hm);
+        unsigned long long slot = 0;
+        if (!MULTI && !s.count_only) {
+            // one claim of global slots for the warp's hits
+            uint32_t inc = nh;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= static_cast<uint32_t>(o)) inc += y;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+            unsigned long long base = 0;
+            if (lane == 31 && total) base = atomicAdd(s.head, static_cast<unsigned long long>(total));
+            slot = __shfl_sync(0xffffffffu, base, 31) + (inc - nh);
+        }
+        if (nh) {
+            const uint32_t e = ev.x & 0xffffu, el = ev.x >> 16;
+            const uint32_t id = ids ? ids[e0 + e] : e0 + e;
+            const uint32_t q = id >> 1, strand = id & 1u;
+            atomicAdd(cnt + e, nh);
+            const uint64_t p0 = static_cast<uint64_t>(ev.z) * kEventBlock + el;
+            uint32_t pidx = 0xffffffffu;
+            while (hm) {
+                const uint32_t bit = static_cast<uint32_t>(__ffs(hm) - 1);  // 8 k + 7 for window k
+                hm &= hm - 1u;
+                const uint64_t p = p0 + 4u * (bit - 7u);                     // = p0 + 32 k
+                if (pidx == 0xffffffffu) {
+                    pidx = find_piece(b.pieces, b.npieces, p);
+                } else {
+                    while (pidx + 1 < b.npieces && b.pieces[pidx + 1].start <= p) pidx++;
+                }
+                const DevPiece pc = b.pieces[pidx];
+                const uint32_t pos = static_cast<uint32_t>(pc.contig_off + (p - pc.start));
+                const uint32_t mm = (ev.y >> (bit - 7u)) & 0xffu;
+                if constexpr (MULTI) {
+                    ring_put(s, q, pc.contig, pos, strand, mm);
+                } else {
+                    const uint64_t v = hit_digest_item(q, pc.contig, pos, strand, mm);
+                    dcount += 1;
+                    dsum += v;
+                    dxor ^= v;
+                    if (!s.count_only) {
+                        if (slot < s.capacity) {
+                            ifa_hit h;
+                            h.query = q;
+                            h.contig = pc.contig;
+                            h.pos = pos;
+                            h.strand = static_cast<uint8_t>(strand);
+                            h.mismatches = static_cast<uint8_t>(mm);
+                            h.reserved = 0;
+                            s.ring[slot] = h;
+                        } else {
+                            *s.overflow = 1u;
+                        }
+                        slot++;
+                    }
+                }
+            }
+        }
         __syncwarp();
     }
 

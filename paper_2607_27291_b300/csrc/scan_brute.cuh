@@ -80,27 +80,6 @@ struct Stage {
     static constexpr int kWords = kWin + WMAX;  // staged words per block
 };
 
-// Piece lookup for the blocks a warp visits, in increasing position: the
-// piece found last stays valid until the next piece's start, and a later
-// lookup searches only the pieces from it on.
-struct PieceCursor {
-    uint32_t idx = 0;   // piece of the last lookup
-    uint64_t next = 0;  // start of piece idx + 1 (~0 past the last); 0 before any lookup
-
-    __device__ __forceinline__ uint32_t find(const Batch &b, uint64_t p) {
-        if (p < next) return idx;
-        // the answer is in [idx, npieces) once a lookup was made (p only grows)
-        uint32_t lo = next == 0 ? 0u : idx, hi = b.npieces;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (b.pieces[mid].start <= p) lo = mid; else hi = mid;
-        }
-        idx = lo;
-        next = idx + 1 < b.npieces ? b.pieces[idx + 1].start : ~0ull;
-        return idx;
-    }
-};
-
 // Generic evaluation of every entry for one window per lane (p = p0 + lane)
 // whose block may hold N, piece boundaries, the batch end or the halo.
 template <int WMAX, class WH>
@@ -138,16 +117,10 @@ __device__ void generic_window(const Batch &b, const QueryTable &qt, const Smem 
         }
         const bool valid = (p + L <= b.nbases) && (p + L >= static_cast<uint64_t>(b.halo) + 1) && bnd == 0u;
         const bool hit = valid && mm <= entry_s(meta, s);
-        if (__any_sync(0xffffffffu, hit)) {
-            uint32_t contig = 0, pos = 0;
-            if (hit) {
-                const DevPiece pc = b.pieces[find_piece(b.pieces, b.npieces, p)];
-                contig = pc.contig;
-                pos = static_cast<uint32_t>(pc.contig_off + (p - pc.start));
-            }
-            const uint32_t id = qt.ids ? qt.ids[e0 + e] : e0 + e;
-            wh.emit(sink, lane, hit, id >> 1, contig, pos, id & 1u, mm, m.cnt + e);
-        }
+        // this call's window is window k of block p0 / 128 (mm <= 255 fits a byte)
+        const uint32_t k = static_cast<uint32_t>(p0 >> 5) & (kWin - 1);
+        wh.event(b, qt.ids, e0, m.cnt, sink, lane, hit, e, mm << (8 * k), static_cast<uint32_t>(p0 / (32 * kWin)),
+                 hit ? 0x80u << (8 * k) : 0u);
     }
 }
 
@@ -171,63 +144,82 @@ __device__ __forceinline__ uint32_t mad(uint32_t a, uint32_t b, uint32_t c) {
 }
 
 // Exact evaluation of one entry for the lane's kWin windows of a block
-// without N, piece boundary or ownership limits, then hit emission.  Counts
-// stay packed one byte per window: d = v - bias holds the word-0 counts
-// (see packed_counts), the entry's Ns are added to every byte, and words
-// 1.. are added by IMAD.  Word j of window k is word 0 of window k + j, so
-// it is taken from the hot loop's registers where k + j < kWin and cut from
-// the staged words otherwise.  No byte can carry: a window's count is at
-// most its query length (<= 255).
+// without N, piece boundary or ownership limits, then one hit event per
+// lane.  Counts stay packed one byte per window.  Word j of window k is word
+// 0 of window k + j, so it is taken from the hot loop's registers where
+// k + j < kWin and cut from the staged words otherwise.
+//  - Queries of up to 64 bases (WMAX <= 2): word-1 counts are added straight
+//    onto v, whose bytes are 128 - (T + 1) + count for the word-0 threshold
+//    T (see packed_counts).  T already is the whole window's threshold
+//    (maxSubs less the query's Ns), and a byte stays below 256 (count <= 64),
+//    so a byte's high bit is clear exactly when its window hits.
+//  - Longer queries: d = v - bias holds the counts themselves, the Ns are
+//    added to every byte, then words 1.. by IMAD, and d is tested against
+//    maxSubs.  No byte can carry: a count is at most the query length.
 template <int WMAX, class WH>
 __device__ __forceinline__ void exact_fast(const Batch &b, const QueryTable &qt, const Smem &m,
                                            const uint4 *R, const uint32_t *hw, const uint32_t *lw,
-                                           const uint32_t *mul, uint32_t e, uint32_t e0, uint64_t p0,
-                                           uint32_t lane, uint32_t s, const HitSink &sink,
-                                           WH &wh, PieceCursor &pcur, uint32_t v, uint32_t bias) {
+                                           const uint32_t *mul, uint32_t e, uint32_t e0, uint32_t blk,
+                                           uint32_t lane, uint32_t s, const HitSink &sink, WH &wh, uint32_t v,
+                                           uint32_t bias) {
     const uint32_t meta = m.meta[e];
-    const uint32_t W = meta_W(meta);
-    const uint32_t se = entry_s(meta, s);
     const uint4 *qw = m.sq + static_cast<size_t>(e) * WMAX;
-    uint32_t d = v - bias + meta_nN(meta) * 0x01010101u;
-#pragma unroll
-    for (int j = 1; j < WMAX; j++) {
-        if (j < static_cast<int>(W)) {
-            const uint4 q = qw[j];
+    uint32_t hm, d;
+    if constexpr (WMAX <= 2) {
+        uint32_t vf = v;
+        if (WMAX == 2 && meta_W(meta) > 1u) {
+            const uint4 q = qw[WMAX - 1];
 #pragma unroll
             for (int k = 0; k < kWin; k++) {
                 uint32_t h, l;
-                if (k + j < kWin) {
-                    h = hw[k + j];
-                    l = lw[k + j];
+                if (k + 1 < kWin) {
+                    h = hw[k + 1];
+                    l = lw[k + 1];
                 } else {
-                    const uint4 a = R[k + j], c = R[k + j + 1];
+                    const uint4 a = R[k + 1], c = R[k + 2];
                     h = __funnelshift_r(a.x, c.x, lane);
                     l = __funnelshift_r(a.y, c.y, lane);
                 }
-                d = mad(__popc(((h ^ q.x) | (l ^ q.y)) & q.z), mul[k], d);
+                vf = mad(__popc(((h ^ q.x) | (l ^ q.y)) & q.z), mul[k], vf);
             }
         }
-    }
-    // byte k of hm has its high bit set when window k hits (count <= se)
-    uint32_t hm;
-    if constexpr (WMAX <= 4) {
-        // counts <= 128 (queries up to 128 bases), so for se <= 127 the
-        // byte-lane test of packed_counts applies (128 - (se + 1) + count
-        // stays below 256); se >= 128 passes every window
-        hm = se >= 128u ? 0x80808080u : ~(d + byte_bias(static_cast<int>(se))) & 0x80808080u;
+        hm = ~vf & 0x80808080u;
+        d = vf - bias + meta_nN(meta) * 0x01010101u;
     } else {
-        hm = 0;
+        const uint32_t W = meta_W(meta);
+        const uint32_t se = entry_s(meta, s);
+        d = v - bias + meta_nN(meta) * 0x01010101u;
 #pragma unroll
-        for (int k = 0; k < kWin; k++) hm |= (((d >> (8 * k)) & 0xffu) <= se ? 0x80u : 0u) << (8 * k);
+        for (int j = 1; j < WMAX; j++) {
+            if (j < static_cast<int>(W)) {
+                const uint4 q = qw[j];
+#pragma unroll
+                for (int k = 0; k < kWin; k++) {
+                    uint32_t h, l;
+                    if (k + j < kWin) {
+                        h = hw[k + j];
+                        l = lw[k + j];
+                    } else {
+                        const uint4 a = R[k + j], c = R[k + j + 1];
+                        h = __funnelshift_r(a.x, c.x, lane);
+                        l = __funnelshift_r(a.y, c.y, lane);
+                    }
+                    d = mad(__popc(((h ^ q.x) | (l ^ q.y)) & q.z), mul[k], d);
+                }
+            }
+        }
+        if constexpr (WMAX <= 4) {
+            // counts <= 128 (queries up to 128 bases), so for se <= 127 the
+            // byte-lane test applies (128 - (se + 1) + count stays below 256);
+            // se >= 128 passes every window
+            hm = se >= 128u ? 0x80808080u : ~(d + byte_bias(static_cast<int>(se))) & 0x80808080u;
+        } else {
+            hm = 0;
+#pragma unroll
+            for (int k = 0; k < kWin; k++) hm |= (((d >> (8 * k)) & 0xffu) <= se ? 0x80u : 0u) << (8 * k);
+        }
     }
-    if (!__any_sync(0xffffffffu, hm != 0u)) return;
-    const DevPiece pc = b.pieces[pcur.find(b, p0)];
-    const uint32_t id = qt.ids ? qt.ids[e0 + e] : e0 + e;
-    const uint32_t pos0 = static_cast<uint32_t>(pc.contig_off + (p0 + lane - pc.start));
-#pragma unroll
-    for (int k = 0; k < kWin; k++)
-        wh.emit(sink, lane, (hm >> (8 * k + 7)) & 1u, id >> 1, pc.contig, pos0 + 32 * k, id & 1u,
-                (d >> (8 * k)) & 0xffu, m.cnt + e);
+    wh.event(b, qt.ids, e0, m.cnt, sink, lane, hm != 0u, e, d, blk, hm);
 }
 
 // Entry word-0 records: {hi0, lo0, bias, -} (class F) or
@@ -252,8 +244,8 @@ template <int WMAX, bool MASKED, class WH>
 __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt, const Smem &m,
                                            const uint4 *rec, const uint16_t *idx, uint32_t n,
                                            const uint32_t *hw, const uint32_t *lw, const uint32_t *mul,
-                                           const uint4 *R, uint32_t e0, uint64_t p0, uint32_t lane,
-                                           uint32_t s, const HitSink &sink, WH &wh, PieceCursor &pcur) {
+                                           const uint4 *R, uint32_t e0, uint32_t blk, uint32_t lane,
+                                           uint32_t s, const HitSink &sink, WH &wh) {
     constexpr uint32_t kHigh = 0x80808080u;
     uint32_t k = 0;
     for (; k + kGroup <= n; k += kGroup) {
@@ -275,7 +267,7 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
                 // v[i] by a select chain (no local array); the bias from the record
                 const uint32_t vi = i == 0 ? v[0] : i == 1 ? v[1] : i == 2 ? v[2] : v[3];
                 const uint4 q = rec[k + i];
-                exact_fast<WMAX>(b, qt, m, R, hw, lw, mul, idx[k + i], e0, p0, lane, s, sink, wh, pcur, vi,
+                exact_fast<WMAX>(b, qt, m, R, hw, lw, mul, idx[k + i], e0, blk, lane, s, sink, wh, vi,
                                  MASKED ? q.w : q.z);
             }
         }
@@ -284,7 +276,7 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
         const uint4 q = rec[k];
         const uint32_t v = packed_counts<MASKED>(q, hw, lw, mul);
         if (__any_sync(0xffffffffu, (v & kHigh) != kHigh))
-            exact_fast<WMAX>(b, qt, m, R, hw, lw, mul, idx[k], e0, p0, lane, s, sink, wh, pcur, v,
+            exact_fast<WMAX>(b, qt, m, R, hw, lw, mul, idx[k], e0, blk, lane, s, sink, wh, v,
                              MASKED ? q.w : q.z);
     }
 }
@@ -398,7 +390,8 @@ __device__ __forceinline__ void scan_blocks(const Batch &b, const QueryTable &qt
                                             uint64_t base, uint64_t blk_end, uint32_t w, uint32_t nw,
                                             uint32_t lane) {
     constexpr int NW = Stage<WMAX>::kWords;
-    PieceCursor pcur;
+    static_assert(32 * kWin == kEventBlock, "events address blocks of 32 x kWin windows");
+    wh.flush(sink, lane);  // the staging buffer now takes events
     const uint64_t jump = static_cast<uint64_t>(nw - 1) * kChunk;
     uint64_t blk = base + static_cast<uint64_t>(w) * kChunk;
     uint32_t in_chunk = 0;
@@ -435,11 +428,13 @@ __device__ __forceinline__ void scan_blocks(const Batch &b, const QueryTable &qt
             hw[k] = __funnelshift_r(R[k].x, R[k + 1].x, lane);
             lw[k] = __funnelshift_r(R[k].y, R[k + 1].y, lane);
         }
-        scan_class<WMAX, false>(b, qt, m, m.sF, m.fidx, nF, hw, lw, mul, R, e0, p0, lane, s, sink, wh, pcur);
-        scan_class<WMAX, true>(b, qt, m, m.sM, m.midx, nM, hw, lw, mul, R, e0, p0, lane, s, sink, wh, pcur);
+        const uint32_t bi = static_cast<uint32_t>(blk);
+        scan_class<WMAX, false>(b, qt, m, m.sF, m.fidx, nF, hw, lw, mul, R, e0, bi, lane, s, sink, wh);
+        scan_class<WMAX, true>(b, qt, m, m.sM, m.midx, nM, hw, lw, mul, R, e0, bi, lane, s, sink, wh);
         __syncwarp();
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
+    wh.flush_events(b, qt.ids, e0, m.cnt, sink, lane);
 }
 
 }  // namespace brute
