@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--total", type=float, default=4e9, help="reference bases (default 4 Gbp)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "serving"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "serving", "indexed", "latency"],
                     help="sweep: the 4 Gbp maxSubs sweep (default); batched: many query sets "
                          "in one persistent launch vs one launch per set; serving: Poisson "
                          "arrivals with continuous batching")
@@ -556,12 +556,147 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_indexed(args):
+    """Indexed mode at scale: 10,000 queries of 20-40 bp against 1 Gbp
+    (GC 50 %), maxSubs 4 / 8 / 16, MinHits from a 10^5-trial Monte Carlo on
+    Philox seed 1; 5 % of the queries are planted once with exactly maxSubs
+    substitutions.  Per maxSubs: a device-resident count-only pass timed with
+    CUDA events, indexed and brute force on the same handle, and the planted
+    windows found (indexed mode's recall, the paper's false-negative rate)."""
+    import torch
+    import paper_2607_27291_b300 as P
+    import synth
+    total = int(args.total if args.total != 4e9 else 1e9)
+    out = {}
+    for s in (4, 8, 16):
+        wl = synth.workload_1gbp_indexed(total=total, plant_subs=s)
+        dev = torch.from_numpy(wl.ref).cuda()
+        stream = torch.cuda.Stream()
+        h = P.ifa_create(count_only=1, segment_bytes=SEG, minhits_trials=100_000, minhits_seed=1, profile=1)
+        P.ifa_set_stream(h, stream)
+        P.ifa_load_queries(h, wl.queries)
+        P.ifa_set_max_subs(h, s)
+        segs = list(P.segment_pieces(wl.contig_len, SEG))
+        _, qb = nominal_work(wl)
+        res = {}
+        for mode, name in ((P.IFA_MODE_INDEXED, "indexed"), (P.IFA_MODE_BRUTE, "brute")):
+            P.ifa_set_mode(h, mode)
+            times = []
+            reps = args.steps if name == "indexed" else 1   # brute force: ~6 s per pass
+            for rep in range(max(1, args.warmup) + reps):
+                P.ifa_reset_results(h)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for x, y, pc in segs:
+                    P.ifa_push_segment(h, dev[x:y], pc)
+                b.record(stream)
+                P.ifa_flush(h)
+                b.synchronize()
+                if rep >= max(1, args.warmup):
+                    times.append(a.elapsed_time(b))
+            st = P.ifa_get_stats(h)
+            dg, _ = P.ifa_get_digest(h)
+            ms = float(np.mean(times))
+            res[name] = {"ms": ms, "effective_qbase_per_s": qb / (ms * 1e-3), "hits": dg[0],
+                         "candidates": st["candidates"],
+                         "candidates_per_s": st["candidates"] / (ms * 1e-3)}
+        P.ifa_destroy(h)
+        del dev
+        torch.cuda.empty_cache()
+        # recall on the planted windows: whether a window is a candidate
+        # depends only on the window, so excerpts around the plants suffice
+        pq = sorted({pl.query for pl in wl.plants})
+        remap = {q: i for i, q in enumerate(pq)}
+        starts = np.concatenate([[0], np.cumsum(wl.contig_len)[:-1]])
+        parts, lens, where = [], [], []
+        for pl in wl.plants:
+            L = len(wl.queries[pl.query])
+            a, b = pl.pos, pl.pos + L   # the planted window alone
+            parts.append(wl.ref[starts[pl.contig] + a:starts[pl.contig] + b])
+            lens.append(b - a)
+            where.append((remap[pl.query], len(lens) - 1, pl.pos - a, pl.strand))
+        exc = np.concatenate(parts)
+        h = P.ifa_create(hit_capacity=1 << 25, segment_bytes=max(1 << 20, exc.size + 64),
+                         minhits_trials=100_000, minhits_seed=1)
+        P.ifa_load_queries(h, [wl.queries[q] for q in pq])
+        P.ifa_set_max_subs(h, s)
+        P.ifa_set_mode(h, P.IFA_MODE_INDEXED)
+        for x, y, pc in P.segment_pieces(np.array(lens, np.int64), exc.size + 64):
+            P.ifa_push_segment(h, exc[x:y], pc)
+        hits, over = P.ifa_drain_hits(h)
+        P.ifa_destroy(h)
+        assert not over
+        got = set(zip(hits["query"].tolist(), hits["contig"].tolist(), hits["pos"].tolist(),
+                      hits["strand"].tolist()))
+        found = sum(1 for w in where if w in got)
+        res["planted"] = len(where)
+        res["planted_found"] = found
+        res["false_negative_rate"] = 1.0 - found / max(1, len(where))
+        out[str(s)] = res
+    line = {"workload": "indexed", "metric": "query-base comparisons/s (effective) and candidates verified/s",
+            "unit": "query-base comparisons/s", "value": out["8"]["indexed"]["effective_qbase_per_s"],
+            "per_max_subs": out,
+            "config": {"reference_bases": total, "queries": 10000, "lengths": "20-40", "gc": 0.5,
+                       "contigs": "log-uniform 10 kbp - 2 Mbp", "minhits_trials": 100000, "philox_seed": 1,
+                       "planted": "5 % of queries, exactly maxSubs substitutions", "hits": "count only",
+                       "steps": args.steps, "warmup": max(1, args.warmup), "brute_steps": 1},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
+def run_latency(args):
+    """One 20 bp query against 10 contigs of 1 Mbp (uniform ACGT), maxSubs 2,
+    20 planted hits: latency of one whole call from pinned host ASCII (push,
+    scan, drain) and of the device-resident scan alone."""
+    import torch
+    import paper_2607_27291_b300 as P
+    import synth
+    wl = synth.workload_1mbp_x10()
+    pin = torch.from_numpy(wl.ref).pin_memory()
+    dev = torch.from_numpy(wl.ref).cuda()
+    h = P.ifa_create(hit_capacity=1 << 16, segment_bytes=16 << 20)
+    P.ifa_load_queries(h, wl.queries)
+    P.ifa_set_max_subs(h, 2)
+    P.ifa_set_mode(h, P.IFA_MODE_BRUTE)
+    segs = list(P.segment_pieces(wl.contig_len, 16 << 20))
+    e2e, devl, nh = [], [], 0
+    for rep in range(args.warmup + max(args.steps, 50)):
+        for src, acc in ((pin, e2e), (dev, devl)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P.ifa_reset_results(h)
+            for x, y, pc in segs:
+                P.ifa_push_segment(h, src[x:y], pc)
+            hits, _ = P.ifa_drain_hits(h)
+            dt = time.perf_counter() - t0
+            if rep >= args.warmup:
+                acc.append(dt * 1e3)
+            nh = hits.size
+    P.ifa_destroy(h)
+    q = lambda a, p: float(np.percentile(a, p))
+    line = {"workload": "latency", "metric": "latency of one call (ms) and ref Gbp/s",
+            "unit": "ms", "value": q(e2e, 50), "higher_is_better": False,
+            "e2e_ms": {"p50": q(e2e, 50), "p99": q(e2e, 99)},
+            "device_resident_ms": {"p50": q(devl, 50), "p99": q(devl, 99)},
+            "ref_gbps_e2e": wl.ref.size / (q(e2e, 50) * 1e-3) / 1e9, "hits": nh, "planted": len(wl.plants),
+            "config": {"queries": 1, "length": 20, "reference": "10 x 1 Mbp uniform ACGT", "max_subs": 2,
+                       "input": "ASCII from pinned host memory (e2e) or device memory",
+                       "reps": len(e2e)},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "indexed":
+        return run_indexed(args)
+    if args.workload == "latency":
+        return run_latency(args)
     rank, world = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
