@@ -62,6 +62,12 @@ typedef enum {
 } ifa_mode;
 
 typedef enum {
+    IFA_BRUTE_AUTO = 0,    /* tensor cores from 256 entries (128 queries) on, when eligible */
+    IFA_BRUTE_POPC = 1,    /* bit-plane XOR/OR/popcount kernel */
+    IFA_BRUTE_TENSOR = 2   /* one-hot GEMM on the tensor cores; queries of at most 64 bases */
+} ifa_brute_kernel;
+
+typedef enum {
     IFA_MEM_HOST = 0,         /* pageable host memory: copied through pinned staging */
     IFA_MEM_HOST_PINNED = 1,  /* page-locked host memory: DMA'd directly */
     IFA_MEM_DEVICE = 2        /* device memory on the handle's device */
@@ -121,7 +127,9 @@ typedef struct {
     uint32_t exhaustive_fallback;  /* 1: queries with no qualifying k are scanned exhaustively */
     uint32_t auto_crossover;       /* IFA_MODE_AUTO picks indexed from this many queries on */
     uint32_t profile;              /* 1: time every scan kernel with CUDA events (ifa_stats.scan_ns) */
-    uint32_t reserved[6];
+    uint32_t brute_kernel;         /* brute-force kernel: 0 automatic, 1 popcount, 2 tensor cores
+                                      (one-hot e4m3 GEMM; queries of at most 64 bases) */
+    uint32_t reserved[5];
 } ifa_config;
 
 typedef struct {

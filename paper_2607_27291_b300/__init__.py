@@ -28,6 +28,7 @@ IFA_ERR_TIMEOUT = 6
 
 IFA_MODE_AUTO, IFA_MODE_BRUTE, IFA_MODE_INDEXED = 0, 1, 2
 IFA_MEM_HOST, IFA_MEM_HOST_PINNED, IFA_MEM_DEVICE = 0, 1, 2
+IFA_BRUTE_AUTO, IFA_BRUTE_POPC, IFA_BRUTE_TENSOR = 0, 1, 2
 IFA_MAX_QUERY_LEN = 255
 
 HIT_DTYPE = np.dtype([("query", "<u4"), ("contig", "<u4"), ("pos", "<u4"),
@@ -43,7 +44,7 @@ class ifa_config(C.Structure):
                 ("minhits_den", C.c_uint32), ("minhits_trials", C.c_uint32),
                 ("minhits_seed", C.c_uint64), ("max_clips", C.c_uint32),
                 ("exhaustive_fallback", C.c_uint32), ("auto_crossover", C.c_uint32),
-                ("profile", C.c_uint32), ("reserved", C.c_uint32 * 6)]
+                ("profile", C.c_uint32), ("brute_kernel", C.c_uint32), ("reserved", C.c_uint32 * 5)]
 
 
 class ifa_digest(C.Structure):

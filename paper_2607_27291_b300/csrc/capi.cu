@@ -104,6 +104,17 @@ ifa_status upload_queries(ifa_handle *h) {
         }
         h->chunks.push_back(c);
     }
+    // tensor-core operand when the brute-force kernel may use it
+    cudaFree(h->d_tcA);
+    h->d_tcA = nullptr;
+    h->tc_lpad = 0;
+    if (h->cfg.brute_kernel != IFA_BRUTE_POPC && tc_eligible(h->lmax)) {
+        std::vector<uint8_t> op;
+        h->tc_lpad = tc_lpad(h->lmax);
+        tc_operand(h->qs, h->tc_lpad, op);
+        CK(h, cudaMalloc(&h->d_tcA, op.size()));
+        CK(h, cudaMemcpy(h->d_tcA, op.data(), op.size(), cudaMemcpyHostToDevice));
+    }
     h->qdirty = false;
     h->idx.invalidate();
     h->batch.plan_valid = false;
@@ -195,6 +206,20 @@ namespace ifa {
 void set_global_error(const std::string &msg) { g_err = msg; }
 }  // namespace ifa
 
+namespace {
+
+// The brute-force kernel of a pass: the tensor cores when forced, or (auto)
+// for query sets large enough to fill their 128-entry tiles.
+constexpr uint32_t kTcAutoEntries = 256;
+
+bool use_tensor_cores(const ifa_handle *h) {
+    if (!h->d_tcA) return false;
+    if (h->cfg.brute_kernel == IFA_BRUTE_TENSOR) return true;
+    return h->cfg.brute_kernel == IFA_BRUTE_AUTO && 2 * h->qs.size() >= kTcAutoEntries;
+}
+
+}  // namespace
+
 // ------------------------------------------------------------------------ API
 
 extern "C" {
@@ -227,6 +252,8 @@ ifa_status ifa_create(const ifa_config *cfg, ifa_handle **out) {
     if (!cfg) return fail(nullptr, IFA_ERR_INVALID_ARG, "cfg is NULL");
     if (cfg->max_clips != 0)
         return fail(nullptr, IFA_ERR_INVALID_ARG, "max_clips must be 0 (soft clipping not implemented)");
+    if (cfg->brute_kernel > IFA_BRUTE_TENSOR)
+        return fail(nullptr, IFA_ERR_INVALID_ARG, "brute_kernel must be 0 (auto), 1 (popcount) or 2 (tensor cores)");
     if (cfg->n_k == 0 || cfg->n_k > IFA_MAX_KLIST)
         return fail(nullptr, IFA_ERR_INVALID_ARG, "n_k must be in 1..8");
     for (uint32_t i = 0; i < cfg->n_k; i++)
@@ -309,6 +336,8 @@ void ifa_destroy(ifa_handle *h) {
     cudaFree(h->d_words);
     cudaFree(h->d_qwords);
     cudaFree(h->d_qmeta);
+    cudaFree(h->d_tcA);
+    cudaFree(h->d_tc_status);
     cudaFree(h->d_ring);
     cudaFree(h->d_head);
     cudaFree(h->d_overflow);
@@ -473,9 +502,23 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
         st = indexed_scan(h->idx, b, qt, h->max_subs, sink, h->stream, &launches, h->err);
         if (st != IFA_OK) return st;
     }
-    if (mode == IFA_MODE_BRUTE)
-        for (const Chunk &c : h->chunks)
-            CK(h, launch_scan_brute(b, qt, c.e0, c.e1, h->max_subs, c.lmin, c.lmax, sink, h->stream, &launches));
+    if (mode == IFA_MODE_BRUTE) {
+        if (h->cfg.brute_kernel == IFA_BRUTE_TENSOR && !h->d_tcA)
+            return fail(h, IFA_ERR_INVALID_ARG, "brute_kernel 2 (tensor cores) takes queries of at most 64 bases");
+        if (use_tensor_cores(h)) {
+            if (!h->d_tc_status) {
+                CK(h, cudaMalloc(&h->d_tc_status, 2 * sizeof(unsigned int)));
+                CK(h, cudaMemsetAsync(h->d_tc_status, 0, 2 * sizeof(unsigned int), h->stream));
+            }
+            CK(h, launch_scan_tc(b, h->d_tcA, h->d_qmeta, qt.n_entries, h->tc_lpad, h->max_subs, sink,
+                                 h->d_tc_status, h->stream));
+            h->tc_used = true;
+            launches++;
+        } else {
+            for (const Chunk &c : h->chunks)
+                CK(h, launch_scan_brute(b, qt, c.e0, c.e1, h->max_subs, c.lmin, c.lmax, sink, h->stream, &launches));
+        }
+    }
     st = prof_end(h, prof_stop, launches - before_scan);
     if (st != IFA_OK) return st;
     // halo for the next segment when the last piece continues
@@ -529,6 +572,11 @@ ifa_status ifa_flush(ifa_handle *h) {
     if (st != IFA_OK) return st;
     st = prof_collect(h);
     if (st != IFA_OK) return st;
+    if (h->tc_used) {
+        unsigned int tcs = 0;
+        CK(h, cudaMemcpy(&tcs, h->d_tc_status, sizeof(tcs), cudaMemcpyDeviceToHost));
+        if (tcs) return fail(h, IFA_ERR_TIMEOUT, "tensor-core scan: a pipeline wait gave up; results incomplete");
+    }
     uint32_t ov = 0;
     CK(h, cudaMemcpy(&ov, h->d_overflow, sizeof(ov), cudaMemcpyDeviceToHost));
     if (ov) return fail(h, IFA_ERR_HIT_OVERFLOW, "hit buffer overflowed; some hit tuples were dropped");

@@ -34,6 +34,13 @@ struct ifa_handle {
     bool qdirty = true;
     uint4 *d_qwords = nullptr;
     uint32_t *d_qmeta = nullptr;
+    // tensor-core operand of the entries (queries up to 64 bases), its row
+    // width in bases, and the kernel's status words (bit 0 of the first: a
+    // wait gave up; the second: the launch's work counter)
+    uint8_t *d_tcA = nullptr;
+    uint32_t tc_lpad = 0;
+    unsigned int *d_tc_status = nullptr;
+    bool tc_used = false;
     std::vector<Chunk> chunks;
     std::vector<uint32_t> qmeta_host;
     std::vector<uint4> qwords_host;
@@ -99,6 +106,7 @@ cudaError_t launch_batch_kernel(uint32_t wmax, const Batch &b, const BatchWork &
                                 cudaStream_t st);
 int batch_kernel_grid(uint32_t wmax);
 void encode_entry(const std::string &q, bool rc, uint32_t wmax, uint32_t s_e, uint4 *out, uint32_t *meta);
+void tc_operand(const std::vector<std::string> &qs, uint32_t lpad, std::vector<uint8_t> &out);
 // Free the serving state.
 void serve_release(ifa_handle *h);
 }  // namespace ifa

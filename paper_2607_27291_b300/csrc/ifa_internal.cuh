@@ -148,6 +148,12 @@ __device__ inline uint32_t find_piece(const DevPiece *pc, uint32_t n, uint64_t p
 // ---------------------------------------------------------------- launchers
 // (defined in the .cu files; all enqueue on `st`)
 
+// Tensor-core brute-force scan (scan_tc.cu): queries up to 64 bases.
+uint32_t tc_lpad(uint32_t lmax);
+bool tc_eligible(uint32_t lmax);
+cudaError_t launch_scan_tc(const Batch &b, const uint8_t *tcA, const uint32_t *meta, uint32_t nent, uint32_t lpad,
+                           uint32_t s, const HitSink &sink, unsigned int *status, cudaStream_t st);
+
 cudaError_t launch_pack(const uint8_t *halo, uint32_t hlen, uint32_t H, const uint8_t *seg,
                         uint64_t slen, uint4 *words, uint64_t nwords_padded, cudaStream_t st);
 cudaError_t launch_mark_pieces(const DevPiece *pieces, uint32_t n, uint4 *words, cudaStream_t st);

@@ -41,7 +41,10 @@ namespace brute {
 constexpr int kScanThreads = 256;
 constexpr int kScanWarps = kScanThreads / kWarp;
 constexpr size_t kScanSmemBudget = 40 * 1024;  // dynamic; + static (hit staging, word staging) < 48 KB
-constexpr int kGroup = 4;                       // entries per warp vote in the hot loop
+#ifndef IFA_SCAN_GROUP
+#define IFA_SCAN_GROUP 4
+#endif
+constexpr int kGroup = IFA_SCAN_GROUP;          // entries per warp vote in the hot loop
 constexpr int kWin = 4;                         // windows per lane (32 * kWin per warp step)
 
 // Per-entry shared memory: WMAX uint4 words, a class-M word-0 record, a
@@ -252,10 +255,12 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
         uint32_t v[kGroup];
 #pragma unroll
         for (int i = 0; i < kGroup; i++) v[i] = packed_counts<MASKED>(rec[k + i], hw, lw, mul);
-        const uint32_t acc = v[0] & v[1] & v[2] & v[3];
+        uint32_t acc = v[0];
+#pragma unroll
+        for (int i = 1; i < kGroup; i++) acc &= v[i];
         if (__any_sync(0xffffffffu, (acc & kHigh) != kHigh)) {
-            // which of the 4 entries fired in any lane; one (not unrolled) copy
-            // of the exact path walks them
+            // which of the group's entries fired in any lane; one (not
+            // unrolled) copy of the exact path walks them
             uint32_t fired = 0;
 #pragma unroll
             for (int i = 0; i < kGroup; i++) fired |= ((v[i] & kHigh) != kHigh ? 1u : 0u) << i;
@@ -265,7 +270,9 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
                 const int i = __ffs(fired) - 1;
                 fired &= fired - 1;
                 // v[i] by a select chain (no local array); the bias from the record
-                const uint32_t vi = i == 0 ? v[0] : i == 1 ? v[1] : i == 2 ? v[2] : v[3];
+                uint32_t vi = v[0];
+#pragma unroll
+                for (int t = 1; t < kGroup; t++) vi = i == t ? v[t] : vi;
                 const uint4 q = rec[k + i];
                 exact_fast<WMAX>(b, qt, m, R, hw, lw, mul, idx[k + i], e0, blk, lane, s, sink, wh, vi,
                                  MASKED ? q.w : q.z);
