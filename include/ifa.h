@@ -62,7 +62,7 @@ typedef enum {
 } ifa_mode;
 
 typedef enum {
-    IFA_BRUTE_AUTO = 0,    /* tensor cores from 256 entries (128 queries) on, when eligible */
+    IFA_BRUTE_AUTO = 0,    /* tensor cores from 32 queries on, when eligible */
     IFA_BRUTE_POPC = 1,    /* bit-plane XOR/OR/popcount kernel */
     IFA_BRUTE_TENSOR = 2   /* one-hot GEMM on the tensor cores; queries of at most 64 bases */
 } ifa_brute_kernel;

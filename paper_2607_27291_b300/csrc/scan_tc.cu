@@ -8,7 +8,7 @@
 //     matches(e, p) = sum_i sum_c Q[e][4 i + c] * R[p + i][c].
 // Q is an M x K operand (entries x 4 L), R a K x N operand whose column for
 // window p is the one-hot reference from p on.  The values are 0/1, exact in
-// e4m3, and the sums (<= 64) exact in the f32 accumulator.
+// e4m3, and the sums (<= 64) exact in the f16 accumulator.
 //
 // The reference operand needs no Toeplitz matrix: in the K-major layout
 // without swizzle, the 8 rows of a core matrix lie 16 bytes apart, and the
@@ -36,6 +36,8 @@
 #include <cstring>
 #include <string>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "hits.cuh"
 
@@ -85,8 +87,10 @@ __device__ __forceinline__ uint64_t mdesc(uint32_t addr, uint32_t lbo, uint32_t 
            (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor: f32 accumulator, e4m3 x e4m3, both K-major, N, M.
-constexpr uint32_t kIdesc = (1u << 4) | (static_cast<uint32_t>(kTcN >> 3) << 17) |
+// Instruction descriptor: f16 accumulator (counts <= 64 are exact; each
+// value still takes one 32-bit TMEM column, in its low half), e4m3 x e4m3,
+// both K-major, N, M.
+constexpr uint32_t kIdesc = (0u << 4) | (static_cast<uint32_t>(kTcN >> 3) << 17) |
                             (static_cast<uint32_t>(kTcM >> 4) << 24);
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abort) {
@@ -121,10 +125,12 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
         : "memory");
 }
 
-// Issue a 32-column TMEM load; the registers are valid after tc_wait_ld_regs().
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t *r) {
+// Issue a 64-column TMEM load of f16 values, two columns per register (the
+// even column in the low half); the registers are valid after
+// tc_wait_ld_regs().
+__device__ __forceinline__ void tc_ld64h(uint32_t taddr, uint32_t *r) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "tcgen05.ld.sync.aligned.32x32b.x32.pack::16b.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
@@ -146,15 +152,17 @@ __device__ __forceinline__ void tc_wait_ld_regs(uint32_t *r) {
                  : "memory");
 }
 
-__device__ __forceinline__ float max32(const uint32_t *r) {
-    float m[16];
+// Largest of the 64 f16 counts held two per register.
+__device__ __forceinline__ float max64h(const uint32_t *r) {
+    __half2 m[16];
 #pragma unroll
-    for (int j = 0; j < 16; j++) m[j] = fmaxf(__uint_as_float(r[j]), __uint_as_float(r[j + 16]));
+    for (int j = 0; j < 16; j++)
+        m[j] = __hmax2(*reinterpret_cast<const __half2 *>(&r[j]), *reinterpret_cast<const __half2 *>(&r[j + 16]));
 #pragma unroll
     for (int w = 8; w > 0; w >>= 1)
 #pragma unroll
-        for (int j = 0; j < w; j++) m[j] = fmaxf(m[j], m[j + w]);
-    return m[0];
+        for (int j = 0; j < w; j++) m[j] = __hmax2(m[j], m[j + w]);
+    return fmaxf(__low2float(m[0]), __high2float(m[0]));
 }
 
 // Whether a piece other than the window's own starts inside [p + 1, p + L).
@@ -355,24 +363,32 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     // 8 chunks of 32 columns, the next chunk's load in flight
                     // while the current one is tested
-                    constexpr uint32_t kChunks = kTcN / 32 / 2;
+                    // two packed loads of 64 columns, the second in flight while
+                    // the first is tested
                     const uint32_t tbase = tmem + ((32u * quarter) << 16) + a * kTcN + half * (kTcN / 2);
                     uint32_t ra[32], rb[32];
-                    tc_ld32(tbase, ra);
+                    tc_ld64h(tbase, ra);
                     tc_wait_ld_regs(ra);
 #pragma unroll
-                    for (uint32_t c = 0; c < kChunks; c++) {
-                        uint32_t *cur = (c & 1u) ? rb : ra;
-                        uint32_t *nxt = (c & 1u) ? ra : rb;
-                        if (c + 1 < kChunks) tc_ld32(tbase + 32u * (c + 1), nxt);
-                        const float mx = max32(cur);
+                    for (uint32_t c = 0; c < 2; c++) {
+                        uint32_t *cur = c ? rb : ra;
+                        if (c == 0) tc_ld64h(tbase + 64u, rb);
+                        const float mx = max64h(cur);
                         if (__any_sync(0xffffffffu, mx >= thr)) {
                             float *mine = scratch + ((warp - 2u) * 32u + lane) * 33u;
 #pragma unroll
-                            for (int j = 0; j < 32; j++) mine[j] = __uint_as_float(cur[j]);
-                            emit_chunk(b, sink, wh, mine, thr, L, e, pt + ph + 4u * (half * (kTcN / 2) + 32u * c), lane);
+                            for (int hh = 0; hh < 2; hh++) {
+#pragma unroll
+                                for (int j = 0; j < 16; j++) {
+                                    const __half2 v2 = *reinterpret_cast<const __half2 *>(&cur[16 * hh + j]);
+                                    mine[2 * j] = __low2float(v2);
+                                    mine[2 * j + 1] = __high2float(v2);
+                                }
+                                emit_chunk(b, sink, wh, mine, thr, L, e,
+                                           pt + ph + 4u * (half * (kTcN / 2) + 64u * c + 32u * hh), lane);
+                            }
                         }
-                        if (c + 1 < kChunks) tc_wait_ld_regs(nxt);
+                        if (c == 0) tc_wait_ld_regs(rb);
                     }
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
