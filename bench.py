@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--total", type=float, default=4e9, help="reference bases (default 4 Gbp)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "serving", "indexed", "latency"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "serving", "indexed", "latency", "brute-kernels"],
                     help="sweep: the 4 Gbp maxSubs sweep (default); batched: many query sets "
                          "in one persistent launch vs one launch per set; serving: Poisson "
                          "arrivals with continuous batching")
@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
     ap.add_argument("--slices", type=int, default=16, help="serving: slices per cycle")
     ap.add_argument("--no-solo", action="store_true", help="serving: skip the one-request-at-a-time baseline")
+    ap.add_argument("--sizes", default="16,32,64,512,10000", help="brute-kernels: query-set sizes")
     ap.add_argument("--solo-max-s", type=float, default=180.0,
                     help="serving: wall-time cap of the one-request-at-a-time baseline")
     return ap.parse_args()
@@ -687,6 +688,53 @@ def run_latency(args):
     print(json.dumps(line), flush=True)
 
 
+def run_brute_kernels(args):
+    """The two brute-force kernels on the same pass: bit-plane popcount and
+    the tensor-core one-hot GEMM, over query-set sizes (queries of 20-40 bp,
+    maxSubs 4) against a reference of the 4 Gbp recipe cut to --total bases
+    (default 256 Mbp), device-resident, hits counted only.  Kernel time from
+    the library's CUDA events; the digests of both kernels must agree."""
+    import torch
+    import paper_2607_27291_b300 as P
+    import synth
+    total = int(args.total if args.total != 4e9 else 256e6)
+    sizes = [int(x) for x in args.sizes.split(",")]
+    wl = synth.workload_4gbp(total=total, plants_per_k=1)
+    dev = torch.from_numpy(wl.ref).cuda()
+    segs = list(P.segment_pieces(wl.contig_len, SEG))
+    allq = synth.random_queries(max(sizes), 20, 40, 11)
+    rows = []
+    for nq in sizes:
+        r = {"queries": nq}
+        for kern, name in ((P.IFA_BRUTE_POPC, "popcount"), (P.IFA_BRUTE_TENSOR, "tensor")):
+            h = P.ifa_create(count_only=1, segment_bytes=SEG, profile=1, brute_kernel=kern)
+            P.ifa_load_queries(h, allq[:nq])
+            P.ifa_set_max_subs(h, 4)
+            P.ifa_set_mode(h, P.IFA_MODE_BRUTE)
+            best = None
+            for rep in range(max(1, args.warmup) + args.steps):
+                P.ifa_reset_results(h)
+                for a, b, pc in segs:
+                    P.ifa_push_segment(h, dev[a:b], pc)
+                P.ifa_flush(h)
+                st = P.ifa_get_stats(h)
+                if rep >= max(1, args.warmup):
+                    ms = st["scan_ns"] / 1e6
+                    best = ms if best is None else min(best, ms)
+            dg, _ = P.ifa_get_digest(h)
+            P.ifa_destroy(h)
+            r[name] = {"ms": best, "evals_per_s": st["windows"] / (best * 1e-3), "digest": list(dg)}
+        r["speedup"] = r["popcount"]["ms"] / r["tensor"]["ms"]
+        r["same_digest"] = r["popcount"]["digest"] == r["tensor"]["digest"]
+        rows.append(r)
+    line = {"workload": "brute-kernels", "metric": "(query, strand, window) evaluations/s per brute-force kernel",
+            "unit": "evaluations/s", "value": rows[-1]["tensor"]["evals_per_s"], "sizes": rows,
+            "config": {"reference_bases": int(wl.ref.size), "query_lengths": "20-40", "max_subs": 4,
+                       "hits": "count only", "timing": "best of --steps passes, library CUDA events"},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "batched":
@@ -697,6 +745,8 @@ def main():
         return run_indexed(args)
     if args.workload == "latency":
         return run_latency(args)
+    if args.workload == "brute-kernels":
+        return run_brute_kernels(args)
     rank, world = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
