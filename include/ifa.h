@@ -390,7 +390,8 @@ ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *const *queries,
  *
  * Readings where the paper is silent: FLAG is 16 for strand '-' plus 256
  * for a secondary record; POS is pos + 1; MAPQ is 255 (not available);
- * CIGAR is "<L>M" (no clipping); RNEXT/PNEXT/TLEN are * 0 0; SEQ is the
+ * CIGAR is "<L>M", or "<left>S<L - left - right>M<right>S" for a hit with
+ * soft clips (ifa_hit.clips); RNEXT/PNEXT/TLEN are * 0 0; SEQ is the
  * query on the reference's forward strand (the reverse complement for
  * '-'), upper case, every non-ACGT byte written as N; QUAL is *; the one
  * tag is NM:i:<mismatches>. */
@@ -405,7 +406,7 @@ typedef struct {
 
 /* SAM records for n hits, one line each, no header.  hits (host) is sorted
  * in place into reference order (contig id, pos, strand, query,
- * mismatches).  primary_seen (host, n_queries bytes, zeroed by the caller
+ * mismatches, clips).  primary_seen (host, n_queries bytes, zeroed by the caller
  * once per pass over the reference) marks queries whose primary was already
  * written: a hit is primary when its query's byte is 0, which this call then
  * sets.  Calls must follow the stream order (drain after ifa_flush).

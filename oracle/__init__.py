@@ -36,11 +36,11 @@ def lib():
         u64p = C.POINTER(C.c_uint64)
         L.oracle_brute.restype = C.c_int64
         L.oracle_brute.argtypes = [u8p, u64p, u32p, C.c_uint32, u8p, u64p, u64p, u32p,
-                                   C.c_uint32, C.c_uint32, C.c_void_p, C.c_int64]
+                                   C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int64]
         L.oracle_indexed.restype = C.c_int64
         L.oracle_indexed.argtypes = [u8p, u64p, u32p, C.c_uint32, u8p, u64p, u64p, u32p,
                                      C.c_uint32, C.c_uint32, u32p, u32p, u8p, C.c_uint32,
-                                     C.c_uint32, C.c_void_p, C.c_int64]
+                                     C.c_uint32, C.c_uint32, C.c_void_p, C.c_int64]
         L.oracle_minhits.restype = C.c_uint32
         L.oracle_minhits.argtypes = [C.c_uint32] * 9 + [C.c_uint64, u64p]
         L.oracle_choose_k.restype = C.c_int
@@ -97,10 +97,10 @@ def _pack_queries(queries: Sequence[bytes]):
 
 
 def sort_hits(h: np.ndarray) -> np.ndarray:
-    """Sort by (query, contig, pos, strand, mismatches)."""
+    """Sort by (query, contig, pos, strand, mismatches, clips)."""
     if h.size == 0:
         return h
-    order = np.lexsort((h["mismatches"], h["strand"], h["pos"], h["contig"], h["query"]))
+    order = np.lexsort((h["reserved"], h["mismatches"], h["strand"], h["pos"], h["contig"], h["query"]))
     return h[order]
 
 
@@ -143,8 +143,10 @@ def _run_chunks(fn, ref, contig_len, contig_ids, threads):
 
 
 def brute(queries: Sequence[bytes], ref: np.ndarray, contig_len, max_subs: int,
-          contig_ids=None, threads: int = 1) -> np.ndarray:
-    """All (query, contig, pos, strand, mismatches) with Hamming <= max_subs."""
+          contig_ids=None, threads: int = 1, clip_pct: int = 0) -> np.ndarray:
+    """All (query, contig, pos, strand, mismatches) with Hamming <= max_subs;
+    with clip_pct > 0 also the windows overhanging a contig end by up to
+    floor(clip_pct * L / 100) bases (clips in the `reserved` field)."""
     qcat, qoff, qlen = _pack_queries(queries)
     L = lib()
 
@@ -152,14 +154,15 @@ def brute(queries: Sequence[bytes], ref: np.ndarray, contig_len, max_subs: int,
         return L.oracle_brute(_ptr(qcat, C.c_uint8), _ptr(qoff, C.c_uint64), _ptr(qlen, C.c_uint32),
                               len(queries), _ptr(ref_, C.c_uint8), _ptr(off, C.c_uint64),
                               _ptr(ln, C.c_uint64), _ptr(ids, C.c_uint32), nc, int(max_subs),
-                              out.ctypes.data, cap)
+                              int(clip_pct), out.ctypes.data, cap)
     return _run_chunks(fn, ref, contig_len, contig_ids, threads)
 
 
 def indexed(queries: Sequence[bytes], ref: np.ndarray, contig_len, max_subs: int,
             k_per_query, minhits_per_query, exhaustive_per_query, step: int = 1,
-            mask_w: int = 0, contig_ids=None, threads: int = 1) -> np.ndarray:
-    """Brute hits whose seed count reaches the per-query threshold."""
+            mask_w: int = 0, contig_ids=None, threads: int = 1, clip_pct: int = 0) -> np.ndarray:
+    """Brute hits whose seed count reaches the per-query threshold (clipped
+    windows, clip_pct > 0, are kept exhaustively)."""
     qcat, qoff, qlen = _pack_queries(queries)
     kq = np.ascontiguousarray(k_per_query, dtype=np.uint32)
     mh = np.ascontiguousarray(minhits_per_query, dtype=np.uint32)
@@ -171,7 +174,7 @@ def indexed(queries: Sequence[bytes], ref: np.ndarray, contig_len, max_subs: int
                                 len(queries), _ptr(ref_, C.c_uint8), _ptr(off, C.c_uint64),
                                 _ptr(ln, C.c_uint64), _ptr(ids, C.c_uint32), nc, int(max_subs),
                                 _ptr(kq, C.c_uint32), _ptr(mh, C.c_uint32), _ptr(ex, C.c_uint8),
-                                int(step), int(mask_w), out.ctypes.data, cap)
+                                int(step), int(mask_w), int(clip_pct), out.ctypes.data, cap)
     return _run_chunks(fn, ref, contig_len, contig_ids, threads)
 
 

@@ -28,8 +28,16 @@
  *  - N on either side counts as one mismatch;
  *  - a '-' hit at pos means revcomp(query) equals ref[pos .. pos+L-1] up to
  *    the mismatches, pos being the leftmost forward coordinate;
- *  - windows never leave a contig (no soft clipping), so a contig shorter
- *    than the query gives no hit;
+ *  - soft clipping at contig ends (Methods, "Algorithm Design": alignments
+ *    may overhang a contig end by up to a share of the query length, 25 %
+ *    by default): with clip_pct > 0 a window may start up to
+ *    C = floor(clip_pct * L / 100) bases before its contig or end up to C
+ *    bases after it.  Its overhanging bases are clips, not mismatches; it
+ *    is a hit when clips <= C, at least one base is aligned and the
+ *    mismatches of the aligned bases are <= maxSubs.  pos is the contig
+ *    coordinate of the first aligned base and `reserved` holds the clips
+ *    (left | right << 8).  With clip_pct = 0 windows never leave a contig,
+ *    so a contig shorter than the query gives no hit;
  *  - palindromic queries report both strands.
  */
 #include <stdint.h>
@@ -109,7 +117,7 @@ uint32_t oracle_window_mismatches(const uint8_t *q, uint32_t L, uint8_t strand,
 }
 
 static void put_hit(oracle_hit *out, int64_t cap, int64_t n, uint32_t q, uint32_t c,
-                    uint64_t p, uint8_t t, uint32_t mm)
+                    uint64_t p, uint8_t t, uint32_t mm, uint16_t clips)
 {
     if (n < cap) {
         out[n].query = q;
@@ -117,8 +125,37 @@ static void put_hit(oracle_hit *out, int64_t cap, int64_t n, uint32_t q, uint32_
         out[n].pos = (uint32_t)p;
         out[n].strand = t;
         out[n].mismatches = (uint8_t)(mm > 255 ? 255 : mm);
-        out[n].reserved = 0;
+        out[n].reserved = clips;
     }
+}
+
+/*
+ * Clipped windows of one (query, strand, contig) (Methods, "Algorithm
+ * Design", soft clipping): every start p in [-C, n - L + C] whose window
+ * overhangs the contig (p < 0 or p + L > n) by 1..C bases in total and
+ * keeps at least one base inside it.  Writes the hits from index n on and
+ * returns the new count.
+ */
+static int64_t clipped_windows(const uint8_t *qq, uint32_t L, const uint8_t *r, uint64_t rn, uint32_t clip_pct,
+                               uint32_t max_subs, uint32_t j, uint32_t cid, uint8_t t, oracle_hit *out,
+                               int64_t cap, int64_t n)
+{
+    const int64_t C = (int64_t)((uint64_t)clip_pct * L / 100u);
+    const int64_t len = (int64_t)rn;
+    for (int64_t p = -C; p <= len - (int64_t)L + C; p++) {
+        const int64_t left = p < 0 ? -p : 0;
+        const int64_t right = p + (int64_t)L > len ? p + (int64_t)L - len : 0;
+        const int64_t clips = left + right;
+        if (clips == 0 || clips > C || clips >= (int64_t)L)
+            continue;
+        const uint32_t aligned = L - (uint32_t)clips;
+        uint32_t mm = window_mismatches(qq + left, r + p + left, aligned, max_subs);
+        if (mm <= max_subs) {
+            put_hit(out, cap, n, j, cid, (uint64_t)(p + left), t, mm, (uint16_t)(left | (right << 8)));
+            n++;
+        }
+    }
+    return n;
 }
 
 /*
@@ -133,7 +170,7 @@ static void put_hit(oracle_hit *out, int64_t cap, int64_t n, uint32_t q, uint32_
  */
 int64_t oracle_brute(const uint8_t *qcat, const uint64_t *qoff, const uint32_t *qlen, uint32_t nq,
                      const uint8_t *rcat, const uint64_t *roff, const uint64_t *rlen,
-                     const uint32_t *rid, uint32_t nc, uint32_t max_subs,
+                     const uint32_t *rid, uint32_t nc, uint32_t max_subs, uint32_t clip_pct,
                      oracle_hit *out, int64_t cap)
 {
     int64_t n = 0;
@@ -149,13 +186,15 @@ int64_t oracle_brute(const uint8_t *qcat, const uint64_t *qoff, const uint32_t *
         for (uint8_t t = 0; t < 2; t++) {
             const uint8_t *qq = t ? rev : fwd;
             for (uint32_t c = 0; c < nc; c++) {
+                const uint8_t *r = rcat + roff[c];
+                if (clip_pct)
+                    n = clipped_windows(qq, L, r, rlen[c], clip_pct, max_subs, j, rid[c], t, out, cap, n);
                 if (rlen[c] < L)
                     continue;
-                const uint8_t *r = rcat + roff[c];
                 for (uint64_t p = 0; p + L <= rlen[c]; p++) {
                     uint32_t mm = window_mismatches(qq, r + p, L, max_subs);
                     if (mm <= max_subs) {
-                        put_hit(out, cap, n, j, rid[c], p, t, mm);
+                        put_hit(out, cap, n, j, rid[c], p, t, mm, 0);
                         n++;
                     }
                 }
@@ -200,12 +239,15 @@ static uint32_t window_seeds(const uint8_t *qq, const uint8_t *r, uint32_t L, ui
  * query's threshold.  Per query j: k[j] is its seed length and minhits[j]
  * its threshold; exhaustive[j] != 0 keeps every brute hit of that query
  * (queries with no usable seed length, e.g. ones that contain N).
+ * Clipped windows (clip_pct > 0) are kept exhaustively, as in brute-force
+ * mode: the seed threshold is planned for whole windows (a reading; the
+ * paper does not say how clips enter the Monte Carlo).
  */
 int64_t oracle_indexed(const uint8_t *qcat, const uint64_t *qoff, const uint32_t *qlen, uint32_t nq,
                        const uint8_t *rcat, const uint64_t *roff, const uint64_t *rlen,
                        const uint32_t *rid, uint32_t nc, uint32_t max_subs,
                        const uint32_t *kq, const uint32_t *minhits, const uint8_t *exhaustive,
-                       uint32_t step, uint32_t mask_w, oracle_hit *out, int64_t cap)
+                       uint32_t step, uint32_t mask_w, uint32_t clip_pct, oracle_hit *out, int64_t cap)
 {
     int64_t n = 0;
     for (uint32_t j = 0; j < nq; j++) {
@@ -220,9 +262,11 @@ int64_t oracle_indexed(const uint8_t *qcat, const uint64_t *qoff, const uint32_t
         for (uint8_t t = 0; t < 2; t++) {
             const uint8_t *qq = t ? rev : fwd;
             for (uint32_t c = 0; c < nc; c++) {
+                const uint8_t *r = rcat + roff[c];
+                if (clip_pct)
+                    n = clipped_windows(qq, L, r, rlen[c], clip_pct, max_subs, j, rid[c], t, out, cap, n);
                 if (rlen[c] < L)
                     continue;
-                const uint8_t *r = rcat + roff[c];
                 for (uint64_t p = 0; p + L <= rlen[c]; p++) {
                     uint32_t mm = window_mismatches(qq, r + p, L, max_subs);
                     if (mm > max_subs)
@@ -232,7 +276,7 @@ int64_t oracle_indexed(const uint8_t *qcat, const uint64_t *qoff, const uint32_t
                         if (sd < minhits[j])
                             continue;
                     }
-                    put_hit(out, cap, n, j, rid[c], p, t, mm);
+                    put_hit(out, cap, n, j, rid[c], p, t, mm, 0);
                     n++;
                 }
             }
@@ -488,13 +532,15 @@ static uint64_t mix64(uint64_t z)
 
 /* Digest of a hit list: count, sum (mod 2^64) and xor of
  * mix64(a ^ mix64(b)) with a = query << 32 | contig and
- * b = pos << 32 | strand << 8 | mismatches. */
+ * b = pos << 32 | clips << 16 | strand << 8 | mismatches (clips is 0 for
+ * a window inside its contig). */
 void oracle_digest(const oracle_hit *h, int64_t n, uint64_t out[3])
 {
     uint64_t sum = 0, xr = 0;
     for (int64_t i = 0; i < n; i++) {
         uint64_t a = ((uint64_t)h[i].query << 32) | h[i].contig;
-        uint64_t b = ((uint64_t)h[i].pos << 32) | ((uint64_t)h[i].strand << 8) | h[i].mismatches;
+        uint64_t b = ((uint64_t)h[i].pos << 32) | ((uint64_t)h[i].reserved << 16) | ((uint64_t)h[i].strand << 8) |
+                     h[i].mismatches;
         uint64_t v = mix64(a ^ mix64(b));
         sum += v;
         xr ^= v;

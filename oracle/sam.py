@@ -9,7 +9,9 @@ first valid alignment in reference order (Results, accuracy validation).
 The record fields follow the SAM format specification v1.6, section 1.4
 (11 mandatory tab-separated fields, then optional TAG:TYPE:VALUE fields);
 the values the paper leaves open take these readings: FLAG 0x10 for the
-reverse strand and 0x100 for secondary records, MAPQ 255, CIGAR "<L>M",
+reverse strand and 0x100 for secondary records, MAPQ 255, CIGAR "<L>M", or
+with soft clips at a contig end "<left>S<L - left - right>M<right>S" (the
+SAM specification's soft clip, POS then being the first aligned base),
 SEQ on the forward strand of the reference in upper case with non-ACGT
 bytes written as N, QUAL "*", and the NM tag holding the mismatch count.
 """
@@ -33,11 +35,12 @@ def _reverse_complement(q: bytes) -> str:
 def sam_records(hits: Sequence[tuple], queries: Sequence[bytes], primary_seen: List[bool],
                 query_names: Optional[Sequence[str]] = None,
                 contig_names: Optional[Dict[int, str]] = None) -> str:
-    """SAM lines for hits given as (query, contig, pos, strand, mismatches)
-    tuples.  `primary_seen[q]` is True once query q's primary was written;
-    it is updated in place."""
+    """SAM lines for hits given as (query, contig, pos, strand, mismatches[,
+    clips]) tuples, clips = left | right << 8.  `primary_seen[q]` is True
+    once query q's primary was written; it is updated in place."""
     out = []
-    for (q, contig, pos, strand, mm) in sorted(hits, key=lambda h: (h[1], h[2], h[3], h[0], h[4])):
+    hits = [tuple(h) + (0,) * (6 - len(h)) for h in hits]
+    for (q, contig, pos, strand, mm, clips) in sorted(hits, key=lambda h: (h[1], h[2], h[3], h[0], h[4], h[5])):
         primary = not primary_seen[q]
         primary_seen[q] = True
         flag = 0
@@ -48,7 +51,10 @@ def sam_records(hits: Sequence[tuple], queries: Sequence[bytes], primary_seen: L
         qname = query_names[q] if query_names is not None else "q%d" % q
         rname = contig_names[contig] if contig_names is not None and contig in contig_names else "c%d" % contig
         seq = _reverse_complement(queries[q]) if strand == 1 else _forward_seq(queries[q])
-        fields = [qname, str(flag), rname, str(pos + 1), "255", "%dM" % len(queries[q]),
+        left, right = clips & 0xff, clips >> 8
+        cigar = ("%dS" % left if left else "") + "%dM" % (len(queries[q]) - left - right) + \
+            ("%dS" % right if right else "")
+        fields = [qname, str(flag), rname, str(pos + 1), "255", cigar,
                   "*", "0", "0", seq, "*", "NM:i:%d" % mm]
         out.append("\t".join(fields) + "\n")
     return "".join(out)

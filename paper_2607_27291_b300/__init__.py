@@ -510,7 +510,7 @@ def ifa_last_error(h=None) -> str:
 def sort_hits(h: np.ndarray) -> np.ndarray:
     if h.size == 0:
         return h
-    order = np.lexsort((h["mismatches"], h["strand"], h["pos"], h["contig"], h["query"]))
+    order = np.lexsort((h["reserved"], h["mismatches"], h["strand"], h["pos"], h["contig"], h["query"]))
     return h[order]
 
 

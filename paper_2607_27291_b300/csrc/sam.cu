@@ -92,7 +92,8 @@ ifa_status ifa_sam_records(ifa_hit *hits, uint64_t n, const ifa_sam_info *info, 
         if (a.pos != b.pos) return a.pos < b.pos;
         if (a.strand != b.strand) return a.strand < b.strand;
         if (a.query != b.query) return a.query < b.query;
-        return a.mismatches < b.mismatches;
+        if (a.mismatches != b.mismatches) return a.mismatches < b.mismatches;
+        return a.reserved < b.reserved;
     });
     // flags as they stand after this call; committed only if the text fits
     std::vector<uint8_t> seen(primary_seen, primary_seen + info->n_queries);
@@ -113,8 +114,19 @@ ifa_status ifa_sam_records(ifa_hit *hits, uint64_t n, const ifa_sam_info *info, 
         s.push_back('\t');
         append_u64(s, static_cast<uint64_t>(h.pos) + 1);
         s.append("\t255\t");
-        append_u64(s, L);
-        s.append("M\t*\t0\t0\t");
+        const uint32_t left = h.reserved & 0xffu, right = h.reserved >> 8;
+        if (left + right >= L && L) return sam_fail("ifa_sam_records: clips cover the whole query");
+        if (left) {
+            append_u64(s, left);
+            s.push_back('S');
+        }
+        append_u64(s, L - left - right);
+        s.push_back('M');
+        if (right) {
+            append_u64(s, right);
+            s.push_back('S');
+        }
+        s.append("\t*\t0\t0\t");
         if (h.strand)
             for (uint32_t j = 0; j < L; j++) s.push_back(complement_base(q[L - 1 - j]));
         else

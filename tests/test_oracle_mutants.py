@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import test_oracle_brute as tb
+import test_oracle_clip as tc
 import test_oracle_indexed as ti
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "ifa_oracle.c")
@@ -36,6 +37,19 @@ MUTANTS = {
     "seed threshold strict": ("if (sd < minhits[j])", "if (sd <= minhits[j])"),
     "seed ignores N": ("            if (a == 'N' || b == 'N' || a != b)\n                ok = 0;", "            if (a != b)\n                ok = 0;"),
     "choose shortest k": ("if (m >= 1 && k > best_k) {", "if (m >= 1 && (best_k == 0 || k < best_k)) {"),
+    "clip range start": ("for (int64_t p = -C; p <= len - (int64_t)L + C; p++) {",
+                         "for (int64_t p = -C + 1; p <= len - (int64_t)L + C; p++) {"),
+    "clip range end": ("for (int64_t p = -C; p <= len - (int64_t)L + C; p++) {",
+                       "for (int64_t p = -C; p < len - (int64_t)L + C; p++) {"),
+    "clip budget strict": ("if (clips == 0 || clips > C || clips >= (int64_t)L)",
+                           "if (clips == 0 || clips >= C || clips >= (int64_t)L)"),
+    "clips counted as mismatches": ("uint32_t mm = window_mismatches(qq + left, r + p + left, aligned, max_subs);",
+                                    "uint32_t mm = window_mismatches(qq + left, r + p + left, aligned, max_subs) + (uint32_t)clips;"),
+    "clipped query not shifted": ("uint32_t mm = window_mismatches(qq + left, r + p + left, aligned, max_subs);",
+                                  "uint32_t mm = window_mismatches(qq, r + p + left, aligned, max_subs);"),
+    "clip sides swapped": ("(uint16_t)(left | (right << 8))", "(uint16_t)(right | (left << 8))"),
+    "clipped pos off by one": ("(uint64_t)(p + left), t, mm,", "(uint64_t)(p + left + 1), t, mm,"),
+    "digest ignores clips": ("((uint64_t)h[i].reserved << 16) | ", ""),
 }
 
 
@@ -64,6 +78,10 @@ def _pins():
         lambda: ti.test_minhits_one_equals_text_seed_test(wl2, 7, 1, 3),
         lambda: ti.test_indexed_subset_and_degenerate_cases(wl2),
         lambda: ti.test_seed_counts_closed_forms(wl2),
+        lambda: tc.test_closed_form_count_when_every_window_passes(25),
+        lambda: tc.test_planted_overhangs_are_found_with_their_clips("start"),
+        lambda: tc.test_planted_overhangs_are_found_with_their_clips("end"),
+        lambda: tc.test_digest_sees_the_clips(),
     ]
 
 

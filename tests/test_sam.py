@@ -91,3 +91,14 @@ def test_library_rejects_bad_hits_and_keeps_flags():
     with pytest.raises(P.IfaError):
         P.ifa_sam_records(bad, _queries(), seen)
     assert P.ifa_sam_records(_hit_array([]), _queries(), seen) == b""
+
+
+def test_clipped_records_match_hand_written():
+    seen = [False, False]
+    text = osam.sam_records([tuple(h) for h in GOLDEN["clipped_hits"]], _queries(), seen)
+    assert text == "".join(r + "\n" for r in GOLDEN["clipped_records"])
+    a = np.zeros(len(GOLDEN["clipped_hits"]), dtype=P.HIT_DTYPE)
+    for i, (q, c, p, t, m, cl) in enumerate(GOLDEN["clipped_hits"]):
+        a[i] = (q, c, p, t, m, cl)
+    got = P.ifa_sam_records(a, _queries(), np.zeros(2, np.uint8))
+    assert got.decode() == "".join(r + "\n" for r in GOLDEN["clipped_records"])
