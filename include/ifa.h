@@ -21,9 +21,9 @@
  *    Methods, "Algorithm Design").
  *  - Positions are 0-based.  Strand 0 is '+', strand 1 is '-'; a '-' hit at
  *    pos means the reverse complement of the query lies at
- *    ref[pos .. pos+L-1] with `mismatches` substitutions.  A window never
- *    leaves its contig (no soft clipping), so contigs shorter than a query
- *    give it no hit.
+ *    ref[pos .. pos+L-1] with `mismatches` substitutions.  A window stays
+ *    inside its contig unless soft clipping is on (ifa_config.clip_pct);
+ *    without it a contig shorter than a query gives that query no hit.
  *  - Query ids are dense in load order.  Contig ids are the caller's; each
  *    new contig's id must be larger than the previous one's.
  *  - Device work runs on the handle's compute stream (ifa_set_stream) and
@@ -80,12 +80,14 @@ typedef struct {
     uint32_t pos;         /* leftmost forward coordinate in the contig */
     uint8_t strand;       /* 0 '+', 1 '-' */
     uint8_t mismatches;   /* Hamming distance of the window */
-    uint16_t reserved;    /* 0 */
+    uint16_t clips;       /* soft clips at a contig end: left | right << 8 (0 inside a contig);
+                             pos is then the first aligned base */
 } ifa_hit;
 
 /* Order-independent digest of every hit produced so far: the count, and
  * the sum (mod 2^64) and xor of mix(a ^ mix(b)) over hits, where
- * a = query << 32 | contig, b = pos << 32 | strand << 8 | mismatches and
+ * a = query << 32 | contig, b = pos << 32 | clips << 16 | strand << 8 |
+ * mismatches and
  * mix is the splitmix64 output function.  Kept apart from the hit buffer,
  * so it stays exact when that buffer overflows or is disabled. */
 typedef struct {
@@ -123,7 +125,10 @@ typedef struct {
     uint32_t minhits_den;
     uint32_t minhits_trials;       /* Monte Carlo trials, paper default 200,000 */
     uint64_t minhits_seed;         /* Philox key of the Monte Carlo */
-    uint32_t max_clips;            /* must be 0: soft clipping is not implemented */
+    uint32_t clip_pct;             /* soft clipping at contig ends (Methods, Algorithm Design): a window may
+                                      overhang its contig by up to floor(clip_pct * L / 100) bases, which
+                                      count as clips, not mismatches; 0 = off, at most 50 (paper: 25);
+                                      streaming API only */
     uint32_t exhaustive_fallback;  /* 1: queries with no qualifying k are scanned exhaustively */
     uint32_t auto_crossover;       /* IFA_MODE_AUTO picks indexed from this many queries on */
     uint32_t profile;              /* 1: time every scan kernel with CUDA events (ifa_stats.scan_ns) */
@@ -150,7 +155,7 @@ ifa_status ifa_config_default(ifa_config *cfg);
 
 /* Create a handle on cfg->device; allocates device buffers for one segment
  * pair, the hit buffer and the digest.  *out is NULL on failure.
- * Errors: INVALID_ARG (NULL, max_clips != 0, bad k list), CUDA (no such
+ * Errors: INVALID_ARG (NULL, clip_pct > 50, bad k list), CUDA (no such
  * device), OOM. */
 ifa_status ifa_create(const ifa_config *cfg, ifa_handle **out);
 

@@ -32,7 +32,7 @@ IFA_BRUTE_AUTO, IFA_BRUTE_POPC, IFA_BRUTE_TENSOR = 0, 1, 2
 IFA_MAX_QUERY_LEN = 255
 
 HIT_DTYPE = np.dtype([("query", "<u4"), ("contig", "<u4"), ("pos", "<u4"),
-                      ("strand", "u1"), ("mismatches", "u1"), ("reserved", "<u2")])
+                      ("strand", "u1"), ("mismatches", "u1"), ("clips", "<u2")])
 PIECE_DTYPE = np.dtype([("contig", "<u4"), ("last", "<u4"), ("offset_in_contig", "<u8"),
                         ("start", "<u8"), ("len", "<u8")])
 
@@ -42,7 +42,7 @@ class ifa_config(C.Structure):
                 ("segment_bytes", C.c_uint64), ("k_list", C.c_uint32 * 8), ("n_k", C.c_uint32),
                 ("kmer_step", C.c_uint32), ("mask_width", C.c_uint32), ("minhits_num", C.c_uint32),
                 ("minhits_den", C.c_uint32), ("minhits_trials", C.c_uint32),
-                ("minhits_seed", C.c_uint64), ("max_clips", C.c_uint32),
+                ("minhits_seed", C.c_uint64), ("clip_pct", C.c_uint32),
                 ("exhaustive_fallback", C.c_uint32), ("auto_crossover", C.c_uint32),
                 ("profile", C.c_uint32), ("brute_kernel", C.c_uint32), ("reserved", C.c_uint32 * 5)]
 
@@ -510,7 +510,7 @@ def ifa_last_error(h=None) -> str:
 def sort_hits(h: np.ndarray) -> np.ndarray:
     if h.size == 0:
         return h
-    order = np.lexsort((h["reserved"], h["mismatches"], h["strand"], h["pos"], h["contig"], h["query"]))
+    order = np.lexsort((h["clips"], h["mismatches"], h["strand"], h["pos"], h["contig"], h["query"]))
     return h[order]
 
 

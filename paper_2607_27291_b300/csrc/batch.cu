@@ -639,7 +639,7 @@ ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, con
         d.start = B.nbases + pieces[i].start;
         d.contig_off = 0;
         d.contig = pieces[i].contig;
-        d.pad = 0;
+        d.last = pieces[i].last ? 1u : 0u;
         fresh.push_back(d);
     }
     if (!fresh.empty()) {
@@ -714,6 +714,8 @@ ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per
     if (!h) return IFA_ERR_INVALID_ARG;
     BatchState &B = h->batch;
     if (B.nbases == 0 || B.sets.empty()) return bfail(h, IFA_ERR_BAD_STATE, "ifa_batch_run: empty store or no sets");
+    if (h->cfg.clip_pct)
+        return bfail(h, IFA_ERR_INVALID_ARG, "ifa_batch_run: soft clipping (clip_pct) applies to the streaming calls only");
     if (kind != IFA_BATCH_PERSISTENT && kind != IFA_BATCH_PER_SET)
         return bfail(h, IFA_ERR_INVALID_ARG, "ifa_batch_run: unknown kind");
     BCK(h, cudaSetDevice(h->dev));

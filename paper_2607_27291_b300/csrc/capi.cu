@@ -242,7 +242,7 @@ ifa_status ifa_config_default(ifa_config *cfg) {
     cfg->minhits_den = 1000;
     cfg->minhits_trials = 200000;  // paper default iterations
     cfg->minhits_seed = 1;
-    cfg->max_clips = 0;
+    cfg->clip_pct = 0;
     cfg->exhaustive_fallback = 0;
     cfg->auto_crossover = 150;  // paper: crossover between 100 and 200 queries (RefSeq)
     return IFA_OK;
@@ -252,8 +252,8 @@ ifa_status ifa_create(const ifa_config *cfg, ifa_handle **out) {
     if (!out) return fail(nullptr, IFA_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!cfg) return fail(nullptr, IFA_ERR_INVALID_ARG, "cfg is NULL");
-    if (cfg->max_clips != 0)
-        return fail(nullptr, IFA_ERR_INVALID_ARG, "max_clips must be 0 (soft clipping not implemented)");
+    if (cfg->clip_pct > 50)
+        return fail(nullptr, IFA_ERR_INVALID_ARG, "clip_pct must be at most 50 (percent of the query length)");
     if (cfg->brute_kernel > IFA_BRUTE_TENSOR)
         return fail(nullptr, IFA_ERR_INVALID_ARG, "brute_kernel must be 0 (auto), 1 (popcount) or 2 (tensor cores)");
     if (cfg->n_k == 0 || cfg->n_k > IFA_MAX_KLIST)
@@ -456,7 +456,7 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
         hp[i].start = i == 0 ? H - hlen : H + pieces[i].start;
         hp[i].contig_off = pieces[i].offset_in_contig - (i == 0 ? hlen : 0);
         hp[i].contig = pieces[i].contig;
-        hp[i].pad = 0;
+        hp[i].last = pieces[i].last ? 1u : 0u;
     }
     CK(h, cudaMemcpyAsync(h->d_pieces[slot], hp, n * sizeof(DevPiece), cudaMemcpyHostToDevice, h->copy_stream));
     const uint8_t *dsrc = ascii;
@@ -520,6 +520,11 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
             for (const Chunk &c : h->chunks)
                 CK(h, launch_scan_brute(b, qt, c.e0, c.e1, h->max_subs, c.lmin, c.lmax, sink, h->stream, &launches));
         }
+    }
+    if (h->cfg.clip_pct) {
+        // windows overhanging contig ends, exhaustively in either mode
+        CK(h, launch_clip_scan(b, qt, qt.n_entries, h->cfg.clip_pct, h->max_subs, h->lmax, sink, h->stream));
+        launches++;
     }
     st = prof_end(h, prof_stop, launches - before_scan);
     if (st != IFA_OK) return st;

@@ -50,7 +50,7 @@ struct WarpHitsT {
         if (n == 0) return;
         if (lane < n) {
             const ifa_hit h = buf[lane];
-            const uint64_t v = hit_digest_item(h.query, h.contig, h.pos, h.strand, h.mismatches);
+            const uint64_t v = hit_digest_item(h.query, h.contig, h.pos, h.strand, h.mismatches, h.clips);
             dcount += 1;
             dsum += v;
             dxor ^= v;
@@ -81,14 +81,14 @@ struct WarpHitsT {
     // when all hitting lanes share one entry; otherwise (null) each hit adds one
     // to the query's global counter.
     __device__ void emit(const HitSink &s, uint32_t lane, bool hit, uint32_t q, uint32_t contig,
-                         uint32_t pos, uint32_t strand, uint32_t mm, uint32_t *entry_count) {
+                         uint32_t pos, uint32_t strand, uint32_t mm, uint32_t *entry_count, uint32_t clips = 0) {
         const uint32_t ballot = __ballot_sync(0xffffffffu, hit);
         if (ballot == 0) return;
         const uint32_t cnt = __popc(ballot);
         if constexpr (MULTI) {
             // each hit goes straight to its request's own ring and digest
             if (hit) {
-                ring_put(s, q, contig, pos, strand, mm);
+                ring_put(s, q, contig, pos, strand, mm, clips);
                 if (!entry_count) atomicAdd(&s.qcount[q], 1ull);
             }
             if (entry_count && lane == static_cast<uint32_t>(__ffs(ballot) - 1)) atomicAdd(entry_count, cnt);
@@ -106,7 +106,7 @@ struct WarpHitsT {
             h.pos = pos;
             h.strand = static_cast<uint8_t>(strand);
             h.mismatches = static_cast<uint8_t>(mm > 255 ? 255 : mm);
-            h.reserved = 0;
+            h.clips = static_cast<uint16_t>(clips);
             buf[n + r] = h;
         }
         n += cnt;
@@ -115,10 +115,10 @@ struct WarpHitsT {
 
     // One hit to a request's own ring and digest (serving).
     __device__ static void ring_put(const HitSink &s, uint32_t q, uint32_t contig, uint32_t pos, uint32_t strand,
-                                    uint32_t mm) {
+                                    uint32_t mm, uint32_t clips = 0) {
         const RingDesc R = s.rings[s.q2r[q]];
         const uint32_t rq = q - R.qfirst;
-        const uint64_t v = hit_digest_item(rq, contig, pos, strand, mm);
+        const uint64_t v = hit_digest_item(rq, contig, pos, strand, mm, clips);
         atomicAdd(&R.counters[2], 1ull);
         atomicAdd(&R.counters[3], static_cast<unsigned long long>(v));
         atomicXor(&R.counters[4], static_cast<unsigned long long>(v));
@@ -130,7 +130,7 @@ struct WarpHitsT {
             h.pos = pos;
             h.strand = static_cast<uint8_t>(strand);
             h.mismatches = static_cast<uint8_t>(mm > 255 ? 255 : mm);
-            h.reserved = 0;
+            h.clips = static_cast<uint16_t>(clips);
             R.ring[idx] = h;
         } else {
             R.counters[1] = 1ull;
@@ -213,7 +213,7 @@ struct WarpHitsT {
                             h.pos = pos;
                             h.strand = static_cast<uint8_t>(strand);
                             h.mismatches = static_cast<uint8_t>(mm);
-                            h.reserved = 0;
+                            h.clips = 0;
                             s.ring[slot] = h;
                         } else {
                             *s.overflow = 1u;

@@ -43,7 +43,7 @@ struct DevPiece {
     uint64_t start;        // first base of the piece in batch coordinates
     uint64_t contig_off;   // contig coordinate of `start`
     uint32_t contig;       // caller's contig id
-    uint32_t pad;
+    uint32_t last;         // 1: the contig ends with this piece (its end is the next piece's start)
 };
 
 // One request's own hit ring (serving): counters = {head, overflow, digest
@@ -122,9 +122,9 @@ __host__ __device__ inline uint64_t mix64(uint64_t z) {
 }
 
 __host__ __device__ inline uint64_t hit_digest_item(uint32_t q, uint32_t contig, uint32_t pos,
-                                                    uint32_t strand, uint32_t mm) {
+                                                    uint32_t strand, uint32_t mm, uint32_t clips = 0) {
     uint64_t a = (static_cast<uint64_t>(q) << 32) | contig;
-    uint64_t b = (static_cast<uint64_t>(pos) << 32) | (strand << 8) | mm;
+    uint64_t b = (static_cast<uint64_t>(pos) << 32) | (static_cast<uint64_t>(clips) << 16) | (strand << 8) | mm;
     return mix64(a ^ mix64(b));
 }
 
@@ -147,6 +147,10 @@ __device__ inline uint32_t find_piece(const DevPiece *pc, uint32_t n, uint64_t p
 
 // ---------------------------------------------------------------- launchers
 // (defined in the .cu files; all enqueue on `st`)
+
+// Soft-clipped windows at contig ends (clip.cu).
+cudaError_t launch_clip_scan(const Batch &b, const QueryTable &qt, uint32_t nent, uint32_t clip_pct, uint32_t s,
+                             uint32_t lmax, const HitSink &sink, cudaStream_t st);
 
 // Tensor-core brute-force scan (scan_tc.cu): queries up to 64 bases.
 uint32_t tc_lpad(uint32_t lmax);

@@ -261,7 +261,7 @@ ifa_status indexed_plan_q(IndexedState &S, const std::vector<std::string> &qs,
         }
     std::vector<uint32_t> bm(bL.size());
     ifa_status r = minhits_device(bL.data(), bS.data(), bK.data(), static_cast<uint32_t>(bL.size()),
-                                  cfg.kmer_step, cfg.mask_width, cfg.max_clips, cfg.minhits_num,
+                                  cfg.kmer_step, cfg.mask_width, 0u /* clipped windows are scanned exhaustively */, cfg.minhits_num,
                                   cfg.minhits_den, cfg.minhits_trials, cfg.minhits_seed, bm.data(), st,
                                   stride, err);
     if (r != IFA_OK) return r;

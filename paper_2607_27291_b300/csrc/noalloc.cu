@@ -147,7 +147,7 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
         hp[i].start = pieces[i].start;
         hp[i].contig_off = 0;
         hp[i].contig = pieces[i].contig;
-        hp[i].pad = 0;
+        hp[i].last = 1;
     }
 
     // ---- enqueue: copies into the scratch, zeroing, pack, scan

@@ -93,7 +93,7 @@ ifa_status ifa_sam_records(ifa_hit *hits, uint64_t n, const ifa_sam_info *info, 
         if (a.strand != b.strand) return a.strand < b.strand;
         if (a.query != b.query) return a.query < b.query;
         if (a.mismatches != b.mismatches) return a.mismatches < b.mismatches;
-        return a.reserved < b.reserved;
+        return a.clips < b.clips;
     });
     // flags as they stand after this call; committed only if the text fits
     std::vector<uint8_t> seen(primary_seen, primary_seen + info->n_queries);
@@ -114,7 +114,7 @@ ifa_status ifa_sam_records(ifa_hit *hits, uint64_t n, const ifa_sam_info *info, 
         s.push_back('\t');
         append_u64(s, static_cast<uint64_t>(h.pos) + 1);
         s.append("\t255\t");
-        const uint32_t left = h.reserved & 0xffu, right = h.reserved >> 8;
+        const uint32_t left = h.clips & 0xffu, right = h.clips >> 8;
         if (left + right >= L && L) return sam_fail("ifa_sam_records: clips cover the whole query");
         if (left) {
             append_u64(s, left);

@@ -242,6 +242,8 @@ ifa_status ifa_serve_start(ifa_handle *h, uint32_t n_slices, uint64_t hbm_budget
     if (!h) return IFA_ERR_INVALID_ARG;
     if (n_slices == 0 || ring_hits == 0) return sfail(h, IFA_ERR_INVALID_ARG, "ifa_serve_start: n_slices and ring_hits must be > 0");
     if (h->batch.nbases == 0) return sfail(h, IFA_ERR_BAD_STATE, "ifa_serve_start: the reference store is empty");
+    if (h->cfg.clip_pct)
+        return sfail(h, IFA_ERR_INVALID_ARG, "ifa_serve_start: soft clipping (clip_pct) applies to the streaming calls only");
     SCK(h, cudaSetDevice(h->dev));
     serve_release(h);
     ServeState &S = h->serve;

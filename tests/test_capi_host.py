@@ -69,11 +69,11 @@ def test_defaults_are_the_papers():
                                                   g["minhits_probability"]["den"])
     assert cfg.minhits_trials == g["minhits_trials"]["value"]
     assert g["crossover_queries"]["low"] <= cfg.auto_crossover <= g["crossover_queries"]["high"]
-    assert cfg.max_clips == 0 and cfg.kmer_step == 1 and cfg.mask_width == 0
+    assert cfg.clip_pct == 0 and cfg.kmer_step == 1 and cfg.mask_width == 0
 
 
 def test_bad_config_rejected_before_device():
-    for kw in ({"max_clips": 1}, {"n_k": 0}, {"kmer_step": 0}, {"minhits_den": 0},
+    for kw in ({"clip_pct": 51}, {"n_k": 0}, {"kmer_step": 0}, {"minhits_den": 0},
                {"k_list": [40]}, {"segment_bytes": 0}):
         with pytest.raises(P.IfaError) as ei:
             P.ifa_create(**kw)

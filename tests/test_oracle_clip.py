@@ -18,7 +18,7 @@ def rc(q: bytes) -> bytes:
 def _keyset(h, with_query=True):
     return set(zip(*( ([h["query"].tolist()] if with_query else []) +
                      [h["contig"].tolist(), h["pos"].tolist(), h["strand"].tolist(),
-                      h["mismatches"].tolist(), h["reserved"].tolist()])))
+                      h["mismatches"].tolist(), h["clips"].tolist()])))
 
 
 def test_zero_clip_is_the_unclipped_scan():
@@ -26,7 +26,7 @@ def test_zero_clip_is_the_unclipped_scan():
     a = oracle.brute(wl.queries, wl.ref, wl.contig_len, 3)
     b = oracle.brute(wl.queries, wl.ref, wl.contig_len, 3, clip_pct=0)
     assert a.tobytes() == b.tobytes()
-    assert (a["reserved"] == 0).all()
+    assert (a["clips"] == 0).all()
 
 
 @pytest.mark.parametrize("pct", [10, 25, 50])
@@ -50,7 +50,7 @@ def test_closed_form_count_when_every_window_passes(pct):
     # clip fields: left + right <= C, and each clipped hit keeps >= 1 aligned base
     for h in hits:
         L = len(queries[h["query"]])
-        left, right = int(h["reserved"]) & 0xff, int(h["reserved"]) >> 8
+        left, right = int(h["clips"]) & 0xff, int(h["clips"]) >> 8
         assert left + right <= pct * L // 100
         assert left + right < L
 
@@ -123,5 +123,5 @@ def test_digest_sees_the_clips():
     h = np.zeros(1, oracle.HIT_DTYPE)
     h[0] = (1, 2, 0, 0, 1, 0)
     d0 = oracle.digest(h)
-    h["reserved"] = 2
+    h["clips"] = 2
     assert oracle.digest(h) != d0

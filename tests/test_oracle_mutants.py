@@ -49,7 +49,7 @@ MUTANTS = {
                                   "uint32_t mm = window_mismatches(qq, r + p + left, aligned, max_subs);"),
     "clip sides swapped": ("(uint16_t)(left | (right << 8))", "(uint16_t)(right | (left << 8))"),
     "clipped pos off by one": ("(uint64_t)(p + left), t, mm,", "(uint64_t)(p + left + 1), t, mm,"),
-    "digest ignores clips": ("((uint64_t)h[i].reserved << 16) | ", ""),
+    "digest ignores clips": ("((uint64_t)h[i].clips << 16) | ", ""),
 }
 
 
