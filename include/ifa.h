@@ -62,7 +62,8 @@ typedef enum {
 } ifa_mode;
 
 typedef enum {
-    IFA_BRUTE_AUTO = 0,    /* tensor cores from 32 queries on, when eligible */
+    IFA_BRUTE_AUTO = 0,    /* tensor cores from 32 queries on when eligible and hits are sparse (a random
+                              window of the shortest query passes with probability <= 1e-4) */
     IFA_BRUTE_POPC = 1,    /* bit-plane XOR/OR/popcount kernel */
     IFA_BRUTE_TENSOR = 2   /* one-hot GEMM on the tensor cores; queries of at most 64 bases */
 } ifa_brute_kernel;

@@ -8,6 +8,7 @@
 // not by the reference size (Methods, "Memory Management").
 #include <algorithm>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -211,13 +212,32 @@ namespace {
 // The brute-force kernel of a pass: the tensor cores when forced, or (auto)
 // from 64 entries (32 queries) on, where one half-filled 128-entry tile
 // already matches the popcount kernel (measured on B300: 1.04x at 32
-// queries, 2.0x from 64 queries on, 256 Mbp, maxSubs 4).
+// queries, 2.0x from 64 queries on, 256 Mbp, maxSubs 4), as long as hits
+// are sparse (below).
 constexpr uint32_t kTcAutoEntries = 64;
+
+// The tensor-core kernel tests whole 64-window chunks and takes every hit of
+// a flagged chunk one by one, so it suits sparse hits.  Probability that a
+// random window of a query of L bases (independent uniform bases, a base
+// matching with probability 1/4) has at most s mismatches.
+double random_window_hit_rate(uint32_t L, uint32_t s) {
+    if (s >= L) return 1.0;
+    double term = std::pow(0.25, static_cast<double>(L));  // i = 0 mismatches
+    double sum = term;
+    for (uint32_t i = 1; i <= s; i++) {
+        term *= 3.0 * static_cast<double>(L - i + 1) / static_cast<double>(i);
+        sum += term;
+    }
+    return sum;
+}
+
+constexpr double kTcAutoMaxHitRate = 1e-4;
 
 bool use_tensor_cores(const ifa_handle *h) {
     if (!h->d_tcA) return false;
     if (h->cfg.brute_kernel == IFA_BRUTE_TENSOR) return true;
-    return h->cfg.brute_kernel == IFA_BRUTE_AUTO && 2 * h->qs.size() >= kTcAutoEntries;
+    return h->cfg.brute_kernel == IFA_BRUTE_AUTO && 2 * h->qs.size() >= kTcAutoEntries &&
+           random_window_hit_rate(h->lmin, h->max_subs) <= kTcAutoMaxHitRate;
 }
 
 }  // namespace
