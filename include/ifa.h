@@ -200,7 +200,9 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len,
 
 /* Wait until every pushed segment is scanned.  Returns HIT_OVERFLOW if the
  * hit buffer filled since the last ifa_reset_results (hits already written
- * stay valid; digest and counts stay exact). */
+ * stay valid; digest and counts stay exact), and TIMEOUT if a tensor-core
+ * scan's pipeline wait gave up (its results are incomplete; the context
+ * stays usable and ifa_reset_results clears the status). */
 ifa_status ifa_flush(ifa_handle *h);
 
 /* Copy up to cap buffered hits into out (host memory) and release them from
@@ -214,9 +216,9 @@ ifa_status ifa_drain_hits(ifa_handle *h, ifa_hit *out, uint64_t cap, uint64_t *n
  * receives one count per loaded query.  Implies ifa_flush(). */
 ifa_status ifa_get_digest(ifa_handle *h, ifa_digest *d, uint64_t *per_query_counts);
 
-/* Forget hits, digest, counts, overflow, statistics and the stream
- * position (the next segment may start any contig); keeps the queries,
- * maxSubs and mode. */
+/* Forget hits, digest, counts, overflow, a tensor-core timeout status,
+ * statistics and the stream position (the next segment may start any
+ * contig); keeps the queries, maxSubs and mode. */
 ifa_status ifa_reset_results(ifa_handle *h);
 
 /* Counters since the last reset. */

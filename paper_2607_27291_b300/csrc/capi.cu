@@ -674,6 +674,8 @@ ifa_status ifa_reset_results(ifa_handle *h) {
     h->stats = ifa_stats{};
     if (h->idx.d_candidates) CK(h, cudaMemset(h->idx.d_candidates, 0, sizeof(unsigned long long)));
     if (h->batch.d_cand) CK(h, cudaMemset(h->batch.d_cand, 0, sizeof(unsigned long long)));
+    if (h->d_tc_status) CK(h, cudaMemset(h->d_tc_status, 0, 2 * sizeof(unsigned int)));
+    h->tc_used = false;
     return IFA_OK;
 }
 
