@@ -135,7 +135,10 @@ typedef struct {
     uint32_t profile;              /* 1: time every scan kernel with CUDA events (ifa_stats.scan_ns) */
     uint32_t brute_kernel;         /* brute-force kernel: 0 automatic, 1 popcount, 2 tensor cores
                                       (one-hot e4m3 GEMM; queries of at most 64 bases) */
-    uint32_t reserved[5];
+    uint32_t test_stall;           /* testing only (keep 0): 1 makes each tensor-core CTA withhold its
+                                      first tile, so a pipeline wait runs out after its 4 s limit and
+                                      ifa_flush reports TIMEOUT -- the bounded-wait path, without a fault */
+    uint32_t reserved[4];
 } ifa_config;
 
 typedef struct {

@@ -44,7 +44,8 @@ class ifa_config(C.Structure):
                 ("minhits_den", C.c_uint32), ("minhits_trials", C.c_uint32),
                 ("minhits_seed", C.c_uint64), ("clip_pct", C.c_uint32),
                 ("exhaustive_fallback", C.c_uint32), ("auto_crossover", C.c_uint32),
-                ("profile", C.c_uint32), ("brute_kernel", C.c_uint32), ("reserved", C.c_uint32 * 5)]
+                ("profile", C.c_uint32), ("brute_kernel", C.c_uint32), ("test_stall", C.c_uint32),
+                ("reserved", C.c_uint32 * 4)]
 
 
 class ifa_digest(C.Structure):

@@ -533,7 +533,7 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
                 CK(h, cudaMemsetAsync(h->d_tc_status, 0, 2 * sizeof(unsigned int), h->stream));
             }
             CK(h, launch_scan_tc(b, h->d_tcA, h->d_qmeta, qt.n_entries, h->tc_lpad, h->max_subs, sink,
-                                 h->d_tc_status, h->stream));
+                                 h->d_tc_status, h->stream, h->cfg.test_stall));
             h->tc_used = true;
             launches++;
         } else {

@@ -156,7 +156,8 @@ cudaError_t launch_clip_scan(const Batch &b, const QueryTable &qt, uint32_t nent
 uint32_t tc_lpad(uint32_t lmax);
 bool tc_eligible(uint32_t lmax);
 cudaError_t launch_scan_tc(const Batch &b, const uint8_t *tcA, const uint32_t *meta, uint32_t nent, uint32_t lpad,
-                           uint32_t s, const HitSink &sink, unsigned int *status, cudaStream_t st);
+                           uint32_t s, const HitSink &sink, unsigned int *status, cudaStream_t st,
+                           uint32_t withhold_first = 0);
 
 cudaError_t launch_pack(const uint8_t *halo, uint32_t hlen, uint32_t H, const uint8_t *seg,
                         uint64_t slen, uint4 *words, uint64_t nwords_padded, cudaStream_t st);

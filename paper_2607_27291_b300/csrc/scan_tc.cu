@@ -30,9 +30,9 @@
 //               compare each entry's row with L - maxSubs and emit the hits
 //               after checking that the window lies inside one piece and
 //               belongs to this batch.
-// Every mbarrier wait is bounded; a wait that gives up sets a status bit and
-// makes every role skip its remaining work, so the CTA still reaches its
-// barriers and frees the TMEM.
+// Every mbarrier wait is bounded (4 s); a wait that gives up sets a status
+// bit and makes every role skip its remaining work, so the CTA still reaches
+// its barriers and frees the TMEM, and the host reads the status.
 #include <cstring>
 #include <string>
 #include <vector>
@@ -56,7 +56,7 @@ constexpr uint32_t kTcMaxLpad = 64;             // queries up to 64 bases
 constexpr size_t kTcHead = 8192;                // barriers, per-row data, hit staging
 constexpr size_t kTcScratch = kTcEpiWarps * 32 * 33 * sizeof(float);
 constexpr size_t kTcSmem = 120 * 1024;          // above half of an SM's shared memory: one CTA per SM
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint64_t kWaitLimitNs = 4000000000ull;  // a pipeline wait gives up after 4 s
 
 struct TcHead {
     unsigned long long full_b[2], empty_b[2], full_acc[2], empty_acc[2];
@@ -93,8 +93,17 @@ __device__ __forceinline__ uint64_t mdesc(uint32_t addr, uint32_t lbo, uint32_t 
 constexpr uint32_t kIdesc = (0u << 4) | (static_cast<uint32_t>(kTcN >> 3) << 17) |
                             (static_cast<uint32_t>(kTcM >> 4) << 24);
 
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the barrier's phase `parity`; false when another role gave up or
+// this wait passed its time limit (then the CTA's abort flag is set).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abort) {
-    for (uint32_t i = 0; i < kSpinLimit; i++) {
+    uint64_t t0 = 0;
+    for (uint32_t i = 0;; i++) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
@@ -102,10 +111,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if ((i & 255u) == 0 && *abort) return false;
+        if ((i & 63u) == 63u) {
+            if (*abort) return false;
+            const uint64_t t = global_ns();
+            if (t0 == 0) {
+                t0 = t;
+            } else if (t - t0 > kWaitLimitNs) {
+                *abort = 1;
+                return false;
+            }
+        }
     }
-    *abort = 1;
-    return false;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -201,7 +217,7 @@ __device__ __noinline__ void emit_chunk(const Batch &b, const HitSink &sink, War
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__ meta, uint32_t nent,
           uint32_t lpad, uint32_t s, uint32_t n_rt, uint32_t rt_per_item, uint32_t n_rchunks, uint32_t n_items,
-          HitSink sink, unsigned int *status, unsigned int *work) {
+          HitSink sink, unsigned int *status, unsigned int *work, uint32_t withhold_first) {
     extern __shared__ __align__(1024) uint8_t smem[];
     TcHead &H = *reinterpret_cast<TcHead *>(smem);
     const uint32_t K = 4u * lpad;                   // bytes per operand row
@@ -339,7 +355,8 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&H.full_b[sbuf]));
+                // (testing: withhold the CTA's first tile so that the MMA's wait runs out)
+                if (lane == 0 && !(withhold_first && g == 0)) mbar_arrive(smem_u32(&H.full_b[sbuf]));
             }
         } else {
             // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns
@@ -441,7 +458,8 @@ void tc_operand(const std::vector<std::string> &qs, uint32_t lpad, std::vector<u
 }
 
 cudaError_t launch_scan_tc(const Batch &b, const uint8_t *tcA, const uint32_t *meta, uint32_t nent, uint32_t lpad,
-                           uint32_t s, const HitSink &sink, unsigned int *status, cudaStream_t st) {
+                           uint32_t s, const HitSink &sink, unsigned int *status, cudaStream_t st,
+                           uint32_t withhold_first) {
     // status[0]: wait gave up (bit 0); status[1]: the launch's work counter
     if (nent == 0 || b.nbases == 0) return cudaSuccess;
     if (lpad == 0 || lpad > kTcMaxLpad || (lpad & 7u)) return cudaErrorInvalidValue;
@@ -470,7 +488,7 @@ cudaError_t launch_scan_tc(const Batch &b, const uint8_t *tcA, const uint32_t *m
     cudaError_t e = cudaMemsetAsync(status + 1, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     k_scan_tc<<<grid, kTcThreads, kTcSmem, st>>>(b, tcA, meta, nent, lpad, s, n_rt, rt_per_item, n_rchunks, n_items,
-                                                 sink, status, status + 1);
+                                                 sink, status, status + 1, withhold_first);
     return cudaGetLastError();
 }
 

@@ -65,3 +65,17 @@ def test_tensor_rejects_long_queries():
     with pytest.raises(P.IfaError) as ei:
         gpu_scan([b"A" * 65], ref, np.array([400]), 2, brute_kernel=P.IFA_BRUTE_TENSOR)
     assert ei.value.status == P.IFA_ERR_INVALID_ARG
+
+
+def test_tensor_wait_timeout_is_reported_and_context_survives():
+    """Each tensor-core CTA withholds its first tile (a flag nothing else
+    sets): the MMA's bounded wait runs out, ifa_flush reports TIMEOUT, and
+    the same process then scans correctly again (the context is intact)."""
+    wl = synth.small_workload(seed=99, n_queries=4, lmin=20, lmax=40, n_contigs=4, cmin=500, cmax=3000)
+    qs = wl.queries + _queries(60, 20, 40, 8)
+    with pytest.raises(P.IfaError) as ei:
+        gpu_scan(qs, wl.ref, wl.contig_len, 3, brute_kernel=P.IFA_BRUTE_TENSOR, test_stall=1)
+    assert ei.value.status == P.IFA_ERR_TIMEOUT
+    got, over, dig, counts, _ = gpu_scan(qs, wl.ref, wl.contig_len, 3, brute_kernel=P.IFA_BRUTE_TENSOR)
+    exp = oracle.brute(qs, wl.ref, wl.contig_len, 3)
+    assert tuples(got) == tuples(exp)
