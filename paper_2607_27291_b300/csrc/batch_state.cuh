@@ -102,6 +102,15 @@ struct Request {
     uint64_t cap = 0;
     uint64_t bytes = 0;                        // charged to the budget
     unsigned long long final_counters[5] = {0, 0, 0, 0, 0};
+    // computed once when admitted: entries encoded with w words each, and
+    // for indexed requests each query's seed length, threshold and whether
+    // it is scanned exhaustively
+    bool prepared = false;
+    uint32_t w = 1;
+    std::vector<uint4> words;
+    std::vector<uint32_t> meta;
+    std::vector<uint32_t> plan_k, plan_minhits;
+    std::vector<uint8_t> plan_exhaustive;
 };
 
 // Continuous-batching serving over the reference store.

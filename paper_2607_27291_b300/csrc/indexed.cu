@@ -308,6 +308,14 @@ ifa_status indexed_plan(IndexedState &S, const std::vector<std::string> &qs, con
 ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
                           const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
                           uint32_t wmax, const ifa_config &cfg, cudaStream_t st, std::string &err) {
+    std::vector<uint32_t> qlen(qs.size());
+    for (size_t q = 0; q < qs.size(); q++) qlen[q] = static_cast<uint32_t>(qs[q].size());
+    return indexed_tables_len(S, qlen, qmeta, qwords, wmax, cfg, st, err);
+}
+
+ifa_status indexed_tables_len(IndexedState &S, const std::vector<uint32_t> &qlen,
+                              const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
+                              uint32_t wmax, const ifa_config &cfg, cudaStream_t st, std::string &err) {
     enum : size_t { kWords, kEmh, kEnts, kFirst, kKeys, kPv, kSums, kExWords, kExMeta, kExIds, kTab0 };
     S.free_tables();
     S.wmax = wmax;
@@ -321,7 +329,7 @@ ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
     auto put = [&](void *d, const void *h, size_t bytes) {
         if (e == cudaSuccess && bytes) ck(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st));
     };
-    const uint32_t nq = static_cast<uint32_t>(qs.size());
+    const uint32_t nq = static_cast<uint32_t>(qlen.size());
     if (!S.d_candidates) {
         ck(cudaMalloc(&S.d_candidates, sizeof(unsigned long long)));
         ck(cudaMemsetAsync(S.d_candidates, 0, sizeof(unsigned long long), st));
@@ -348,7 +356,7 @@ ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
             std::vector<uint32_t> ents, first{0};
             for (uint32_t q = 0; q < nq; q++) {
                 if (!S.plan_in[q] || S.plan_exhaustive[q] || S.plan_k[q] != k) continue;
-                const uint32_t L = static_cast<uint32_t>(qs[q].size());
+                const uint32_t L = qlen[q];
                 const uint32_t n_off = L >= k ? (L - k) / cfg.kmer_step + 1 : 0;
                 for (uint32_t t = 0; t < 2; t++) {
                     ents.push_back(2 * q + t);

@@ -98,6 +98,12 @@ ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
                           const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
                           uint32_t wmax, const ifa_config &cfg, cudaStream_t st, std::string &err);
 
+// The same from query lengths alone (the only property of the queries the
+// tables need besides their encoded words).
+ifa_status indexed_tables_len(IndexedState &S, const std::vector<uint32_t> &qlen,
+                              const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
+                              uint32_t wmax, const ifa_config &cfg, cudaStream_t st, std::string &err);
+
 // Device table construction (ktables.cu).
 uint64_t device_scan_sums_words(uint64_t n);
 cudaError_t device_scan(const uint32_t *in, uint32_t *out, uint64_t n, bool popc, bool exclusive,

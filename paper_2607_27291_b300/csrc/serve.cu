@@ -69,48 +69,85 @@ uint64_t request_bytes(const ServeState &S, const Request &r) {
     return b;
 }
 
-// Merged plan of the active requests.
+// Encoding and (indexed requests) per-query plan of one request, made once.
+ifa_status prepare_request(ifa_handle *h, Request &r) {
+    if (r.prepared) return IFA_OK;
+    uint32_t lmax = 1;
+    for (const auto &q : r.qs) lmax = std::max<uint32_t>(lmax, static_cast<uint32_t>(q.size()));
+    r.w = 1;
+    while (r.w * 32 < lmax) r.w <<= 1;
+    const size_t nq = r.qs.size();
+    r.words.assign(2 * nq * r.w, make_uint4(0, 0, 0, 0));
+    r.meta.assign(2 * nq, 0);
+    for (size_t q = 0; q < nq; q++)
+        for (uint32_t t = 0; t < 2; t++)
+            encode_entry(r.qs[q], t == 1, r.w, r.s, &r.words[(2 * q + t) * r.w], &r.meta[2 * q + t]);
+    if (r.mode == IFA_MODE_INDEXED) {
+        IndexedState plan;
+        const ifa_status st = indexed_plan_q(plan, r.qs, std::vector<uint32_t>(nq, r.s),
+                                             std::vector<uint8_t>(nq, 1), h->cfg, h->stream, h->err);
+        if (st != IFA_OK) return st;
+        r.plan_k = plan.plan_k;
+        r.plan_minhits = plan.plan_minhits;
+        r.plan_exhaustive = plan.plan_exhaustive;
+    }
+    r.prepared = true;
+    return IFA_OK;
+}
+
+// Merged plan of the active requests: their cached encodings and plans,
+// concatenated (entries padded to the widest request), then the merged
+// seed tables and the compact brute-force table.
 ifa_status build_serve_plan(ifa_handle *h) {
     ServeState &S = h->serve;
     free_serve_plan(S);
-    std::vector<std::string> aq;
-    std::vector<uint32_t> as, q2r, rfirst;
-    std::vector<uint8_t> cand;
-    uint32_t lmax = 1;
-    for (size_t slot = 0; slot < S.active.size(); slot++) {
-        const Request &r = S.reqs[S.active[slot]];
-        rfirst.push_back(static_cast<uint32_t>(aq.size()));
-        for (const auto &q : r.qs) {
-            aq.push_back(q);
-            as.push_back(r.s);
-            q2r.push_back(static_cast<uint32_t>(slot));
-            cand.push_back(r.mode == IFA_MODE_INDEXED ? 1 : 0);
-            lmax = std::max<uint32_t>(lmax, static_cast<uint32_t>(q.size()));
-        }
-    }
-    const uint32_t nq = static_cast<uint32_t>(aq.size());
+    std::vector<uint32_t> q2r, rfirst, qlen;
     uint32_t wmax = 1;
-    while (wmax * 32 < lmax) wmax <<= 1;
+    size_t nqs = 0;
+    for (uint32_t id : S.active) {
+        wmax = std::max(wmax, S.reqs[id].w);
+        nqs += S.reqs[id].qs.size();
+    }
+    const uint32_t nq = static_cast<uint32_t>(nqs);
     S.wmax = wmax;
     S.nq = nq;
-    std::vector<uint4> words(static_cast<size_t>(2) * nq * wmax);
-    std::vector<uint32_t> meta(2 * nq);
-    for (uint32_t q = 0; q < nq; q++)
-        for (uint32_t t = 0; t < 2; t++)
-            encode_entry(aq[q], t == 1, wmax, as[q], &words[static_cast<size_t>(2 * q + t) * wmax], &meta[2 * q + t]);
-    // which indexed queries are exhaustive, then the merged tables of the seeded ones
-    IndexedState plan_all;
-    ifa_status st = IFA_OK;
-    const bool any_cand = std::any_of(cand.begin(), cand.end(), [](uint8_t x) { return x != 0; });
+    std::vector<uint4> words(static_cast<size_t>(2) * nq * wmax, make_uint4(0, 0, 0, 0));
+    std::vector<uint32_t> meta(2 * static_cast<size_t>(nq));
     std::vector<uint8_t> seeded(nq, 0);
-    if (any_cand) {
-        st = indexed_plan_q(plan_all, aq, as, cand, h->cfg, h->stream, h->err);
-        if (st != IFA_OK) return st;
-        for (uint32_t q = 0; q < nq; q++) seeded[q] = cand[q] && !plan_all.plan_exhaustive[q];
+    IndexedState &M = S.merged;
+    M.plan_k.assign(nq, 0);
+    M.plan_minhits.assign(nq, 0);
+    M.plan_exhaustive.assign(nq, 0);
+    qlen.reserve(nq);
+    uint32_t q0 = 0;
+    for (size_t slot = 0; slot < S.active.size(); slot++) {
+        const Request &r = S.reqs[S.active[slot]];
+        rfirst.push_back(q0);
+        const uint32_t n = static_cast<uint32_t>(r.qs.size());
+        for (uint32_t i = 0; i < n; i++) {
+            const uint32_t q = q0 + i;
+            q2r.push_back(static_cast<uint32_t>(slot));
+            qlen.push_back(static_cast<uint32_t>(r.qs[i].size()));
+            for (uint32_t t = 0; t < 2; t++) {
+                const size_t src = (2 * static_cast<size_t>(i) + t) * r.w, dst = (2 * static_cast<size_t>(q) + t) * wmax;
+                std::copy(r.words.begin() + src, r.words.begin() + src + r.w, words.begin() + dst);
+                meta[2 * q + t] = r.meta[2 * i + t];
+            }
+            if (r.mode == IFA_MODE_INDEXED) {
+                M.plan_k[q] = r.plan_k[i];
+                M.plan_minhits[q] = r.plan_minhits[i];
+                M.plan_exhaustive[q] = r.plan_exhaustive[i];
+                seeded[q] = r.plan_exhaustive[i] ? 0 : 1;
+            }
+        }
+        q0 += n;
     }
+    ifa_status st = IFA_OK;
     if (std::any_of(seeded.begin(), seeded.end(), [](uint8_t x) { return x != 0; })) {
-        st = indexed_plan_q(S.merged, aq, as, seeded, h->cfg, h->stream, h->err);
-        if (st == IFA_OK) st = indexed_tables(S.merged, aq, meta, words, wmax, h->cfg, h->stream, h->err);
+        M.plan_in = seeded;
+        M.plan_valid = true;
+        M.plan_uniform = false;
+        st = indexed_tables_len(M, qlen, meta, words, wmax, h->cfg, h->stream, h->err);
         if (st != IFA_OK) return st;
     }
     // compact brute table (brute requests and exhaustive indexed queries)
@@ -315,6 +352,12 @@ ifa_status ifa_serve_step(ifa_handle *h, uint32_t *n_active, uint32_t *n_complet
         SCK(h, cudaMalloc(&r.d_ring, r.cap * sizeof(ifa_hit)));
         SCK(h, cudaMalloc(&r.d_counters, 5 * sizeof(unsigned long long)));
         SCK(h, cudaMemset(r.d_counters, 0, 5 * sizeof(unsigned long long)));
+        {
+            const double tp = now_s();
+            const ifa_status pst = prepare_request(h, r);
+            S.plan_s += now_s() - tp;
+            if (pst != IFA_OK) return pst;
+        }
         r.state = 1;
         r.t_admit = now_s() - S.t0;
         r.slices_done = 0;
