@@ -20,7 +20,7 @@ import numpy as np
 from .build import build as _build, LIB_PATH
 
 HIT_DTYPE = np.dtype([("query", "<u4"), ("contig", "<u4"), ("pos", "<u4"),
-                      ("strand", "u1"), ("mismatches", "u1"), ("reserved", "<u2")])
+                      ("strand", "u1"), ("mismatches", "u1"), ("clips", "<u2")])
 
 _lib = None
 
@@ -100,7 +100,7 @@ def sort_hits(h: np.ndarray) -> np.ndarray:
     """Sort by (query, contig, pos, strand, mismatches, clips)."""
     if h.size == 0:
         return h
-    order = np.lexsort((h["reserved"], h["mismatches"], h["strand"], h["pos"], h["contig"], h["query"]))
+    order = np.lexsort((h["clips"], h["mismatches"], h["strand"], h["pos"], h["contig"], h["query"]))
     return h[order]
 
 
@@ -146,7 +146,7 @@ def brute(queries: Sequence[bytes], ref: np.ndarray, contig_len, max_subs: int,
           contig_ids=None, threads: int = 1, clip_pct: int = 0) -> np.ndarray:
     """All (query, contig, pos, strand, mismatches) with Hamming <= max_subs;
     with clip_pct > 0 also the windows overhanging a contig end by up to
-    floor(clip_pct * L / 100) bases (clips in the `reserved` field)."""
+    floor(clip_pct * L / 100) bases (clips = left | right << 8)."""
     qcat, qoff, qlen = _pack_queries(queries)
     L = lib()
 

@@ -35,7 +35,7 @@
  *    bases after it.  Its overhanging bases are clips, not mismatches; it
  *    is a hit when clips <= C, at least one base is aligned and the
  *    mismatches of the aligned bases are <= maxSubs.  pos is the contig
- *    coordinate of the first aligned base and `reserved` holds the clips
+ *    coordinate of the first aligned base and `clips` holds the clips
  *    (left | right << 8).  With clip_pct = 0 windows never leave a contig,
  *    so a contig shorter than the query gives no hit;
  *  - palindromic queries report both strands.
@@ -47,7 +47,7 @@
 typedef struct {
     uint32_t query, contig, pos;
     uint8_t strand, mismatches;
-    uint16_t reserved;
+    uint16_t clips;
 } oracle_hit;
 
 /* ------------------------------------------------------------------ bases */
@@ -125,7 +125,7 @@ static void put_hit(oracle_hit *out, int64_t cap, int64_t n, uint32_t q, uint32_
         out[n].pos = (uint32_t)p;
         out[n].strand = t;
         out[n].mismatches = (uint8_t)(mm > 255 ? 255 : mm);
-        out[n].reserved = clips;
+        out[n].clips = clips;
     }
 }
 
@@ -539,7 +539,7 @@ void oracle_digest(const oracle_hit *h, int64_t n, uint64_t out[3])
     uint64_t sum = 0, xr = 0;
     for (int64_t i = 0; i < n; i++) {
         uint64_t a = ((uint64_t)h[i].query << 32) | h[i].contig;
-        uint64_t b = ((uint64_t)h[i].pos << 32) | ((uint64_t)h[i].reserved << 16) | ((uint64_t)h[i].strand << 8) |
+        uint64_t b = ((uint64_t)h[i].pos << 32) | ((uint64_t)h[i].clips << 16) | ((uint64_t)h[i].strand << 8) |
                      h[i].mismatches;
         uint64_t v = mix64(a ^ mix64(b));
         sum += v;
