@@ -63,7 +63,7 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
     using namespace brute;
     constexpr int NW = Stage<WMAX>::kWords;
     extern __shared__ uint4 smem4[];
-    __shared__ ifa_hit wbuf[kBWarps][32];
+    __shared__ __align__(16) ifa_hit wbuf[kBWarps][32];
     __shared__ uint4 stage[kBWarps][2][NW];
     __shared__ uint32_t s_nF, s_nM, s_item;
     const uint32_t lane = threadIdx.x & 31u;

@@ -59,7 +59,7 @@ __device__ __forceinline__ uint32_t clipped_mismatches(const Batch &b, const uin
 
 __global__ void __launch_bounds__(kClipThreads)
 k_clip_scan(Batch b, QueryTable qt, uint32_t nent, uint32_t clip_pct, uint32_t s, uint32_t cmax, HitSink sink) {
-    __shared__ ifa_hit wbuf[kClipThreads / 32][32];
+    __shared__ __align__(16) ifa_hit wbuf[kClipThreads / 32][32];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     WarpHits wh;
     wh.init(wbuf[warp]);

@@ -35,7 +35,8 @@ constexpr uint32_t kEventBlock = 128;
 //    query id, digest, one slot claim per flush.
 template <bool MULTI>
 struct WarpHitsT {
-    ifa_hit *buf;          // this warp's 32 staged hits (shared memory)
+    ifa_hit *buf;          // this warp's 32 staged hits (shared memory, 16-byte aligned:
+                           // hits and events move through it as uint4)
     uint32_t n;            // staged count (warp-uniform)
     unsigned long long dcount, dsum, dxor;  // this lane's digest terms
 

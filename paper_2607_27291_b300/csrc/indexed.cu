@@ -40,7 +40,7 @@ template <int WMAX>
 __global__ void __launch_bounds__(kSeedThreads)
 k_seed_scan(Batch b, QueryTable qt, KTablesArg tabs, const uint32_t *__restrict__ entry_minhits,
             uint32_t step, uint32_t s, HitSink sink, unsigned long long *candidates) {
-    __shared__ ifa_hit wbuf[kSeedWarps][32];
+    __shared__ __align__(16) ifa_hit wbuf[kSeedWarps][32];
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
     WarpHits wh;

@@ -52,7 +52,7 @@ k_scan_brute(Batch b, QueryTable qt, uint32_t e0, uint32_t e1, uint32_t s, uint3
              uint32_t lmax, HitSink sink) {
     constexpr int NW = Stage<WMAX>::kWords;
     extern __shared__ uint4 smem4[];
-    __shared__ ifa_hit wbuf[kScanWarps][32];
+    __shared__ __align__(16) ifa_hit wbuf[kScanWarps][32];
     __shared__ uint4 stage[kScanWarps][2][NW];
     __shared__ uint32_t s_nF, s_nM;
     const uint32_t nent = e1 - e0;

@@ -67,9 +67,12 @@ struct TcHead {
     float thr[kTcM];
     uint32_t len[kTcM];
     uint4 words[40];    // the builder's packed words of the current tile
-    ifa_hit stage[kTcEpiWarps][32];
+    uint32_t tile_clean[2];  // per B buffer: 1 when every window of the tile lies in one piece and in this batch
+    uint32_t discard;        // takes the per-call hit counts of the clean-tile path (counted per lane instead)
+    alignas(16) ifa_hit stage[kTcEpiWarps][32];  // read and written as uint4
 };
 static_assert(sizeof(TcHead) <= kTcHead, "tensor-core scan header");
+static_assert(offsetof(TcHead, stage) % 16 == 0, "hit staging is moved as uint4");
 // header + Q tile (128 x 256 B) + strings (2 x 4 x 4 (1024 + 64) B) + scratch
 static_assert(kTcHead + 128 * 256 + 2 * 4 * 4 * (1024 + 64) + kTcScratch <= kTcSmem, "tensor-core scan smem");
 
@@ -195,12 +198,14 @@ __device__ __forceinline__ bool crosses_piece(const Batch &b, uint64_t p, uint32
     return false;
 }
 
-// Hits of one flagged chunk: counts mine[j] (this lane's row, windows
-// p0 + 4 j) against thr, window checks, emission (all lanes of the warp).
-__device__ __noinline__ void emit_chunk(const Batch &b, const HitSink &sink, WarpHits &wh, const float *mine,
+// Hits of one flagged chunk with every check: 64 counts of this lane's row
+// (two f16 per word of mine2, even column low), windows p0 + 4 j; window
+// bounds, piece crossing and piece lookup per hit (all lanes of the warp).
+__device__ __noinline__ void emit_chunk(const Batch &b, const HitSink &sink, WarpHits &wh, const uint32_t *mine2,
                                         float thr, uint32_t L, uint32_t e, uint64_t p0, uint32_t lane) {
-    for (int j = 0; j < 32; j++) {
-        const float mt_j = mine[j];
+    for (int j = 0; j < 64; j++) {
+        const __half2 v2 = *reinterpret_cast<const __half2 *>(&mine2[j >> 1]);
+        const float mt_j = (j & 1) ? __high2float(v2) : __low2float(v2);
         const uint64_t p = p0 + 4u * static_cast<uint32_t>(j);
         bool hit = mt_j >= thr && p + L <= b.nbases && p + L >= static_cast<uint64_t>(b.halo) + 1;
         if (hit) hit = !crosses_piece(b, p, L);
@@ -353,6 +358,16 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                         *reinterpret_cast<uint4 *>(bb + ph * SB + 16u * q) =
                             make_uint4(oh[ph], oh[ph + 1], oh[ph + 2], oh[ph + 3]);
                 }
+                // whether every window of the tile stays in one piece and in the batch
+                // (no piece starts after its first base; halo and batch end clear)
+                {
+                    uint32_t starts = lane < nw ? H.words[lane].w : 0u;
+                    if (lane == 0) starts &= ~1u;
+                    if (32u + lane < nw) starts |= H.words[32u + lane].w;
+                    const bool inside = pt >= b.halo && pt + kTcTile + lpad + 3 <= b.nbases;
+                    const bool clean = inside && !__any_sync(0xffffffffu, starts != 0u);
+                    if (lane == 0) H.tile_clean[sbuf] = clean && b.npieces > 0 ? 1u : 0u;
+                }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 // (testing: withhold the CTA's first tile so that the MMA's wait runs out)
@@ -366,10 +381,15 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
             const uint32_t row = 32u * quarter + lane;
             const uint32_t e = mt * kTcM + row;
             const float thr = H.thr[row];
+            const __half2 thr2 = __float2half2_rn(thr < 60000.0f ? thr : 60000.0f);
             const uint32_t L = H.len[row];
+            uint32_t row_hits = 0;  // this lane's hits in clean tiles (counted once per item)
             for (uint32_t ti = 0; ti < ntiles && !*abort; ti++) {
                 const uint32_t g = gtile + ti;
                 const uint64_t pt = static_cast<uint64_t>(rt0 + ti) * kTcTile;
+                uint32_t clean = 0;
+                bool have_piece = false;  // tpc looked up (first flagged chunk of a clean tile)
+                DevPiece tpc{};
                 bool ok = true;
                 for (uint32_t ph = 0; ph < kTcPhases; ph++) {
                     const uint32_t u = 4u * g + ph, a = u & 1u, w = u >> 1;
@@ -378,8 +398,17 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    // 8 chunks of 32 columns, the next chunk's load in flight
-                    // while the current one is tested
+                    if (ph == 0) {
+                        // the builder's clean flag: the tile's full_b phase has completed
+                        // (acquire; returns at once), and the flag is not rewritten before
+                        // this phase's readout lets the MMAs of phases 2 and 3 run, after
+                        // which empty_b frees the buffer
+                        if (!mbar_wait(smem_u32(&H.full_b[g & 1u]), (g >> 1) & 1u, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        clean = H.tile_clean[g & 1u];
+                    }
                     // two packed loads of 64 columns, the second in flight while
                     // the first is tested
                     const uint32_t tbase = tmem + ((32u * quarter) << 16) + a * kTcN + half * (kTcN / 2);
@@ -392,17 +421,37 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                         if (c == 0) tc_ld64h(tbase + 64u, rb);
                         const float mx = max64h(cur);
                         if (__any_sync(0xffffffffu, mx >= thr)) {
-                            float *mine = scratch + ((warp - 2u) * 32u + lane) * 33u;
+                            uint32_t *mine2 = reinterpret_cast<uint32_t *>(scratch) + ((warp - 2u) * 32u + lane) * 33u;
+                            uint64_t bits = 0;
 #pragma unroll
-                            for (int hh = 0; hh < 2; hh++) {
-#pragma unroll
-                                for (int j = 0; j < 16; j++) {
-                                    const __half2 v2 = *reinterpret_cast<const __half2 *>(&cur[16 * hh + j]);
-                                    mine[2 * j] = __low2float(v2);
-                                    mine[2 * j + 1] = __high2float(v2);
+                            for (int j = 0; j < 32; j++) {
+                                mine2[j] = cur[j];
+                                const uint32_t m = __hge2_mask(*reinterpret_cast<const __half2 *>(&cur[j]), thr2);
+                                bits |= static_cast<uint64_t>((m & 1u) | ((m >> 15) & 2u)) << (2 * j);
+                            }
+                            const uint64_t p0 = pt + ph + 4u * (half * (kTcN / 2) + 64u * c);
+                            if (clean) {
+                                // every window of the tile is valid and in one piece: emit
+                                // the set bits only, the piece looked up once per tile
+                                if (!have_piece) {
+                                    tpc = b.pieces[find_piece(b.pieces, b.npieces, pt)];
+                                    have_piece = true;
                                 }
-                                emit_chunk(b, sink, wh, mine, thr, L, e,
-                                           pt + ph + 4u * (half * (kTcN / 2) + 64u * c + 32u * hh), lane);
+                                const uint32_t rounds = __reduce_max_sync(0xffffffffu, __popcll(bits));
+                                for (uint32_t r = 0; r < rounds; r++) {
+                                    const bool has = bits != 0;
+                                    const uint32_t col = has ? static_cast<uint32_t>(__ffsll(bits) - 1) : 0u;
+                                    bits &= bits - 1;
+                                    const __half2 v2 = *reinterpret_cast<const __half2 *>(&mine2[col >> 1]);
+                                    const float mt_c = (col & 1u) ? __high2float(v2) : __low2float(v2);
+                                    const uint32_t pos =
+                                        static_cast<uint32_t>(tpc.contig_off + (p0 + 4u * col - tpc.start));
+                                    wh.emit(sink, lane, has, e >> 1, tpc.contig, pos, e & 1u,
+                                            L - static_cast<uint32_t>(mt_c), &H.discard);
+                                    row_hits += has ? 1u : 0u;
+                                }
+                            } else {
+                                emit_chunk(b, sink, wh, mine2, thr, L, e, p0, lane);
                             }
                         }
                         if (c == 0) tc_wait_ld_regs(rb);
@@ -413,6 +462,7 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                 }
                 if (!ok) break;
             }
+            if (row_hits && e < nent) atomicAdd(&sink.qcount[e >> 1], static_cast<unsigned long long>(row_hits));
         }
         gtile += ntiles;
         __syncthreads();

@@ -79,3 +79,42 @@ def test_tensor_wait_timeout_is_reported_and_context_survives():
     got, over, dig, counts, _ = gpu_scan(qs, wl.ref, wl.contig_len, 3, brute_kernel=P.IFA_BRUTE_TENSOR)
     exp = oracle.brute(qs, wl.ref, wl.contig_len, 3)
     assert tuples(got) == tuples(exp)
+
+
+@pytest.mark.parametrize("s,seg", [(5, 1 << 20), (6, 70_000)])
+def test_tensor_dense_hits_in_long_contigs(s, seg):
+    """Contigs much longer than a 1024-window tile, so most tiles lie inside
+    one piece, and short queries at a high maxSubs, so that many windows of
+    such tiles are hits (the per-tile fast path), with segments cutting the
+    contigs (halo tiles take the checked path)."""
+    wl = synth.small_workload(seed=150 + s, n_queries=4, lmin=10, lmax=30, n_contigs=7, cmin=15_000,
+                              cmax=45_000, plant_ks=[0, 1, 2, 3] * 2)
+    qs = wl.queries + _queries(70, 10, 30, 2000 + s, n_frac=0.02)
+    got, over, dig, counts, _ = gpu_scan(qs, wl.ref, wl.contig_len, s, seg_bytes=seg,
+                                         brute_kernel=P.IFA_BRUTE_TENSOR, hit_capacity=1 << 23)
+    exp = oracle.brute(qs, wl.ref, wl.contig_len, s)
+    assert not over
+    assert exp.size > 100_000
+    assert tuples(got) == tuples(exp)
+    assert dig == oracle.digest(exp)
+    assert counts.tolist() == np.bincount(exp["query"], minlength=len(qs)).tolist()
+
+
+def test_tensor_pieces_starting_on_tile_boundaries():
+    """Contig boundaries exactly at multiples of the 1024-window tile (a
+    tile whose first window is a piece's first base is still one piece) and
+    one base either side of them."""
+    rng = np.random.default_rng(160)
+    lens = np.array([1024 * 9, 1024 * 3, 1024 * 5 + 1, 1024 * 4 - 2, 1024 * 6, 1, 1024 * 2 + 1023, 1024 * 8],
+                    np.int64)
+    ref = rng.choice(np.frombuffer(b"ACGT", np.uint8), int(lens.sum()))
+    qs = _queries(90, 8, 24, 161, n_frac=0.0)
+    for i, q in enumerate(qs[:40]):
+        # copies of the queries across and beside the boundaries
+        a = int(np.cumsum(lens)[i % 7]) - len(q) // 2 + (i % 3) - 1
+        ref[a:a + len(q)] = np.frombuffer(q, np.uint8)
+    _, _, dig, counts, _ = gpu_scan(qs, ref, lens, 5, count_only=1, brute_kernel=P.IFA_BRUTE_TENSOR)
+    exp = oracle.brute(qs, ref, lens, 5)
+    assert exp.size > 50_000
+    assert dig == oracle.digest(exp)
+    assert counts.tolist() == np.bincount(exp["query"], minlength=len(qs)).tolist()
