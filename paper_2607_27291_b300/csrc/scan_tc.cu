@@ -68,6 +68,7 @@ struct TcHead {
     uint32_t len[kTcM];
     uint4 words[40];    // the builder's packed words of the current tile
     uint32_t tile_clean[2];  // per B buffer: 1 when every window of the tile lies in one piece and in this batch
+    uint32_t tile_piece[2];  // per B buffer: that piece (valid when clean)
     uint32_t discard;        // takes the per-call hit counts of the clean-tile path (counted per lane instead)
     alignas(16) ifa_hit stage[kTcEpiWarps][32];  // read and written as uint4
 };
@@ -326,6 +327,11 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
             const uint32_t nq4 = (kTcTile + lpad) / 4;   // chunks per string
             const uint64_t nwords = (b.nbases + 31) / 32;
             const uint32_t nw = (kTcTile + lpad + 31) / 32 + 1;  // words per tile (<= 35)
+            // the piece holding the current tile's first window: one search per
+            // item, then advanced tile by tile (the item's tiles are consecutive)
+            uint32_t pi = lane == 0 && ntiles && b.npieces
+                              ? find_piece(b.pieces, b.npieces, static_cast<uint64_t>(rt0) * kTcTile)
+                              : 0u;
             for (uint32_t ti = 0; ti < ntiles && !*abort; ti++) {
                 const uint32_t g = gtile + ti, sbuf = g & 1u, v = g >> 1;
                 const uint64_t pt = static_cast<uint64_t>(rt0 + ti) * kTcTile;
@@ -334,6 +340,8 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                 const uint4 w0 = (pt >> 5) + lane < nwords ? __ldg(b.words + (pt >> 5) + lane) : nword;
                 const uint4 w1 = 32u + lane < nw && (pt >> 5) + 32u + lane < nwords
                                      ? __ldg(b.words + (pt >> 5) + 32u + lane) : nword;
+                if (lane == 0)
+                    while (pi + 1 < b.npieces && b.pieces[pi + 1].start <= pt) pi++;
                 if (v >= 1 && !mbar_wait(smem_u32(&H.empty_b[sbuf]), (v - 1) & 1u, abort)) break;
                 H.words[lane] = w0;
                 if (32u + lane < nw) H.words[32u + lane] = w1;
@@ -366,7 +374,10 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                     if (32u + lane < nw) starts |= H.words[32u + lane].w;
                     const bool inside = pt >= b.halo && pt + kTcTile + lpad + 3 <= b.nbases;
                     const bool clean = inside && !__any_sync(0xffffffffu, starts != 0u);
-                    if (lane == 0) H.tile_clean[sbuf] = clean && b.npieces > 0 ? 1u : 0u;
+                    if (lane == 0) {
+                        H.tile_clean[sbuf] = clean && b.npieces > 0 ? 1u : 0u;
+                        H.tile_piece[sbuf] = pi;
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
@@ -388,7 +399,8 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                 const uint32_t g = gtile + ti;
                 const uint64_t pt = static_cast<uint64_t>(rt0 + ti) * kTcTile;
                 uint32_t clean = 0;
-                bool have_piece = false;  // tpc looked up (first flagged chunk of a clean tile)
+                uint32_t tpi = 0;         // the tile's piece (builder's record)
+                bool have_piece = false;  // tpc loaded (first flagged chunk of a clean tile)
                 DevPiece tpc{};
                 bool ok = true;
                 for (uint32_t ph = 0; ph < kTcPhases; ph++) {
@@ -408,6 +420,7 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                             break;
                         }
                         clean = H.tile_clean[g & 1u];
+                        tpi = H.tile_piece[g & 1u];
                     }
                     // two packed loads of 64 columns, the second in flight while
                     // the first is tested
@@ -434,7 +447,7 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                                 // every window of the tile is valid and in one piece: emit
                                 // the set bits only, the piece looked up once per tile
                                 if (!have_piece) {
-                                    tpc = b.pieces[find_piece(b.pieces, b.npieces, pt)];
+                                    tpc = b.pieces[tpi];
                                     have_piece = true;
                                 }
                                 const uint32_t rounds = __reduce_max_sync(0xffffffffu, __popcll(bits));
