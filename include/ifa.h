@@ -370,10 +370,12 @@ ifa_status ifa_serve_stop(ifa_handle *h);
  *
  * queries/qlens: host ASCII, as for ifa_load_queries.  ref_device: len
  * ASCII bytes in device memory.  pieces: host, as for ifa_push_segment.
- * hits_device: room for hit_capacity ifa_hit (device).  counters_device:
- * 5 uint64 on the device, set to {hits claimed (may exceed hit_capacity),
+ * hits_device: room for hit_capacity ifa_hit (device, 16-byte aligned:
+ * hits are stored 16 bytes at a time).  counters_device: 5 uint64 on the
+ * device (8-byte aligned), set to {hits claimed (may exceed hit_capacity),
  * overflow flag, digest count, digest sum, digest xor}.
- * per_query_counts_device: nq uint64 on the device, or NULL.  stream: the
+ * per_query_counts_device: nq uint64 on the device (8-byte aligned), or
+ * NULL.  A misaligned buffer returns IFA_ERR_INVALID_ARG.  stream: the
  * cudaStream_t to enqueue on (NULL = legacy default stream).  Results are
  * in the caller's buffers once the stream has passed this call's work; hit
  * order is unspecified.

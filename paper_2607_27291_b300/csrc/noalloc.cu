@@ -95,6 +95,12 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
         return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: 1 to 32768 contigs per call");
     if (!ref_device || !pieces || !hits_device || !counters_device || hit_capacity == 0)
         return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: NULL buffer or zero hit capacity");
+    // hits are written 16 bytes at a time and the counters take 64-bit atomics
+    if (reinterpret_cast<uintptr_t>(hits_device) % 16 != 0 || reinterpret_cast<uintptr_t>(counters_device) % 8 != 0 ||
+        reinterpret_cast<uintptr_t>(per_query_counts_device) % 8 != 0)
+        return na_fail(IFA_ERR_INVALID_ARG,
+                       "ifa_scan_brute_noalloc: hits_device must be 16-byte aligned, counters_device and "
+                       "per_query_counts_device 8-byte aligned");
     uint64_t at = 0;
     for (uint32_t i = 0; i < n_pieces; i++) {
         const ifa_piece &p = pieces[i];

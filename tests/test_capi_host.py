@@ -124,3 +124,18 @@ def test_create_without_gpu_fails_cleanly():
     with pytest.raises(P.IfaError) as ei:
         P.ifa_create()
     assert ei.value.status == P.IFA_ERR_CUDA
+
+
+def test_noalloc_rejects_misaligned_buffers_before_device():
+    """The allocation-free scan stores hits 16 bytes at a time and updates
+    its counters with 64-bit atomics, so misaligned caller buffers are
+    refused on the host.  The pointers below are never dereferenced: the
+    check comes before any CUDA call, so this runs without a GPU."""
+    pieces = [(0, 0, 0, 64, True)]
+    q = [b"ACGTACGTAC"]
+    cases = [(0x10004, 0x20000, 0), (0x10008, 0x20000, 0), (0x10000, 0x20004, 0), (0x10000, 0x20000, 0x30004)]
+    for hits, counters, per_query in cases:
+        with pytest.raises(P.IfaError) as ei:
+            P.ifa_scan_brute_noalloc(0, q, 0x40000, 64, pieces, 1, hits, 16, counters, per_query)
+        assert ei.value.status == P.IFA_ERR_INVALID_ARG
+        assert "aligned" in str(ei.value)
