@@ -43,7 +43,7 @@ POPC_PER_CLK_SM = 16  # 32-bit population count issue rate per SM per clock (CUD
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--total", type=float, default=4e9, help="reference bases (default 4 Gbp)")
@@ -128,10 +128,15 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+            return
+        # the timed region starts once the sampler has written its first row
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.p.poll() is None and os.path.getsize(self.f.name) == 0:
+            time.sleep(0.01)
 
     def stop(self):
         if self.p is None:
