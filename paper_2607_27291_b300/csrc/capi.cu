@@ -244,8 +244,8 @@ double mean_window_hit_rate(const ifa_handle *h) {
 }
 
 // Above this mean hit rate the popcount kernel's per-hit path wins
-// (256 Mbp, 128 and 2048 queries: tensor cores 1.2-1.4x faster at a mean
-// rate of 0.7-0.8e-4, 0.6-0.7x at 1.3-2.7e-3).
+// (256 Mbp, 2048 queries: tensor cores 1.35-1.6x faster at a mean rate of
+// 0.7-0.8e-4, 0.6x at 1.3e-3).
 constexpr double kTcAutoMaxHitRate = 2e-4;
 
 bool use_tensor_cores(const ifa_handle *h) {

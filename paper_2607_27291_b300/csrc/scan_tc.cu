@@ -422,16 +422,21 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                         clean = H.tile_clean[g & 1u];
                         tpi = H.tile_piece[g & 1u];
                     }
-                    // two packed loads of 64 columns, the second in flight while
-                    // the first is tested
+                    // the warp's 128 columns in two packed loads; the accumulator is
+                    // handed back to the MMAs as soon as they are in registers, so
+                    // the tests and hits below overlap the next MMAs into it
                     const uint32_t tbase = tmem + ((32u * quarter) << 16) + a * kTcN + half * (kTcN / 2);
                     uint32_t ra[32], rb[32];
                     tc_ld64h(tbase, ra);
+                    tc_ld64h(tbase + 64u, rb);
                     tc_wait_ld_regs(ra);
+                    tc_wait_ld_regs(rb);
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&H.empty_acc[a]));
 #pragma unroll
                     for (uint32_t c = 0; c < 2; c++) {
                         uint32_t *cur = c ? rb : ra;
-                        if (c == 0) tc_ld64h(tbase + 64u, rb);
                         const float mx = max64h(cur);
                         if (__any_sync(0xffffffffu, mx >= thr)) {
                             uint32_t *mine2 = reinterpret_cast<uint32_t *>(scratch) + ((warp - 2u) * 32u + lane) * 33u;
@@ -467,11 +472,7 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                                 emit_chunk(b, sink, wh, mine2, thr, L, e, p0, lane);
                             }
                         }
-                        if (c == 0) tc_wait_ld_regs(rb);
                     }
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&H.empty_acc[a]));
                 }
                 if (!ok) break;
             }
