@@ -380,6 +380,9 @@ ifa_status ifa_serve_stop(ifa_handle *h);
  * in the caller's buffers once the stream has passed this call's work; hit
  * order is unspecified.
  *
+ * The work is enqueued on `device` (a device ordinal); the calling
+ * thread's current device is the same after the call as before it.
+ *
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call on a device shares the one scratch array and leaves its

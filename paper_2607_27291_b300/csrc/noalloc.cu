@@ -113,9 +113,22 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
     }
     if (at != len) return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: pieces must cover the reference");
 
-    cudaError_t e = cudaSetDevice(device);
-    if (e != cudaSuccess) return na_fail(IFA_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     if (device < 0 || device >= 64) return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: device ordinal");
+    // work on `device`; the calling thread's current device is put back on return
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return na_fail(IFA_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (prev != device) {
+        e = cudaSetDevice(device);
+        if (e != cudaSuccess) return na_fail(IFA_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    }
+    struct RestoreDevice {
+        int dev;
+        bool on;
+        ~RestoreDevice() {
+            if (on) cudaSetDevice(dev);
+        }
+    } restore{prev, prev != device};
 
     // ---- set-up, once per device, with that device current
     unsigned char *base = nullptr;
