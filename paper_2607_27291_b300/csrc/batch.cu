@@ -196,7 +196,8 @@ ifa_status sync_pieces(ifa_handle *h) {
     B.d_pieces = nullptr;
     BCK(h, cudaMalloc(&B.d_pieces, std::max<size_t>(1, B.pieces.size()) * sizeof(DevPiece)));
     if (!B.pieces.empty())
-        BCK(h, cudaMemcpy(B.d_pieces, B.pieces.data(), B.pieces.size() * sizeof(DevPiece), cudaMemcpyHostToDevice));
+        BCK(h, cudaMemcpyAsync(B.d_pieces, B.pieces.data(), B.pieces.size() * sizeof(DevPiece), cudaMemcpyHostToDevice,
+                               h->stream));
     B.d_pieces_n = static_cast<uint32_t>(B.pieces.size());
     B.pieces_dirty = false;
     return IFA_OK;
@@ -358,15 +359,19 @@ ifa_status build_plan(ifa_handle *h) {
     uint32_t *d_c0 = plan_alloc<uint32_t>(h, nch, e), *d_c1 = plan_alloc<uint32_t>(h, nch, e);
     uint32_t *d_cl = plan_alloc<uint32_t>(h, nch, e), *d_ch = plan_alloc<uint32_t>(h, nch, e);
     if (e == cudaSuccess) {
-        e = cudaMemcpy(d_bw, bw.data(), bw.size() * sizeof(uint4), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(d_bm, bm.data(), nbe * sizeof(uint32_t), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && !ids.empty()) e = cudaMemcpy(d_bids, ids.data(), ids.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        // on the compute stream, ahead of the kernels that read them (pageable
+        // sources are staged before each call returns)
+        const cudaMemcpyKind hd = cudaMemcpyHostToDevice;
+        e = cudaMemcpyAsync(d_bw, bw.data(), bw.size() * sizeof(uint4), hd, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_bm, bm.data(), nbe * sizeof(uint32_t), hd, h->stream);
+        if (e == cudaSuccess && !ids.empty())
+            e = cudaMemcpyAsync(d_bids, ids.data(), ids.size() * sizeof(uint32_t), hd, h->stream);
         if (e == cudaSuccess && !B.bchunk_e0.empty()) {
             const size_t nb = B.bchunk_e0.size() * sizeof(uint32_t);
-            e = cudaMemcpy(d_c0, B.bchunk_e0.data(), nb, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemcpy(d_c1, B.bchunk_e1.data(), nb, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemcpy(d_cl, B.bchunk_lmin.data(), nb, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemcpy(d_ch, B.bchunk_lmax.data(), nb, cudaMemcpyHostToDevice);
+            e = cudaMemcpyAsync(d_c0, B.bchunk_e0.data(), nb, hd, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_c1, B.bchunk_e1.data(), nb, hd, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_cl, B.bchunk_lmin.data(), nb, hd, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_ch, B.bchunk_lmax.data(), nb, hd, h->stream);
         }
     }
     if (e != cudaSuccess) return bfail(h, IFA_ERR_CUDA, std::string("batch plan: ") + cudaGetErrorString(e));
@@ -497,7 +502,7 @@ ifa_status calibrate(ifa_handle *h) {
         if (st == IFA_OK) st = indexed_tables(one, h->qs, h->qmeta_host, h->qwords_host, h->wmax, h->cfg, h->stream, h->err);
         if (st == IFA_OK && one.targ.n) {
             cudaMalloc(&one.d_candidates, sizeof(unsigned long long));
-            cudaMemset(one.d_candidates, 0, sizeof(unsigned long long));
+            cudaMemsetAsync(one.d_candidates, 0, sizeof(unsigned long long), h->stream);
             for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
                 cudaEventRecord(e0, h->stream);
                 e = launch_seed_scan(b, qt, one.targ, one.d_entry_minhits, h->cfg.kmer_step, kSPerEntry, sink,
@@ -520,7 +525,7 @@ ifa_status calibrate(ifa_handle *h) {
             if (st == IFA_OK) st = indexed_tables(dense, h->qs, h->qmeta_host, h->qwords_host, h->wmax, c8, h->stream, h->err);
             if (st == IFA_OK && dense.targ.n) {
                 cudaMalloc(&dense.d_candidates, sizeof(unsigned long long));
-                cudaMemset(dense.d_candidates, 0, sizeof(unsigned long long));
+                cudaMemsetAsync(dense.d_candidates, 0, sizeof(unsigned long long), h->stream);
                 cudaEventRecord(e0, h->stream);
                 e = launch_seed_scan(b, qt, dense.targ, dense.d_entry_minhits, 1, kSPerEntry, sink,
                                      dense.d_candidates, h->stream);
@@ -608,7 +613,9 @@ ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, con
         uint4 *nw = nullptr;
         BCK(h, cudaMalloc(&nw, cap * sizeof(uint4)));
         if (B.d_words) {
-            cudaError_t e = cudaMemcpy(nw, B.d_words, (B.nbases / 32) * sizeof(uint4), cudaMemcpyDeviceToDevice);
+            cudaError_t e = cudaMemcpyAsync(nw, B.d_words, (B.nbases / 32) * sizeof(uint4), cudaMemcpyDeviceToDevice,
+                                            h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // before the old store is freed
             if (e != cudaSuccess) {
                 cudaFree(nw);
                 return bfail(h, IFA_ERR_CUDA, std::string("ifa_ref_append: ") + cudaGetErrorString(e));
@@ -645,7 +652,8 @@ ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, con
     if (!fresh.empty()) {
         DevPiece *tmp = nullptr;
         BCK(h, cudaMalloc(&tmp, fresh.size() * sizeof(DevPiece)));
-        cudaError_t e = cudaMemcpy(tmp, fresh.data(), fresh.size() * sizeof(DevPiece), cudaMemcpyHostToDevice);
+        cudaError_t e =
+            cudaMemcpyAsync(tmp, fresh.data(), fresh.size() * sizeof(DevPiece), cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) e = launch_mark_pieces(tmp, static_cast<uint32_t>(fresh.size()), B.d_words, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         cudaFree(tmp);

@@ -90,8 +90,8 @@ ifa_status upload_queries(ifa_handle *h) {
     h->d_qmeta = nullptr;
     CK(h, cudaMalloc(&h->d_qwords, words.size() * sizeof(uint4)));
     CK(h, cudaMalloc(&h->d_qmeta, ne * sizeof(uint32_t)));
-    CK(h, cudaMemcpy(h->d_qwords, words.data(), words.size() * sizeof(uint4), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->d_qmeta, h->qmeta_host.data(), ne * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpyAsync(h->d_qwords, words.data(), words.size() * sizeof(uint4), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->d_qmeta, h->qmeta_host.data(), ne * sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream));
     // entry chunks that fit the scan kernel's shared-memory budget
     uint32_t cap = scan_brute_chunk_entries(w) & ~1u;
     if (cap < 2) cap = 2;
@@ -114,7 +114,7 @@ ifa_status upload_queries(ifa_handle *h) {
         h->tc_lpad = tc_lpad(h->lmax);
         tc_operand(h->qs, h->tc_lpad, op);
         CK(h, cudaMalloc(&h->d_tcA, op.size()));
-        CK(h, cudaMemcpy(h->d_tcA, op.data(), op.size(), cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpyAsync(h->d_tcA, op.data(), op.size(), cudaMemcpyHostToDevice, h->stream));
     }
     h->qdirty = false;
     h->idx.invalidate();
@@ -337,9 +337,9 @@ ifa_status ifa_create(const ifa_config *cfg, ifa_handle **out) {
     CKC(cudaMalloc(&h->d_head, sizeof(unsigned long long)));
     CKC(cudaMalloc(&h->d_overflow, sizeof(uint32_t)));
     CKC(cudaMalloc(&h->d_digest, 3 * sizeof(unsigned long long)));
-    CKC(cudaMemset(h->d_head, 0, sizeof(unsigned long long)));
-    CKC(cudaMemset(h->d_overflow, 0, sizeof(uint32_t)));
-    CKC(cudaMemset(h->d_digest, 0, 3 * sizeof(unsigned long long)));
+    CKC(cudaMemsetAsync(h->d_head, 0, sizeof(unsigned long long), h->stream));
+    CKC(cudaMemsetAsync(h->d_overflow, 0, sizeof(uint32_t), h->stream));
+    CKC(cudaMemsetAsync(h->d_digest, 0, 3 * sizeof(unsigned long long), h->stream));
 #undef CKC
     ifa_status st = ensure_pieces(h, 0, 1024);
     if (st == IFA_OK) st = ensure_pieces(h, 1, 1024);
@@ -417,7 +417,7 @@ ifa_status ifa_load_queries(ifa_handle *h, const uint8_t *const *seqs, const uin
     cudaFree(h->d_qcount);
     h->d_qcount = nullptr;
     CK(h, cudaMalloc(&h->d_qcount, std::max<size_t>(1, h->qs.size()) * sizeof(unsigned long long)));
-    CK(h, cudaMemset(h->d_qcount, 0, std::max<size_t>(1, h->qs.size()) * sizeof(unsigned long long)));
+    CK(h, cudaMemsetAsync(h->d_qcount, 0, std::max<size_t>(1, h->qs.size()) * sizeof(unsigned long long), h->stream));
     return IFA_OK;
 }
 
@@ -675,10 +675,13 @@ ifa_status ifa_reset_results(ifa_handle *h) {
     CK(h, cudaSetDevice(h->dev));
     ifa_status st = sync_all(h);
     if (st != IFA_OK) return st;
-    CK(h, cudaMemset(h->d_head, 0, sizeof(unsigned long long)));
-    CK(h, cudaMemset(h->d_overflow, 0, sizeof(uint32_t)));
-    CK(h, cudaMemset(h->d_digest, 0, 3 * sizeof(unsigned long long)));
-    if (h->d_qcount) CK(h, cudaMemset(h->d_qcount, 0, std::max<size_t>(1, h->qs.size()) * sizeof(unsigned long long)));
+    // on the compute stream, so the next pass's kernels see the zeros
+    CK(h, cudaMemsetAsync(h->d_head, 0, sizeof(unsigned long long), h->stream));
+    CK(h, cudaMemsetAsync(h->d_overflow, 0, sizeof(uint32_t), h->stream));
+    CK(h, cudaMemsetAsync(h->d_digest, 0, 3 * sizeof(unsigned long long), h->stream));
+    if (h->d_qcount)
+        CK(h, cudaMemsetAsync(h->d_qcount, 0, std::max<size_t>(1, h->qs.size()) * sizeof(unsigned long long),
+                              h->stream));
     h->drained = 0;
     h->open = false;
     h->halo_len = 0;
@@ -687,9 +690,9 @@ ifa_status ifa_reset_results(ifa_handle *h) {
     st = prof_collect(h);
     if (st != IFA_OK) return st;
     h->stats = ifa_stats{};
-    if (h->idx.d_candidates) CK(h, cudaMemset(h->idx.d_candidates, 0, sizeof(unsigned long long)));
-    if (h->batch.d_cand) CK(h, cudaMemset(h->batch.d_cand, 0, sizeof(unsigned long long)));
-    if (h->d_tc_status) CK(h, cudaMemset(h->d_tc_status, 0, 2 * sizeof(unsigned int)));
+    if (h->idx.d_candidates) CK(h, cudaMemsetAsync(h->idx.d_candidates, 0, sizeof(unsigned long long), h->stream));
+    if (h->batch.d_cand) CK(h, cudaMemsetAsync(h->batch.d_cand, 0, sizeof(unsigned long long), h->stream));
+    if (h->d_tc_status) CK(h, cudaMemsetAsync(h->d_tc_status, 0, 2 * sizeof(unsigned int), h->stream));
     h->tc_used = false;
     return IFA_OK;
 }

@@ -298,7 +298,7 @@ ifa_status ifa_serve_start(ifa_handle *h, uint32_t n_slices, uint64_t hbm_budget
     S.scan_s = 0;
     SCK(h, cudaMalloc(&S.d_queue, sizeof(unsigned int)));
     SCK(h, cudaMalloc(&S.d_cand, sizeof(unsigned long long)));
-    SCK(h, cudaMemset(S.d_cand, 0, sizeof(unsigned long long)));
+    SCK(h, cudaMemsetAsync(S.d_cand, 0, sizeof(unsigned long long), h->stream));
     // the store's piece table on the device
     BatchState &B = h->batch;
     if (B.pieces_dirty) {
@@ -306,7 +306,8 @@ ifa_status ifa_serve_start(ifa_handle *h, uint32_t n_slices, uint64_t hbm_budget
         B.d_pieces = nullptr;
         SCK(h, cudaMalloc(&B.d_pieces, std::max<size_t>(1, B.pieces.size()) * sizeof(DevPiece)));
         if (!B.pieces.empty())
-            SCK(h, cudaMemcpy(B.d_pieces, B.pieces.data(), B.pieces.size() * sizeof(DevPiece), cudaMemcpyHostToDevice));
+            SCK(h, cudaMemcpyAsync(B.d_pieces, B.pieces.data(), B.pieces.size() * sizeof(DevPiece),
+                                   cudaMemcpyHostToDevice, h->stream));
         B.d_pieces_n = static_cast<uint32_t>(B.pieces.size());
         B.pieces_dirty = false;
     }
@@ -351,7 +352,7 @@ ifa_status ifa_serve_step(ifa_handle *h, uint32_t *n_active, uint32_t *n_complet
         if (S.used + r.bytes > S.budget && !S.active.empty()) break;
         SCK(h, cudaMalloc(&r.d_ring, r.cap * sizeof(ifa_hit)));
         SCK(h, cudaMalloc(&r.d_counters, 5 * sizeof(unsigned long long)));
-        SCK(h, cudaMemset(r.d_counters, 0, 5 * sizeof(unsigned long long)));
+        SCK(h, cudaMemsetAsync(r.d_counters, 0, 5 * sizeof(unsigned long long), h->stream));
         {
             const double tp = now_s();
             const ifa_status pst = prepare_request(h, r);
