@@ -247,7 +247,7 @@ ifa_status ifa_minhits(int32_t device, const uint32_t *L, const uint32_t *subs, 
 
 /* ---- Many query sets against a device-resident reference ------------
  *
- * Batching and serving (SURVEY S9; the paper's mode choice by query count,
+ * Batching and serving (the paper's mode choice by query count,
  * Discussion, generalised): the reference is packed once into a store on
  * the device, any number of query sets -- each with its own maxSubs and
  * mode -- are registered, and one call scans all of them.  Hits, digest
