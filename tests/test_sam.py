@@ -102,3 +102,50 @@ def test_clipped_records_match_hand_written():
         a[i] = (q, c, p, t, m, cl)
     got = P.ifa_sam_records(a, _queries(), np.zeros(2, np.uint8))
     assert got.decode() == "".join(r + "\n" for r in GOLDEN["clipped_records"])
+
+
+def _random_case(rng):
+    nq = int(rng.integers(1, 8))
+    alphabet = np.frombuffer(b"ACGTacgtNRY-", np.uint8)
+    queries = [bytes(rng.choice(alphabet, int(rng.integers(1, 61))).astype(np.uint8)) for _ in range(nq)]
+    n = int(rng.integers(0, 120))
+    hits = np.zeros(n, dtype=P.HIT_DTYPE)
+    for i in range(n):
+        q = int(rng.integers(0, nq))
+        L = len(queries[q])
+        left = right = 0
+        if L > 1 and rng.random() < 0.3:
+            budget = int(rng.integers(1, L))          # clips < L: one base stays aligned
+            left = int(rng.integers(0, budget + 1))
+            right = budget - left
+        hits[i] = (q, int(rng.integers(0, 6)), int(rng.integers(0, 5000)), int(rng.integers(0, 2)),
+                   int(rng.integers(0, L + 1)), left | (right << 8))
+    return queries, hits
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_library_matches_oracle_on_random_hits(seed):
+    """Random query sets (IUPAC bytes, lower case, lengths 1..60) and random
+    hits with clips, cut into calls at contig boundaries (reference order)
+    and formatted by the library with the primary flags carried across the
+    calls: the text equals one oracle call, with and without long names
+    (which force the output buffer to grow)."""
+    rng = np.random.default_rng(1000 + seed)
+    queries, hits = _random_case(rng)
+    tuples = [tuple(int(x) for x in (h["query"], h["contig"], h["pos"], h["strand"], h["mismatches"], h["clips"]))
+              for h in hits]
+    named = seed % 2 == 1
+    qnames = ["read_%d_" % i + "x" * int(rng.integers(0, 300)) for i in range(len(queries))] if named else None
+    cnames = ["contig_%d_" % c + "y" * int(rng.integers(0, 200)) for c in range(6)] if named else None
+    seen_o = [False] * len(queries)
+    expect = osam.sam_records(tuples, queries, seen_o, query_names=qnames,
+                              contig_names=dict(enumerate(cnames)) if named else None)
+    cuts = sorted(set(int(c) for c in rng.integers(0, 7, size=int(rng.integers(0, 4)))))
+    bounds = [0] + cuts + [7]
+    seen = np.zeros(len(queries), dtype=np.uint8)
+    got = b""
+    for lo, hi in zip(bounds[:-1], bounds[1:]):
+        part = hits[(hits["contig"] >= lo) & (hits["contig"] < hi)].copy()
+        got += P.ifa_sam_records(part, queries, seen, query_names=qnames, contig_names=cnames)
+    assert got.decode() == expect
+    assert seen.astype(bool).tolist() == seen_o
