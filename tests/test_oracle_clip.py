@@ -125,3 +125,51 @@ def test_digest_sees_the_clips():
     d0 = oracle.digest(h)
     h["clips"] = 2
     assert oracle.digest(h) != d0
+
+
+_ACGT = set(b"ACGT")
+
+
+def _fold(b):
+    b = int(b) & 0xDF   # upper case
+    return b if b in _ACGT else ord("N")
+
+
+def _brute_clipped(queries, ref, lens, s, pct):
+    """The definition in plain Python loops: every window start p from -C
+    to n - L + C of every contig, clips = bases outside the contig
+    (left | right << 8), at most C of them and at least one base aligned,
+    mismatches counted over the aligned bases only (N never matches)."""
+    comp = {ord("A"): ord("T"), ord("C"): ord("G"), ord("G"): ord("C"), ord("T"): ord("A")}
+    out = set()
+    starts = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    for qi, q in enumerate(queries):
+        L = len(q)
+        C = pct * L // 100
+        fwd = [_fold(b) for b in q]
+        rev = [comp.get(b, ord("N")) for b in reversed(fwd)]
+        for t, qq in enumerate((fwd, rev)):
+            for ci, n in enumerate(lens.tolist()):
+                r = [_fold(b) for b in ref[starts[ci]:starts[ci] + n]]
+                for p in range(-C, n - L + C + 1):
+                    left, right = max(0, -p), max(0, p + L - n)
+                    if left + right > C or left + right >= L:
+                        continue
+                    mm = sum(1 for i in range(left, L - right)
+                             if qq[i] == ord("N") or r[p + i] == ord("N") or qq[i] != r[p + i])
+                    if mm <= s:
+                        out.add((qi, ci, p + left, t, mm, left | (right << 8)))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_matches_plain_python_definition_on_tiny_inputs(seed):
+    rng = np.random.default_rng(500 + seed)
+    lens = rng.integers(1, 40, size=int(rng.integers(1, 6))).astype(np.int64)
+    alphabet = np.frombuffer(b"ACGTACGTacgN", np.uint8)
+    ref = rng.choice(alphabet, int(lens.sum())).astype(np.uint8)
+    queries = [bytes(rng.choice(alphabet, int(rng.integers(1, 20))).astype(np.uint8)) for _ in range(4)]
+    for pct in (10, 25, 50):
+        for s in (0, 2, 5):
+            got = _keyset(oracle.brute(queries, ref, lens, s, clip_pct=pct))
+            assert got == _brute_clipped(queries, ref, lens, s, pct), (pct, s)

@@ -82,6 +82,7 @@ def _pins():
         lambda: tc.test_planted_overhangs_are_found_with_their_clips("start"),
         lambda: tc.test_planted_overhangs_are_found_with_their_clips("end"),
         lambda: tc.test_digest_sees_the_clips(),
+        lambda: tc.test_matches_plain_python_definition_on_tiny_inputs(0),
     ]
 
 
