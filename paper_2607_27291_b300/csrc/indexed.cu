@@ -78,23 +78,6 @@ cudaError_t seed_launch_t(const Batch &b, const QueryTable &qt, const KTablesArg
     return cudaGetLastError();
 }
 
-// k-mer key of query q (strand t) at offset o: planar hi/lo bits of the
-// counted positions (same code as the device: A=0, C=1, T=2, G=3).
-uint32_t query_key(const std::string &q, bool rc, uint32_t o, uint32_t k, uint32_t care) {
-    const uint32_t L = static_cast<uint32_t>(q.size());
-    uint32_t hi = 0, lo = 0;
-    for (uint32_t i = 0; i < k; i++) {
-        if (!((care >> i) & 1u)) continue;
-        const uint32_t pos = o + i;
-        const uint32_t c = static_cast<uint8_t>(rc ? q[L - 1 - pos] : q[pos]);
-        uint32_t code = base_code(c);
-        if (rc) code ^= 2u;
-        hi |= (code >> 1) << i;
-        lo |= (code & 1u) << i;
-    }
-    return (hi << k) | lo;
-}
-
 bool has_n(const std::string &q) {
     for (char c : q)
         if (!is_base(static_cast<uint8_t>(c))) return true;
