@@ -205,6 +205,27 @@ def test_minhits_one_equals_text_seed_test(wl_idx, k, step, mask_w):
     assert got == expect
 
 
+@pytest.mark.parametrize("step,mask_w", [(1, 0), (2, 0), (1, 2), (3, 1)])
+def test_thresholds_above_one_equal_text_seed_counts(wl_idx, step, mask_w):
+    """Per-query k and minHits (2..6): a brute-force hit is kept exactly when
+    its plain-text seed count reaches the query's threshold."""
+    wl = wl_idx
+    s = 5
+    nq = len(wl.queries)
+    ks = [(5, 6, 7, 8, 6)[i % 5] for i in range(nq)]
+    mh = [(2, 3, 4, 6, 2)[i % 5] for i in range(nq)]
+    got = tuples(oracle.indexed(wl.queries, wl.ref, wl.contig_len, s, ks, mh, [0] * nq, step, mask_w))
+    brute = tuples(oracle.brute(wl.queries, wl.ref, wl.contig_len, s))
+    expect = []
+    for h in brute:
+        q = wl.queries[h[0]]
+        qq = q if h[3] == 0 else _rc(q)
+        if _text_seeded(qq, wl.contig(h[1]), h[2], ks[h[0]], step, mask_w) >= mh[h[0]]:
+            expect.append(h)
+    assert len(expect) < len(brute)       # the thresholds filter something
+    assert got == expect
+
+
 def test_n_is_never_part_of_a_seed():
     # an N opposite an N is still a mismatch: no k-mer holding it is a seed
     ctg = np.frombuffer(b"ACGTNACGTA", np.uint8).copy()
