@@ -201,6 +201,26 @@ ifa_status ifa_set_mode(ifa_handle *h, ifa_mode mode);
 ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len,
                             const ifa_piece *pieces, uint32_t n_pieces, ifa_mem mem);
 
+/* Start the stream in the middle of a contig, as if the segments before
+ * had been pushed: the next segment continues contig `contig` at offset
+ * offset_in_contig + len, and `ascii` (len bytes, memory of kind `mem`)
+ * holds that contig's bases just before it, from offset_in_contig on.  The
+ * last min(len, L_max - 1) of them become the halo (L_max = the longest
+ * loaded query), so windows (and soft-clipped windows) that straddle the
+ * boundary are found, while windows lying wholly inside these bases are not
+ * reported: they belong to whoever scans that part of the reference.  This
+ * is how one reference is split by range over several handles or GPUs (the
+ * paper splits its work by contig over threads, Methods, "Memory
+ * Management"): each range's handle primes its halo and streams its range,
+ * and the ranges' hits together are exactly one pass's hits.
+ * Call it after ifa_load_queries and before the range's first segment, with
+ * no contig open.  Host buffers may be reused on return; a device buffer
+ * must stay unchanged until the next ifa_flush().
+ * Errors: INVALID_ARG (len 0, contig order), BAD_STATE (no queries, a
+ * contig open), CUDA. */
+ifa_status ifa_prime_halo(ifa_handle *h, uint32_t contig, uint64_t offset_in_contig, const uint8_t *ascii,
+                          uint64_t len, ifa_mem mem);
+
 /* Wait until every pushed segment is scanned.  Returns HIT_OVERFLOW if the
  * hit buffer filled since the last ifa_reset_results (hits already written
  * stay valid; digest and counts stay exact), and TIMEOUT if a tensor-core
@@ -358,15 +378,25 @@ ifa_status ifa_serve_stop(ifa_handle *h);
  * fixed memory plan.  The caller passes every input and output buffer; the
  * library's own scratch (packed reference planes, encoded queries, piece
  * table, per-query counts when per_query_counts_device is NULL) lives in one
- * file-scope device array of about 17 MB, which every GPU that loads the
- * library holds until the process exits.  No call allocates device or
- * pinned memory (torch's allocator included).
+ * file-scope device array of about 17 MB.  No call allocates device or
+ * pinned memory itself (torch's allocator included).
+ *
+ * When that array takes device memory: the CUDA runtime loads the library's
+ * device code into a context module by module, on first use (lazy loading,
+ * its default), so on each device the array is placed by the first call of
+ * this function there and stays until the process exits.  A call with
+ * nq = 0 does only that set-up (every other argument but device is then
+ * ignored) and returns IFA_OK: make it once per device at start-up, before
+ * a caching allocator reserves the device's memory and before any stream
+ * capture.  Later calls need no new device memory.  (With the environment
+ * variable CUDA_MODULE_LOADING=EAGER the array is placed when the context
+ * is created.)
  *
  * Limits: 1..256 queries (1..255 bp each), 1..32 MiB of reference, 1..32768
  * whole contigs (every piece has last = 1 and offset_in_contig = 0; no
  * halo is carried between calls).  Larger sizes return
  * IFA_ERR_INVALID_ARG with a message naming the limit, before anything is
- * enqueued.
+ * enqueued.  max_subs takes any value (255 or more reports every window).
  *
  * queries/qlens: host ASCII, as for ifa_load_queries.  ref_device: len
  * ASCII bytes in device memory.  pieces: host, as for ifa_push_segment.
@@ -383,8 +413,10 @@ ifa_status ifa_serve_stop(ifa_handle *h);
  * The work is enqueued on `device` (a device ordinal); the calling
  * thread's current device is the same after the call as before it.
  *
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The call copies queries and the piece table from host memory that it
+ * frees on return, so it cannot be captured into a CUDA graph: on a stream
+ * that is being captured it returns IFA_ERR_INVALID_ARG before enqueuing
+ * anything.
  * Every call on a device shares the one scratch array and leaves its
  * contents behind; each call clears what must start at zero (the counters
  * and per-query counts) itself.  Calls whose device work overlaps -- two

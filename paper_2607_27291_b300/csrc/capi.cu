@@ -423,7 +423,10 @@ ifa_status ifa_load_queries(ifa_handle *h, const uint8_t *const *seqs, const uin
 
 ifa_status ifa_set_max_subs(ifa_handle *h, uint32_t s) {
     if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
-    h->max_subs = s;
+    // A window has at most IFA_MAX_QUERY_LEN = 255 bases, so every value of
+    // 255 or more reports every window (and plans MinHits bins with s >= L);
+    // the clamp keeps launches clear of the per-entry threshold sentinel.
+    h->max_subs = s < 255u ? s : 255u;
     return IFA_OK;
 }
 
@@ -604,6 +607,35 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
             }
         }
     }
+    return IFA_OK;
+}
+
+ifa_status ifa_prime_halo(ifa_handle *h, uint32_t contig, uint64_t offset_in_contig, const uint8_t *ascii,
+                          uint64_t len, ifa_mem mem) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    if (len == 0 || !ascii) return fail(h, IFA_ERR_INVALID_ARG, "the halo needs at least one base");
+    if (mem != IFA_MEM_HOST && mem != IFA_MEM_HOST_PINNED && mem != IFA_MEM_DEVICE)
+        return fail(h, IFA_ERR_INVALID_ARG, "unknown memory kind");
+    if (h->qs.empty()) return fail(h, IFA_ERR_BAD_STATE, "no queries loaded");
+    if (h->open) return fail(h, IFA_ERR_BAD_STATE, "a contig is still open; the halo must come first");
+    if (h->any_contig && contig <= h->last_contig) return fail(h, IFA_ERR_INVALID_ARG, "contig ids must increase");
+    if (offset_in_contig + len > 0xffffffffull) return fail(h, IFA_ERR_INVALID_ARG, "contig longer than 2^32 - 1 bases");
+    CK(h, cudaSetDevice(h->dev));
+    // the same halo a preceding segment of this contig would have left: its
+    // last min(len, L_max - 1) bases
+    const uint32_t keep = static_cast<uint32_t>(std::min<uint64_t>(len, h->lmax > 0 ? h->lmax - 1 : 0));
+    const int nxt = h->halo_cur ^ 1;
+    if (keep)
+        CK(h, cudaMemcpyAsync(h->d_halo[nxt], ascii + (len - keep), keep, cudaMemcpyDefault, h->stream));
+    h->halo_cur = nxt;
+    h->halo_len = keep;
+    h->open = true;
+    h->open_contig = contig;
+    h->open_next = offset_in_contig + len;
+    h->any_contig = true;
+    h->last_contig = contig;
+    h->pushed = true;
+    if (mem != IFA_MEM_DEVICE) CK(h, cudaStreamSynchronize(h->stream));
     return IFA_OK;
 }
 

@@ -7,8 +7,16 @@
 // entry point that takes the caller's input and output buffers and keeps
 // all of its scratch -- the packed reference planes, the encoded query
 // table, the piece table and the per-query counts -- in a file-scope
-// device array of fixed size.  Every GPU that loads the library holds that
-// array (about 17 MB) until the process exits.
+// device array of fixed size (about 17 MB).
+//
+// When the array takes its device memory: the array belongs to this file's
+// CUDA module, and the runtime loads a module into a context when it is
+// first used (lazy loading, CUDA's default), so on each device the array is
+// placed by the first call here -- its cudaGetSymbolAddress -- and then stays
+// until the process exits.  A call with nq = 0 does only that set-up; make it
+// once per device at start-up, before a caching allocator reserves the
+// device's memory and before any stream capture.  (With
+// CUDA_MODULE_LOADING=EAGER the array is placed when the context is made.)
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -81,19 +89,22 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
                                              uint32_t max_subs, ifa_hit *hits_device,
                                              uint64_t hit_capacity, uint64_t *counters_device,
                                              uint64_t *per_query_counts_device, void *stream) {
+    if (device < 0 || device >= 64) return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: device ordinal");
     // ---- arguments (host only; nothing is enqueued before they pass)
-    if (nq == 0 || nq > kNaMaxQueries)
-        return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: 1 to 256 queries per call");
-    if (!queries || !qlens) return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: queries/qlens is NULL");
+    const bool setup_only = nq == 0;
+    if (nq > kNaMaxQueries)
+        return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: at most 256 queries per call (0: set-up only)");
+    if (!setup_only && (!queries || !qlens))
+        return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: queries/qlens is NULL");
     for (uint32_t i = 0; i < nq; i++)
         if (!queries[i] || qlens[i] == 0 || qlens[i] > IFA_MAX_QUERY_LEN)
             return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: query length must be in 1..255");
-    if (len == 0 || len > kNaMaxBases)
+    if (!setup_only && (len == 0 || len > kNaMaxBases))
         return na_fail(IFA_ERR_INVALID_ARG,
                        "ifa_scan_brute_noalloc: reference length must be in 1..33554432 bytes (32 MiB)");
-    if (n_pieces == 0 || n_pieces > kNaMaxPieces)
+    if (!setup_only && (n_pieces == 0 || n_pieces > kNaMaxPieces))
         return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: 1 to 32768 contigs per call");
-    if (!ref_device || !pieces || !hits_device || !counters_device || hit_capacity == 0)
+    if (!setup_only && (!ref_device || !pieces || !hits_device || !counters_device || hit_capacity == 0))
         return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: NULL buffer or zero hit capacity");
     // hits are written 16 bytes at a time and the counters take 64-bit atomics
     if (reinterpret_cast<uintptr_t>(hits_device) % 16 != 0 || reinterpret_cast<uintptr_t>(counters_device) % 8 != 0 ||
@@ -102,7 +113,7 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
                        "ifa_scan_brute_noalloc: hits_device must be 16-byte aligned, counters_device and "
                        "per_query_counts_device 8-byte aligned");
     uint64_t at = 0;
-    for (uint32_t i = 0; i < n_pieces; i++) {
+    for (uint32_t i = 0; i < (setup_only ? 0u : n_pieces); i++) {
         const ifa_piece &p = pieces[i];
         if (p.start != at || p.len == 0 || !p.last || p.offset_in_contig != 0 || p.len > 0xffffffffull)
             return na_fail(IFA_ERR_INVALID_ARG,
@@ -111,9 +122,12 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
             return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: contig ids must increase");
         at += p.len;
     }
-    if (at != len) return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: pieces must cover the reference");
-
-    if (device < 0 || device >= 64) return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: device ordinal");
+    if (!setup_only && at != len)
+        return na_fail(IFA_ERR_INVALID_ARG, "ifa_scan_brute_noalloc: pieces must cover the reference");
+    // a window has at most 255 bases, so any maxSubs of 255 or more reports every
+    // window; clamping keeps the value clear of the per-entry launch sentinel
+    const uint32_t s_launch = max_subs < 255u ? max_subs : 255u;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // work on `device`; the calling thread's current device is put back on return
     int prev = 0;
     cudaError_t e = cudaGetDevice(&prev);
@@ -129,6 +143,17 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
             if (on) cudaSetDevice(dev);
         }
     } restore{prev, prev != device};
+    if (!setup_only) {
+        // the call copies from host memory that is freed on return, so a
+        // captured graph could not replay it
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        const cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+        if (ce != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+            if (ce != cudaSuccess) cudaGetLastError();
+            return na_fail(IFA_ERR_INVALID_ARG,
+                           "ifa_scan_brute_noalloc: the stream is being captured; calls cannot be captured");
+        }
+    }
 
     // ---- set-up, once per device, with that device current
     unsigned char *base = nullptr;
@@ -143,7 +168,7 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
         }
         base = g_na_addr[device];
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (setup_only) return IFA_OK;
     uint4 *words = reinterpret_cast<uint4 *>(base + kOffWords);
     uint4 *qwords = reinterpret_cast<uint4 *>(base + kOffQWords);
     uint32_t *qmeta = reinterpret_cast<uint32_t *>(base + kOffQMeta);
@@ -213,7 +238,7 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
             lo = L < lo ? L : lo;
             hi = L > hi ? L : hi;
         }
-        ck(launch_scan_brute(b, qt, e0, e1, max_subs, lo, hi, sink, st, nullptr));
+        ck(launch_scan_brute(b, qt, e0, e1, s_launch, lo, hi, sink, st, nullptr));
     }
     if (e != cudaSuccess)
         return na_fail(IFA_ERR_CUDA, std::string("ifa_scan_brute_noalloc: ") + cudaGetErrorString(e));

@@ -56,6 +56,28 @@ def test_every_window_when_subs_reach_length():
     assert got.size == 2 * sum(max(0, int(n) - len(q) + 1) for q in wl.queries for n in wl.contig_len)
 
 
+@pytest.mark.parametrize("mode", [P.IFA_MODE_BRUTE, P.IFA_MODE_INDEXED])
+def test_unlimited_max_subs(mode):
+    """maxSubs has no upper limit (Methods): 2^32 - 1 must report every
+    window, like any value at or above the query length, in both modes."""
+    wl = synth.small_workload(seed=19, n_queries=3, lmin=4, lmax=40, n_contigs=6, cmax=400)
+    n_win = 2 * sum(max(0, int(n) - len(q) + 1) for q in wl.queries for n in wl.contig_len)
+    if mode == P.IFA_MODE_BRUTE:
+        exp = oracle.brute(wl.queries, wl.ref, wl.contig_len, 60)
+        assert exp.size == n_win
+    else:
+        # s >= L leaves no error-free k-mer, so every query takes the clamped
+        # plan (smallest k, threshold 1) and stays seed-filtered
+        plan = [oracle.choose_k(len(q), 255, trials=1000) for q in wl.queries]
+        exp = oracle.indexed(wl.queries, wl.ref, wl.contig_len, 255, [p[1] for p in plan],
+                             [p[2] for p in plan], [1 if p[0] < 0 else 0 for p in plan])
+    for s in (255, 1000, 0xFFFFFFFF):
+        got, over, dig, _, _ = gpu_scan(wl.queries, wl.ref, wl.contig_len, s, mode=mode,
+                                        seg_bytes=500, minhits_trials=1000)
+        assert not over and got.size == dig[0]
+        assert tuples(got) == tuples(exp)
+
+
 def test_one_base_segments_and_tiny_contigs():
     queries = [b"ACGTA", b"GGT", b"TTTTTTTT"]
     rng = np.random.default_rng(1)
