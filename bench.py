@@ -37,7 +37,8 @@ METRIC = "query-base comparisons/s and ref Gbp/s scanned (% of roofline); p50/p9
 UNIT = "query-base comparisons/s"
 SUBS = (0, 4, 8, 16)
 SEG = 256 << 20
-POPC_PER_CLK_SM = 16  # 32-bit population count issue rate per SM per clock (CUDA guide, cc 10.x)
+PIPE_RATES_MD = os.path.join(ROOT, "profiles", "int_pipe_rates.md")
+PIPE_KINDS = ("popc", "lop3", "shf", "imad")
 
 
 def parse():
@@ -49,7 +50,8 @@ def parse():
     ap.add_argument("--total", type=float, default=4e9, help="reference bases (default 4 Gbp)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "serving", "indexed", "latency", "brute-kernels"],
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "batched", "serving", "indexed", "latency", "brute-kernels", "pipe-rates"],
                     help="sweep: the 4 Gbp maxSubs sweep (default); batched: many query sets "
                          "in one persistent launch vs one launch per set; serving: Poisson "
                          "arrivals with continuous batching")
@@ -167,6 +169,82 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         return {}
+
+
+def popc_rate():
+    """POPC results per SM per clock, from the committed microbenchmark
+    record (bench.py --workload pipe-rates, kept in profiles/)."""
+    for line in open(PIPE_RATES_MD):
+        if line.strip().startswith("popc_per_clk_sm:"):
+            return float(line.split(":", 1)[1])
+    raise RuntimeError("no popc_per_clk_sm line in " + PIPE_RATES_MD)
+
+
+def pcie_peaks(dev, mb=256, reps=10):
+    """Best-of-`reps` pinned host <-> device copy rates of `mb` MiB (GB/s)."""
+    import torch
+    n = mb << 20
+    host = torch.empty(n, dtype=torch.uint8).pin_memory()
+    devb = torch.empty(n, dtype=torch.uint8, device=f"cuda:{dev}")
+    st = torch.cuda.Stream(device=dev)
+    out = {}
+    for name, fn in (("h2d_gbps", lambda: devb.copy_(host, non_blocking=True)),
+                     ("d2h_gbps", lambda: host.copy_(devb, non_blocking=True))):
+        best = None
+        with torch.cuda.stream(st):
+            fn()
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                fn()
+                b.record(st)
+                b.synchronize()
+                ms = a.elapsed_time(b)
+                best = ms if best is None else min(best, ms)
+        out[name] = n / (best * 1e-3) / 1e9
+    out["bytes"] = n
+    out["how"] = "pinned %d MiB copy, best of %d, CUDA events" % (mb, reps)
+    del host, devb
+    return out
+
+
+def run_pipe_rates(args):
+    """Integer-pipe issue rates per SM per clock (POPC, LOP3, SHF, IMAD) from
+    the probe library, with the SM clock sampled meanwhile, and the pinned
+    PCIe copy peaks."""
+    import ctypes as C
+    import torch
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    lib = C.CDLL(os.path.join(ROOT, "paper_2607_27291_b300", "libifa_probe.so"))
+    f = lib.ifa_probe_pipe_rate
+    f.restype = C.c_int
+    f.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                  C.POINTER(C.c_double)]
+    clocks = Clocks(dev)
+    clocks.start()
+    rates = {}
+    for kind, name in enumerate(PIPE_KINDS):
+        rows = []
+        for _ in range(max(1, args.steps)):
+            r, ms, mhz = C.c_double(), C.c_double(), C.c_double()
+            rc = f(dev, kind, 4, 2000, C.byref(r), C.byref(ms), C.byref(mhz))
+            if rc:
+                raise RuntimeError("probe failed for %s: %d" % (name, rc))
+            rows.append((r.value, ms.value, mhz.value))
+        rows.sort()
+        med = rows[len(rows) // 2]
+        rates[name] = {"per_clk_sm": med[0], "ms": med[1], "sm_mhz_from_cycles": med[2],
+                       "min": rows[0][0], "max": rows[-1][0]}
+    clk = clocks.stop()
+    pcie = pcie_peaks(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    line = {"workload": "pipe-rates", "metric": "results per SM per clock", "unit": "ops/clk/SM",
+            "rates": rates, "sms": sms, "clocks": clk, "pcie": pcie,
+            "config": {"blocks_per_sm": 4, "threads": 256, "chains_per_thread": 8,
+                       "instructions_per_thread": 2000 * 16 * 8, "runs": max(1, args.steps)}}
+    print(json.dumps(line), flush=True)
 
 
 def kernel_source_digest():
@@ -336,8 +414,9 @@ def run_ours(args, rank, world):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     avg_launch_s = (scan_ns * 1e-9) / max(1, scan_launches)
     evals_per_launch = win_pass * len(SUBS) * steps / max(1, scan_launches)
+    popc_clk = popc_rate()
     achieved = evals_per_launch / avg_launch_s / 1e9           # G popc / s
-    peak = sms * POPC_PER_CLK_SM * sm_mhz * 1e6 / 1e9          # G popc / s
+    peak = sms * popc_clk * sm_mhz * 1e6 / 1e9                 # G popc / s
     traffic = traffic_record()
 
     # ---- end to end through pinned host memory
@@ -357,9 +436,12 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         dt = allmax(dt, world)
+        pk = pcie_peaks(dev)
+        h2d = wl.ref.size * len(SUBS) / dt / 1e9
         e2e = {"value": world * qb_step / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(wl.ref.size) * len(SUBS), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": dt * 1e3, "pcie_h2d_gbps": wl.ref.size * len(SUBS) / dt / 1e9}
+               "ms_per_step": dt * 1e3, "pcie_h2d_gbps": h2d,
+               "pcie_peak": pk, "pcie_h2d_frac": h2d / pk["h2d_gbps"]}
     P.ifa_destroy(h)
 
     cpu = None
@@ -393,8 +475,9 @@ def run_ours(args, rank, world):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_scan_brute", "launches": scan_launches,
                      "avg_launch_ms": avg_launch_s * 1e3,
-                     "peak_basis": "%d SMs x %d POPC/clk/SM x %.0f MHz (median SM clock sampled "
-                                   "during the timed region)" % (sms, POPC_PER_CLK_SM, sm_mhz)},
+                     "peak_basis": "%d SMs x %.1f POPC/clk/SM (measured, profiles/int_pipe_rates.md) x "
+                                   "%.0f MHz (median SM clock sampled during the timed region)"
+                                   % (sms, popc_clk, sm_mhz)},
         "clocks": clk,
         "gpu_launches": int(launches),
         "e2e": e2e,
@@ -752,6 +835,8 @@ def main():
         return run_latency(args)
     if args.workload == "brute-kernels":
         return run_brute_kernels(args)
+    if args.workload == "pipe-rates":
+        return run_pipe_rates(args)
     rank, world = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -83,6 +83,7 @@ _SYMBOLS = {
     "ifa_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "ifa_push_segment": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32,
                                    C.c_int]),
+    "ifa_prime_halo": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint64, C.c_void_p, C.c_uint64, C.c_int]),
     "ifa_flush": (C.c_int, [C.c_void_p]),
     "ifa_drain_hits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64),
                                  C.POINTER(C.c_int)]),
@@ -205,25 +206,36 @@ def _as_pieces(pieces) -> np.ndarray:
     return arr
 
 
+def _buffer(data, mem: Optional[int]):
+    """(pointer, length, memory kind) of a numpy uint8 array (pageable host),
+    a torch uint8 tensor (CUDA, or pinned CPU) or a (pointer, length, mem)
+    tuple."""
+    if isinstance(data, tuple):
+        return data
+    if isinstance(data, np.ndarray):
+        assert data.dtype == np.uint8 and data.flags.c_contiguous
+        return data.ctypes.data, data.size, IFA_MEM_HOST if mem is None else mem
+    assert data.is_contiguous()  # torch tensor
+    if mem is None:
+        mem = IFA_MEM_DEVICE if data.is_cuda else (IFA_MEM_HOST_PINNED if data.is_pinned() else IFA_MEM_HOST)
+    return data.data_ptr(), data.numel(), mem
+
+
 def ifa_push_segment(h, data, pieces, mem: Optional[int] = None) -> None:
     """Push one segment.  `data`: a numpy uint8 array (pageable host), a torch
     uint8 tensor (CUDA, or pinned CPU), or a (pointer, length, mem) tuple.
     `pieces`: PIECE_DTYPE array or (contig, offset_in_contig, start, len,
     last) tuples."""
     pa = _as_pieces(pieces)
-    if isinstance(data, tuple):
-        ptr, ln, mem = data
-    elif isinstance(data, np.ndarray):
-        assert data.dtype == np.uint8 and data.flags.c_contiguous
-        ptr, ln = data.ctypes.data, data.size
-        mem = IFA_MEM_HOST if mem is None else mem
-    else:  # torch tensor
-        assert data.is_contiguous()
-        ptr, ln = data.data_ptr(), data.numel()
-        if mem is None:
-            mem = IFA_MEM_DEVICE if data.is_cuda else (
-                IFA_MEM_HOST_PINNED if data.is_pinned() else IFA_MEM_HOST)
+    ptr, ln, mem = _buffer(data, mem)
     _check(lib().ifa_push_segment(h, C.c_void_p(ptr), ln, pa.ctypes.data, pa.size, mem), h)
+
+
+def ifa_prime_halo(h, contig: int, offset_in_contig: int, data, mem: Optional[int] = None) -> None:
+    """Start the stream inside contig `contig`: `data` holds its bases from
+    offset_in_contig up to where the next pushed segment begins."""
+    ptr, ln, mem = _buffer(data, mem)
+    _check(lib().ifa_prime_halo(h, int(contig), int(offset_in_contig), C.c_void_p(ptr), ln, mem), h)
 
 
 def ifa_flush(h) -> int:
@@ -425,7 +437,8 @@ def ifa_scan_brute_noalloc(device: int, queries: Sequence[bytes], ref_ptr: int, 
                            pieces, max_subs: int, hits_ptr: int, hit_capacity: int,
                            counters_ptr: int, per_query_counts_ptr: int = 0, stream=None) -> None:
     """Allocation-free brute-force scan of one chunk of whole contigs; every
-    buffer is the caller's (device pointers as ints)."""
+    buffer is the caller's (device pointers as ints).  With no queries the
+    call only places the library's scratch array on `device` (set-up)."""
     n = len(queries)
     bufs = [C.create_string_buffer(bytes(q), len(q)) for q in queries]
     ptrs = (C.c_void_p * max(1, n))(*[C.cast(b, C.c_void_p) for b in bufs])
@@ -515,12 +528,17 @@ def sort_hits(h: np.ndarray) -> np.ndarray:
     return h[order]
 
 
-def segment_pieces(contig_len: np.ndarray, seg_bytes: int, contig_ids=None):
-    """Cut a concatenated reference into (begin, end, PIECE_DTYPE array)."""
+def segment_pieces(contig_len: np.ndarray, seg_bytes: int, contig_ids=None, lo: int = 0,
+                   hi: Optional[int] = None):
+    """Cut the range [lo, hi) (default: all) of a concatenated reference into
+    (begin, end, PIECE_DTYPE array); begin/end are offsets into the whole
+    reference.  A range starting inside a contig gives a first piece with
+    offset_in_contig > 0 (prime the handle with ifa_prime_halo first, see
+    shard_halo); one ending inside a contig gives a last piece with last = 0."""
     starts = np.concatenate([[0], np.cumsum(np.asarray(contig_len, np.int64))]).astype(np.int64)
-    total = int(starts[-1])
+    total = int(starts[-1]) if hi is None else min(int(hi), int(starts[-1]))
     ids = np.arange(len(contig_len), dtype=np.int64) if contig_ids is None else np.asarray(contig_ids)
-    pos = 0
+    pos = int(lo)
     while pos < total:
         end = min(total, pos + seg_bytes)
         a = int(np.searchsorted(starts, pos, side="right")) - 1
@@ -538,6 +556,33 @@ def segment_pieces(contig_len: np.ndarray, seg_bytes: int, contig_ids=None):
         keep = arr["len"] > 0
         yield pos, end, arr[keep]
         pos = end
+
+
+def shard_range(total: int, world: int, rank: int) -> Tuple[int, int]:
+    """Rank `rank`'s share [lo, hi) of a reference of `total` bases split into
+    `world` contiguous ranges of (nearly) equal length.  Ranges may cut
+    contigs; the scans need no exchange step (each window belongs to the
+    range holding its last base), so hits concatenate and digests add."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    return total * rank // world, total * (rank + 1) // world
+
+
+def shard_halo(contig_len: np.ndarray, lo: int, lmax: int, contig_ids=None):
+    """The halo a range starting at `lo` needs: (contig id, offset_in_contig,
+    begin, end) of the up to lmax - 1 bases of lo's contig just before lo
+    (begin/end are offsets into the whole reference), or None when lo is a
+    contig start.  Pass ref[begin:end] to ifa_prime_halo."""
+    starts = np.concatenate([[0], np.cumsum(np.asarray(contig_len, np.int64))]).astype(np.int64)
+    if lo <= 0 or lo >= int(starts[-1]):
+        return None
+    ci = int(np.searchsorted(starts, lo, side="right")) - 1
+    off = lo - int(starts[ci])
+    if off == 0 or lmax <= 1:
+        return None
+    h = min(off, lmax - 1)
+    cid = ci if contig_ids is None else int(np.asarray(contig_ids)[ci])
+    return cid, off - h, lo - h, lo
 
 
 class Aligner:

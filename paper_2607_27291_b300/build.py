@@ -14,6 +14,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(HERE, "libifa.so")
+# the integer-pipe issue-rate microbenchmark (a measurement tool, not the aligner)
+PROBE_SRC = os.path.join(HERE, "probe", "pipe_rates.cu")
+PROBE_LIB = os.path.join(HERE, "libifa_probe.so")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -69,6 +72,15 @@ def build(force: bool = False, verbose: bool = False, extra=(), out: str = None)
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
         os.replace(tmp, lib_path)
+    if out is None and (force or _stale(PROBE_LIB, [PROBE_SRC])):
+        tmp = PROBE_LIB + ".tmp%d" % os.getpid()
+        cmd = [NVCC] + ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+                               PROBE_SRC, "-o", tmp, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            sys.stderr.write(r.stdout + r.stderr)
+            raise RuntimeError("probe build failed")
+        os.replace(tmp, PROBE_LIB)
     return lib_path
 
 
