@@ -91,26 +91,48 @@ def allmax(x, world):
     return float(t.item())
 
 
-def shard_seed(rank):
-    """Reference seed of a rank's shard: rank 0 scans the 4 Gbp reference of
-    the single-GPU run, rank r > 0 a reference drawn from its own seed (weak
-    scaling: the N ranks together scan N independent shards)."""
-    return 2 + 1000 * rank
+def allsum(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
 
 
-def make_workload(total, rank=0):
+def make_workload(total, rank=0, world=1):
+    """The 4 Gbp recipe.  Under N ranks it is one reference of N x `total`
+    bases split by range: rank r builds only its range [lo, hi) (plus the
+    bases its halo needs) and scans it; the ranges' hits together are one
+    pass's hits (weak scaling: every rank scans `total` bases).  Returns
+    (workload, lo, hi, halo) with halo as from P.shard_halo."""
     import synth
-    return synth.workload_4gbp(total=int(total), seed=shard_seed(rank))
+    import paper_2607_27291_b300 as P
+    if world <= 1:
+        wl = synth.workload_4gbp(total=int(total))
+        return wl, 0, int(wl.ref.size), None
+    lens = synth.contig_lengths(int(world * total), 1000, 5_000_000, "lognormal", 2)
+    lo, hi = P.shard_range(int(lens.sum()), world, rank)
+    lmax = max(len(q) for q in synth.random_queries(10, 30, 40, 2))
+    halo = P.shard_halo(lens, lo, lmax)
+    wl = synth.workload_4gbp(total=int(world * total), window=(halo[2] if halo else lo, hi))
+    return wl, lo, hi, halo
 
 
-def nominal_work(wl, contig_sel=None):
-    """(windows, query-base comparisons) for one maxSubs pass, both strands."""
+def nominal_work(wl, contig_sel=None, lo=0, hi=None):
+    """(windows, query-base comparisons) for one maxSubs pass, both strands:
+    the windows whose last base lies in [lo, hi) (default: all)."""
     lens = wl.contig_len if contig_sel is None else wl.contig_len[contig_sel]
+    starts = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64)
+    hi = int(lens.sum()) if hi is None else hi
     win = 0
     qb = 0
     for q in wl.queries:
         L = len(q)
-        w = int(np.maximum(lens - L + 1, 0).sum())
+        first = np.maximum(starts + L - 1, lo)           # last base of the contig's first window
+        last = np.minimum(starts + lens - 1, hi - 1)     # last base of its last window
+        w = int(np.maximum(last - first + 1, 0).sum())
         win += 2 * w
         qb += 2 * w * L
     return win, qb
@@ -285,9 +307,9 @@ def cpu_sample(wl, target_bases):
     return np.arange(n)
 
 
-def time_oracle(wl, sel, subs=SUBS):
+def time_oracle(wl, sel, subs=SUBS, threads=None):
     import oracle
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     end = int(wl.contig_len[sel].sum())
     ref = wl.ref[:end]
     lens = wl.contig_len[sel]
@@ -302,7 +324,8 @@ def time_oracle(wl, sel, subs=SUBS):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = make_workload(args.total)
+    import synth
+    wl = synth.workload_4gbp(total=int(args.total), window=(0, 16_000_000))   # the sample's contigs
     sel = cpu_sample(wl, 4_000_000)
     for _ in range(max(0, args.warmup)):
         time_oracle(wl, sel[:1])
@@ -335,9 +358,10 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     t_gen = time.perf_counter()
-    wl = make_workload(args.total, rank)
+    wl, lo, hi, halo = make_workload(args.total, rank, world)
     t_gen = time.perf_counter() - t_gen
-    segs = list(P.segment_pieces(wl.contig_len, SEG))
+    off = wl.ref_offset
+    segs = list(P.segment_pieces(wl.contig_len, SEG, lo=lo, hi=hi))
     ref_dev = torch.from_numpy(wl.ref).to(f"cuda:{dev}")
     stream = torch.cuda.Stream(device=dev)
     # hit buffer sized to the reference: the 4 Gbp sweep's maxSubs-16 pass emits
@@ -347,13 +371,15 @@ def run_ours(args, rank, world):
     P.ifa_set_stream(h, stream)
     P.ifa_load_queries(h, wl.queries)
     P.ifa_set_mode(h, P.IFA_MODE_BRUTE)
-    win_pass, qb_pass = nominal_work(wl)
+    win_pass, qb_pass = nominal_work(wl, lo=lo, hi=hi)
 
     def one_pass(s, source, drain):
         P.ifa_reset_results(h)
         P.ifa_set_max_subs(h, s)
+        if halo:
+            P.ifa_prime_halo(h, halo[0], halo[1], source[halo[2] - off:halo[3] - off])
         for a, b, pc in segs:
-            P.ifa_push_segment(h, source[a:b], pc)
+            P.ifa_push_segment(h, source[a - off:b - off], pc)
         if drain:
             hits, _ = P.ifa_drain_hits(h, copy=False)
             return hits.size
@@ -405,8 +431,10 @@ def run_ours(args, rank, world):
     total_ms = allmax(total_ms, world)
     steps = args.steps
     qb_step = qb_pass * len(SUBS)
-    value = world * qb_step * steps / (total_ms * 1e-3)
-    gbps = world * wl.ref.size * len(SUBS) * steps / (total_ms * 1e-3) / 1e9
+    qb_all = allsum(qb_step, world)            # every rank's windows: one pass over the whole reference
+    bases_all = allsum(hi - lo, world)
+    value = qb_all * steps / (total_ms * 1e-3)
+    gbps = bases_all * len(SUBS) * steps / (total_ms * 1e-3) / 1e9
 
     # ---- roofline of the scan kernel (POPC pipe)
     peaks = measured_peaks()
@@ -438,7 +466,7 @@ def run_ours(args, rank, world):
         dt = allmax(dt, world)
         pk = pcie_peaks(dev)
         h2d = wl.ref.size * len(SUBS) / dt / 1e9
-        e2e = {"value": world * qb_step / dt, "unit": UNIT,
+        e2e = {"value": qb_all / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(wl.ref.size) * len(SUBS), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": dt * 1e3, "pcie_h2d_gbps": h2d,
                "pcie_peak": pk, "pcie_h2d_frac": h2d / pk["h2d_gbps"]}
@@ -448,9 +476,14 @@ def run_ours(args, rank, world):
     if rank == 0 and world == 1 and not args.no_cpu:
         sel = cpu_sample(wl, 4_000_000)
         v, threads, dt, nb = time_oracle(wl, sel)
+        sel1 = cpu_sample(wl, 250_000)
+        v1, _, dt1, nb1 = time_oracle(wl, sel1, threads=1)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "first %d contigs (%d bases) at maxSubs 0/4/8/16, %.1f s" % (
-                   len(sel), nb, dt)}
+                   len(sel), nb, dt),
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                 "sample": "first %d contigs (%d bases) at maxSubs 0/4/8/16, %.1f s"
+                                           % (len(sel1), nb1, dt1)}}
 
     if rank != 0:
         return
@@ -460,7 +493,10 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "10q30-40bp_4Gbp_GC40_sweep0-4-8-16",
-                   "reference_bases": int(wl.ref.size), "contigs": int(wl.contig_len.size),
+                   "reference_bases": int(bases_all), "contigs": int(wl.contig_len.size),
+                   "sharding": ("one reference of %d bases split by range over %d ranks "
+                                "(%d bases each, halo inside split contigs, no exchange)"
+                                % (bases_all, world, hi - lo)) if world > 1 else "none",
                    "queries": len(wl.queries), "query_lengths": [len(q) for q in wl.queries],
                    "max_subs": list(SUBS), "segment_bytes": SEG, "mode": "brute-force",
                    "l2": "inputs (4 GB ASCII, 2 GB packed) exceed the 126 MB L2; no flush",

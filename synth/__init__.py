@@ -105,11 +105,25 @@ def _fill_chunk(out: np.ndarray, start: int, n: int, gc_of, seed: int, ci: int):
 
 def random_bases(total: int, gc, seed: int, threads: Optional[int] = None,
                  contig_len: Optional[np.ndarray] = None,
-                 contig_gc: Optional[np.ndarray] = None) -> np.ndarray:
+                 contig_gc: Optional[np.ndarray] = None, window=None) -> np.ndarray:
     """ASCII bases (uint8) with the GC model above.
 
     `gc` is a float, or None together with per-contig `contig_gc` values
-    (then `contig_len` gives the contig layout)."""
+    (then `contig_len` gives the contig layout).  `window` = (a, b) returns
+    only bases [a, b) of the `total`, equal to that slice of the whole."""
+    if window is not None:
+        a, b = int(window[0]), int(window[1])
+        if contig_gc is not None:
+            raise ValueError("window needs a fixed gc")
+        out = np.empty(b - a, dtype=np.uint8)
+        tmp = np.empty(CHUNK, dtype=np.uint8)
+        for ci in range(a // CHUNK, (b + CHUNK - 1) // CHUNK):
+            c0 = ci * CHUNK
+            n = min(CHUNK, total - c0)
+            _fill_chunk(tmp, 0, n, lambda st, k: float(gc), seed, ci)
+            lo, hi = max(a, c0), min(b, c0 + n)
+            out[lo - a:hi - a] = tmp[lo - c0:hi - c0]
+        return out
     out = np.empty(total, dtype=np.uint8)
     if contig_gc is not None:
         starts = np.concatenate([[0], np.cumsum(contig_len)[:-1]])
@@ -152,21 +166,42 @@ class _Occupied:
         self.ends.insert(i, b)
 
 
-def add_n_runs(ref: np.ndarray, frac: float, seed: int, occ: _Occupied) -> int:
+def _write(ref: np.ndarray, offset: int, a: int, data) -> None:
+    """ref holds bases [offset, offset + ref.size) of the whole reference:
+    write `data` (a byte value or bytes) at whole-reference position a, only
+    where it overlaps."""
+    n = 1 if isinstance(data, int) else len(data)
+    lo, hi = max(a, offset), min(a + n, offset + ref.size)
+    if lo >= hi:
+        return
+    if isinstance(data, int):
+        ref[lo - offset:hi - offset] = data
+    else:
+        ref[lo - offset:hi - offset] = np.frombuffer(bytes(data), dtype=np.uint8)[lo - a:hi - a]
+
+
+def add_n_runs(ref: np.ndarray, frac: float, seed: int, occ: _Occupied, total: Optional[int] = None,
+               offset: int = 0) -> int:
     """Overwrite runs of 'N' (length uniform in [10, 1000]) until `frac` of
-    the bases are N.  Returns the number of N bases written."""
+    the bases are N.  Returns the number of N bases written.  With `total`,
+    ref is the window [offset, offset + ref.size) of a reference of `total`
+    bases: the runs are drawn for the whole and written where they overlap."""
     if frac <= 0:
         return 0
+    total = ref.size if total is None else int(total)
     rng = _rng(seed, _S_NRUNS)
-    target = int(frac * ref.size)
+    target = int(frac * total)
     done = 0
     while done < target:
         L = int(rng.integers(10, 1001))
         L = min(L, target - done) if target - done >= 10 else L
-        a = int(rng.integers(0, max(1, ref.size - L)))
+        a = int(rng.integers(0, max(1, total - L)))
         if not occ.free(a, a + L):
             continue
-        ref[a:a + L] = ord("N")
+        if offset == 0 and total == ref.size:
+            ref[a:a + L] = ord("N")
+        else:
+            _write(ref, offset, a, b"N" * L)
         occ.add(a, a + L)
         done += L
     return done
@@ -183,8 +218,10 @@ class Plant:
 
 def plant_hits(ref: np.ndarray, starts: np.ndarray, lens: np.ndarray,
                queries: Sequence[bytes], ks: Sequence[int], seed: int,
-               occ: _Occupied) -> List[Plant]:
-    """Write one plant per entry of `ks` (its substitution count)."""
+               occ: _Occupied, offset: int = 0) -> List[Plant]:
+    """Write one plant per entry of `ks` (its substitution count); ref holds
+    the whole reference, or its window from `offset` on (plants are drawn
+    for the whole and written where they overlap)."""
     rng = _rng(seed, _S_PLANTS)
     plants = []
     for k in ks:
@@ -209,7 +246,7 @@ def plant_hits(ref: np.ndarray, starts: np.ndarray, lens: np.ndarray,
                 cur = seq[j]
                 others = [c for c in b"ACGT" if c != cur]
                 seq[j] = others[int(rng.integers(0, 3))]
-            ref[a:a + L] = np.frombuffer(bytes(seq), dtype=np.uint8)
+            _write(ref, offset, a, seq)
             occ.add(a, a + L)
             plants.append(Plant(qi, ci, p, t, k_eff))
             break
@@ -228,6 +265,7 @@ class Workload:
     max_subs: List[int]
     plants: List[Plant]
     n_bases_N: int = 0
+    ref_offset: int = 0        # ref holds bases [ref_offset, ref_offset + ref.size) of the whole
 
     @property
     def contig_start(self) -> np.ndarray:
@@ -316,22 +354,28 @@ def workload_1mbp_x10() -> Workload:
 
 
 def workload_4gbp(total: int = 4_000_000_000, plants_per_k: int = 1000,
-                  max_subs: Sequence[int] = (0, 4, 8, 16), seed: int = 2) -> Workload:
+                  max_subs: Sequence[int] = (0, 4, 8, 16), seed: int = 2, window=None) -> Workload:
     """10 queries of 30-40 bp against a GC-40% reference of log-normal
     contigs (1 kbp - 5 Mbp) with 0.1% N in runs of 10-1000, and
     `plants_per_k` plants for every k <= max(max_subs).  `total` can be
     lowered to build a scaled-down instance of the same recipe.  The queries
-    are always drawn from seed 2; `seed` draws the reference and plants."""
+    are always drawn from seed 2; `seed` draws the reference and plants.
+    `window` = (a, b): build only bases [a, b) of the reference (ref_offset
+    = a), byte for byte that slice of the whole -- one rank's range of a
+    reference too large for one host."""
     queries = random_queries(10, 30, 40, 2)
     lens = contig_lengths(total, 1000, 5_000_000, "lognormal", seed)
     tot = int(lens.sum())
-    ref = random_bases(tot, 0.40, seed)
+    a, b = (0, tot) if window is None else (max(0, int(window[0])), min(tot, int(window[1])))
+    ref = random_bases(tot, 0.40, seed, window=None if window is None else (a, b))
     occ = _Occupied()
-    nN = add_n_runs(ref, 0.001, seed, occ)
+    nN = add_n_runs(ref, 0.001, seed, occ, total=tot, offset=a)
     starts = np.concatenate([[0], np.cumsum(lens)[:-1]])
     ks = [k for k in range(max(max_subs) + 1) for _ in range(plants_per_k)]
-    plants = plant_hits(ref, starts, lens, queries, ks, seed, occ)
-    return Workload("10q30-40bp_4Gbp", queries, ref, lens, list(max_subs), plants, nN)
+    plants = plant_hits(ref, starts, lens, queries, ks, seed, occ, offset=a)
+    wl = Workload("10q30-40bp_4Gbp", queries, ref, lens, list(max_subs), plants, nN)
+    wl.ref_offset = a
+    return wl
 
 
 def workload_1gbp_indexed(total: int = 1_000_000_000, n_queries: int = 10_000,
