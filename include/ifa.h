@@ -115,7 +115,7 @@ typedef struct {
 typedef struct {
     int32_t device;                /* CUDA device ordinal */
     uint32_t count_only;           /* 1: keep digest/counts only, write no hit tuples */
-    uint64_t hit_capacity;         /* device hit buffer entries */
+    uint64_t hit_capacity;         /* device hit ring entries (16 bytes each) */
     uint64_t segment_bytes;        /* largest segment accepted by ifa_push_segment */
     /* indexed mode (Methods, indexed mode) */
     uint32_t k_list[IFA_MAX_KLIST];/* candidate seed lengths, paper default 8,9,10,12,14 */
@@ -228,12 +228,26 @@ ifa_status ifa_prime_halo(ifa_handle *h, uint32_t contig, uint64_t offset_in_con
  * stays usable and ifa_reset_results clears the status). */
 ifa_status ifa_flush(ifa_handle *h);
 
-/* Copy up to cap buffered hits into out (host memory) and release them from
- * the device buffer; *n_out gets the number copied, *more (may be NULL)
- * whether buffered hits remain.  Order is unspecified (compare as sets).
- * Implies ifa_flush().  Returns HIT_OVERFLOW (with the data) if hits were
- * dropped. */
+/* Hits wait in a ring of hit_capacity entries in device memory (Methods,
+ * "Output Format": hits leave as the stream goes).  A hit that finds the
+ * ring full is dropped: the digest and per-query counts still count it,
+ * HIT_OVERFLOW is reported, and hits claimed after the first dropped one are
+ * not drained (they are part of the overflow).
+ *
+ * Copy up to cap buffered hits into out (host memory) and release their
+ * ring slots; *n_out gets the number copied, *more (may be NULL) whether
+ * buffered hits remain.  Order is unspecified (compare as sets).  Implies
+ * ifa_flush().  Returns HIT_OVERFLOW (with the data) if hits were dropped;
+ * once everything before the drop is drained the ring takes hits again. */
 ifa_status ifa_drain_hits(ifa_handle *h, ifa_hit *out, uint64_t cap, uint64_t *n_out, int *more);
+
+/* Like ifa_drain_hits, without waiting: copies (up to cap) the hits of the
+ * segments whose scans have already finished, on a stream of its own, while
+ * later segments are still being scanned, and frees their ring slots.  Call
+ * it between ifa_push_segment calls to stream hits out of a ring smaller
+ * than a pass's hits.  *more: finished hits remain.  Returns HIT_OVERFLOW
+ * (with the data) once a hit was dropped. */
+ifa_status ifa_poll_hits(ifa_handle *h, ifa_hit *out, uint64_t cap, uint64_t *n_out, int *more);
 
 /* Digest of all hits since the last reset; per_query_counts (may be NULL)
  * receives one count per loaded query.  Implies ifa_flush(). */
@@ -376,9 +390,9 @@ ifa_status ifa_serve_stop(ifa_handle *h);
  * inside a framework whose caching allocator already holds the device
  * memory, where any allocation outside it fails, or a serving loop with a
  * fixed memory plan.  The caller passes every input and output buffer; the
- * library's own scratch (packed reference planes, encoded queries, piece
+ * library's own scratch (packed reference words, encoded queries, piece
  * table, per-query counts when per_query_counts_device is NULL) lives in one
- * file-scope device array of about 17 MB.  No call allocates device or
+ * file-scope device array of about 26 MB.  No call allocates device or
  * pinned memory itself (torch's allocator included).
  *
  * When that array takes device memory: the CUDA runtime loads the library's

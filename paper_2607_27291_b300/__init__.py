@@ -87,6 +87,8 @@ _SYMBOLS = {
     "ifa_flush": (C.c_int, [C.c_void_p]),
     "ifa_drain_hits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64),
                                  C.POINTER(C.c_int)]),
+    "ifa_poll_hits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64),
+                                C.POINTER(C.c_int)]),
     "ifa_get_digest": (C.c_int, [C.c_void_p, C.POINTER(ifa_digest), C.c_void_p]),
     "ifa_reset_results": (C.c_int, [C.c_void_p]),
     "ifa_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ifa_stats)]),
@@ -293,6 +295,29 @@ def ifa_drain_hits(h, cap: Optional[int] = None, copy: bool = True) -> Tuple[np.
     if len(parts) == 1:
         return parts[0], overflowed
     return (np.concatenate(parts) if parts else np.zeros(0, HIT_DTYPE)), overflowed
+
+
+def ifa_poll_hits(h, out: np.ndarray) -> Tuple[int, bool, bool]:
+    """Copy the hits of already finished segments into `out` (a HIT_DTYPE
+    array; pinned memory copies fastest) without waiting for the device;
+    returns (hits copied, overflowed, more finished hits waiting)."""
+    assert out.dtype == HIT_DTYPE and out.flags.c_contiguous
+    n = C.c_uint64()
+    more = C.c_int()
+    st = _check(lib().ifa_poll_hits(h, out.ctypes.data, out.size, C.byref(n), C.byref(more)), h,
+                allow=(IFA_OK, IFA_ERR_HIT_OVERFLOW))
+    return n.value, st == IFA_ERR_HIT_OVERFLOW, bool(more.value)
+
+
+def ifa_drain_into(h, out: np.ndarray) -> Tuple[int, bool, bool]:
+    """ifa_drain_hits into the caller's HIT_DTYPE array `out` (waits for the
+    device); returns (hits copied, overflowed, more hits waiting)."""
+    assert out.dtype == HIT_DTYPE and out.flags.c_contiguous
+    n = C.c_uint64()
+    more = C.c_int()
+    st = _check(lib().ifa_drain_hits(h, out.ctypes.data, out.size, C.byref(n), C.byref(more)), h,
+                allow=(IFA_OK, IFA_ERR_HIT_OVERFLOW))
+    return n.value, st == IFA_ERR_HIT_OVERFLOW, bool(more.value)
 
 
 def ifa_get_digest(h, nq: Optional[int] = None):

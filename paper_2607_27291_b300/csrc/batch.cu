@@ -38,7 +38,7 @@ namespace {
 
 constexpr int kBThreads = 256;
 constexpr int kBWarps = kBThreads / kWarp;
-constexpr uint64_t kStorePad = 16;  // zeroed words after the last packed word
+constexpr uint64_t kStorePad = 16;  // padding words after the last packed word (packed as N)
 
 ifa_status bfail(ifa_handle *h, ifa_status st, const std::string &msg) {
     h->err = msg;
@@ -61,10 +61,9 @@ template <int WMAX, bool MULTI>
 __global__ void __launch_bounds__(kBThreads)
 k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
     using namespace brute;
-    constexpr int NW = Stage<WMAX>::kWords;
     extern __shared__ uint4 smem4[];
     __shared__ __align__(16) ifa_hit wbuf[kBWarps][32];
-    __shared__ uint4 stage[kBWarps][2][NW];
+    __shared__ __align__(8) uint2 stage[kBWarps][2][Stage<WMAX>::kSlots];
     __shared__ uint32_t s_nF, s_nM, s_item;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
@@ -167,14 +166,28 @@ int batch_kernel_grid(uint32_t wmax) { return batch_grid(wmax); }
 
 namespace {
 
-Batch store_batch(const BatchState &B) {
-    Batch b;
-    b.words = B.d_words;
-    b.nbases = B.nbases;
-    b.halo = 0;
-    b.pieces = B.d_pieces;
-    b.npieces = B.d_pieces_n;
-    return b;
+Batch store_batch(const BatchState &B) { return make_batch(B.ref, B.nbases, 0, B.d_pieces, B.d_pieces_n); }
+
+// Grow a device array to `want` elements, keeping its first `keep` (the
+// copy is finished before the old array is freed).
+template <class T>
+cudaError_t grow(T *&p, uint64_t &cap, uint64_t want, uint64_t keep, cudaStream_t st) {
+    if (want <= cap && p) return cudaSuccess;
+    T *n = nullptr;
+    cudaError_t e = cudaMalloc(&n, want * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (p && keep) {
+        e = cudaMemcpyAsync(n, p, keep * sizeof(T), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaFree(n);
+            return e;
+        }
+    }
+    cudaFree(p);
+    p = n;
+    cap = want;
+    return cudaSuccess;
 }
 
 HitSink handle_sink(const ifa_handle *h) {
@@ -186,6 +199,8 @@ HitSink handle_sink(const ifa_handle *h) {
     s.qcount = h->d_qcount;
     s.overflow = h->d_overflow;
     s.count_only = h->cfg.count_only ? 1 : 0;
+    s.ovf_at = h->d_head + 1;
+    s.tail = h->d_head + 2;
     return s;
 }
 
@@ -558,11 +573,11 @@ namespace ifa {
 void batch_release(ifa_handle *h) {
     BatchState &B = h->batch;
     free_plan(B);
-    cudaFree(B.d_words);
+    refbufs_free(B.ref);
+    B.exc_used = 0;
     cudaFree(B.d_pieces);
     cudaFree(B.d_queue);
     cudaFree(B.d_cand);
-    B.d_words = nullptr;
     B.d_pieces = nullptr;
     B.d_queue = nullptr;
     B.d_cand = nullptr;
@@ -606,39 +621,33 @@ ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, con
     if (at != len) return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: pieces must cover the bytes");
     BCK(h, cudaSetDevice(h->dev));
     BCK(h, cudaStreamSynchronize(h->stream));
-    // grow the store (geometric), keeping the packed words
-    const uint64_t need = (B.nbases + len + 31) / 32 + kStorePad;
-    if (need > B.words_cap) {
-        const uint64_t cap = std::max<uint64_t>(need, B.words_cap + B.words_cap / 2);
-        uint4 *nw = nullptr;
-        BCK(h, cudaMalloc(&nw, cap * sizeof(uint4)));
-        if (B.d_words) {
-            cudaError_t e = cudaMemcpyAsync(nw, B.d_words, (B.nbases / 32) * sizeof(uint4), cudaMemcpyDeviceToDevice,
-                                            h->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // before the old store is freed
-            if (e != cudaSuccess) {
-                cudaFree(nw);
-                return bfail(h, IFA_ERR_CUDA, std::string("ifa_ref_append: ") + cudaGetErrorString(e));
-            }
-            cudaFree(B.d_words);
-        }
-        B.d_words = nw;
-        B.words_cap = cap;
-    }
-    // copy (via the handle's segment buffer) and pack, one segment at a time
+    // grow the store (geometric), keeping the packed words and directory
     const uint64_t seg = h->cfg.segment_bytes & ~uint64_t(31);
-    for (uint64_t off = 0; off < len; off += seg) {
-        const uint64_t c = std::min<uint64_t>(seg, len - off);
-        const uint8_t *src = ascii + off;
-        if (mem != IFA_MEM_DEVICE) {
-            BCK(h, cudaMemcpyAsync(h->d_seg[0], src, c, cudaMemcpyHostToDevice, h->stream));
-            src = h->d_seg[0];
-        }
-        const uint64_t w0 = (B.nbases + off) / 32;
-        BCK(h, launch_pack(nullptr, 0, 0, src, c, B.d_words + w0, (c + 31) / 32 + kStorePad, h->stream));
-        BCK(h, cudaStreamSynchronize(h->stream));
+    const uint64_t old_words = B.nbases / 32;
+    const uint64_t need = (B.nbases + len + 31) / 32 + kStorePad;
+    if (need > B.ref.words_cap || !B.ref.hl) {
+        const uint64_t cap = std::max<uint64_t>(need, B.ref.words_cap + B.ref.words_cap / 2);
+        uint64_t hc = B.ref.words_cap, dc = B.ref.words_cap ? dir_entries(B.ref.words_cap) : 0;
+        BCK(h, grow(B.ref.hl, hc, cap, old_words, h->stream));
+        BCK(h, grow(B.ref.dir, dc, dir_entries(cap), dir_entries(old_words + 1), h->stream));
+        B.ref.words_cap = cap;
     }
-    // pieces (a continuation extends the open piece) and their start bits
+    const uint64_t chunk_words = (std::min<uint64_t>(seg, len) + 31) / 32 + kStorePad;
+    if (chunk_words > B.ref.nb_cap) {
+        cudaFree(B.ref.nb);
+        B.ref.nb = nullptr;
+        B.ref.nb_cap = 0;
+        BCK(h, cudaMalloc(&B.ref.nb, chunk_words * sizeof(uint2)));
+        B.ref.nb_cap = chunk_words;
+    }
+    if (!B.ref.exc) {
+        uint64_t c = 0;
+        BCK(h, grow(B.ref.exc, c, std::max<uint64_t>(1u << 16, need / 64), 0, h->stream));
+        B.ref.exc_cap = c;
+        BCK(h, cudaMalloc(&B.ref.exc_n, 2 * sizeof(unsigned long long)));
+    }
+    // the new pieces (a continuation extends the open piece); their start bits
+    // go into each chunk's masks
     std::vector<DevPiece> fresh;
     for (uint32_t i = 0; i < n; i++) {
         if (i == 0 && B.open) continue;
@@ -649,17 +658,50 @@ ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, con
         d.last = pieces[i].last ? 1u : 0u;
         fresh.push_back(d);
     }
+    DevPiece *dfresh = nullptr;
+    struct FreeLater {
+        DevPiece *&p;
+        ~FreeLater() { cudaFree(p); }
+    } free_later{dfresh};
     if (!fresh.empty()) {
-        DevPiece *tmp = nullptr;
-        BCK(h, cudaMalloc(&tmp, fresh.size() * sizeof(DevPiece)));
-        cudaError_t e =
-            cudaMemcpyAsync(tmp, fresh.data(), fresh.size() * sizeof(DevPiece), cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = launch_mark_pieces(tmp, static_cast<uint32_t>(fresh.size()), B.d_words, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        cudaFree(tmp);
-        if (e != cudaSuccess) return bfail(h, IFA_ERR_CUDA, std::string("ifa_ref_append: ") + cudaGetErrorString(e));
-        B.pieces.insert(B.pieces.end(), fresh.begin(), fresh.end());
+        BCK(h, cudaMalloc(&dfresh, fresh.size() * sizeof(DevPiece)));
+        BCK(h, cudaMemcpyAsync(dfresh, fresh.data(), fresh.size() * sizeof(DevPiece), cudaMemcpyHostToDevice,
+                               h->stream));
     }
+    // copy (via the handle's segment buffer) and pack, one segment at a time
+    for (uint64_t off = 0; off < len; off += seg) {
+        const uint64_t c = std::min<uint64_t>(seg, len - off);
+        const uint8_t *src = ascii + off;
+        if (mem != IFA_MEM_DEVICE) {
+            BCK(h, cudaMemcpyAsync(h->d_seg[0], src, c, cudaMemcpyHostToDevice, h->stream));
+            src = h->d_seg[0];
+        }
+        const uint64_t w0 = (B.nbases + off) / 32;
+        const uint64_t nw = (c + 31) / 32 + kStorePad;
+        BCK(h, launch_pack(nullptr, 0, 0, src, c, B.ref.hl + w0, B.ref.nb, nw, h->stream));
+        if (!fresh.empty())
+            BCK(h, launch_mark_pieces(dfresh, static_cast<uint32_t>(fresh.size()), 32 * w0, nw, B.ref.nb, h->stream));
+        // directory and exceptions; when the exception table runs out it
+        // grows and the build runs again (it is idempotent)
+        for (;;) {
+            const unsigned long long cnt[2] = {B.exc_used, 0ull};
+            BCK(h, cudaMemcpyAsync(B.ref.exc_n, cnt, sizeof(cnt), cudaMemcpyHostToDevice, h->stream));
+            BCK(h, launch_build_dir(B.ref.nb, w0, nw, B.ref.dir, B.ref.exc, B.ref.exc_cap, B.ref.exc_n, h->stream));
+            unsigned long long got[2] = {0, 0};
+            BCK(h, cudaMemcpyAsync(got, B.ref.exc_n, sizeof(got), cudaMemcpyDeviceToHost, h->stream));
+            BCK(h, cudaStreamSynchronize(h->stream));
+            if (!got[1]) {
+                B.exc_used = got[0];
+                break;
+            }
+            // directory bases are 32-bit
+            const uint64_t want = std::min<uint64_t>(std::max<uint64_t>(2 * B.ref.exc_cap, got[0] + nw), 0xffffffffull);
+            if (want <= B.ref.exc_cap)
+                return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: more than 2^32 - 1 words hold an N or a contig start");
+            BCK(h, grow(B.ref.exc, B.ref.exc_cap, want, B.exc_used, h->stream));
+        }
+    }
+    if (!fresh.empty()) B.pieces.insert(B.pieces.end(), fresh.begin(), fresh.end());
     const ifa_piece &lp = pieces[n - 1];
     B.open = !lp.last;
     B.open_contig = lp.contig;
@@ -679,11 +721,10 @@ ifa_status ifa_ref_reset(ifa_handle *h) {
     BCK(h, cudaStreamSynchronize(h->stream));
     BatchState &B = h->batch;
     free_plan(B);
-    cudaFree(B.d_words);
+    refbufs_free(B.ref);
+    B.exc_used = 0;
     cudaFree(B.d_pieces);
-    B.d_words = nullptr;
     B.d_pieces = nullptr;
-    B.words_cap = 0;
     B.nbases = 0;
     B.pieces.clear();
     B.d_pieces_n = 0;

@@ -45,8 +45,8 @@ struct BatchWork {
 
 struct BatchState {
     // reference store
-    uint4 *d_words = nullptr;
-    uint64_t words_cap = 0;
+    RefBufs ref;               // the store: 2-bit words, directory, exceptions (nb: one chunk's scratch)
+    uint64_t exc_used = 0;     // exception entries in use
     uint64_t nbases = 0;
     std::vector<DevPiece> pieces;
     DevPiece *d_pieces = nullptr;

@@ -22,7 +22,7 @@ namespace {
 thread_local std::string g_err = "no error";
 
 constexpr uint32_t kHaloCap = 256;   // >= halo region H = 32 * ceil((IFA_MAX_QUERY_LEN - 1) / 32)
-constexpr uint64_t kWordPad = 16;    // zeroed words after the last packed word
+constexpr uint64_t kWordPad = 16;    // padding words after the last packed word (packed as N)
 
 }  // namespace
 
@@ -154,7 +154,59 @@ HitSink make_sink(const ifa_handle *h) {
     s.qcount = h->d_qcount;
     s.overflow = h->d_overflow;
     s.count_only = h->cfg.count_only ? 1 : 0;
+    s.ovf_at = h->d_head + 1;
+    s.tail = h->d_head + 2;
     return s;
+}
+
+// Fold the completed segment marks, oldest first (all of them, waiting, when
+// `wait`).
+ifa_status collect_marks(ifa_handle *h, bool wait) {
+    size_t i = 0;
+    for (; i < h->marks_pending.size(); i++) {
+        const int k = h->marks_pending[i];
+        cudaError_t e = wait ? cudaEventSynchronize(h->ev_mark[k]) : cudaEventQuery(h->ev_mark[k]);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) return fail_cuda(h, "segment mark", e);
+        h->done_head = h->h_marks[2 * k];
+        h->done_ovf = h->h_marks[2 * k + 1];
+    }
+    h->marks_pending.erase(h->marks_pending.begin(), h->marks_pending.begin() + i);
+    return IFA_OK;
+}
+
+// Copy ring claims [tail, min(end, tail + cap)) to out (host) on the drain
+// stream, then advance the device tail (after the copies, same stream) so
+// producers may reuse the slots.  Waits for the drain stream only.
+ifa_status drain_span(ifa_handle *h, ifa_hit *out, uint64_t cap, uint64_t end, uint64_t *n_out) {
+    *n_out = 0;
+    if (end <= h->tail || cap == 0) return IFA_OK;
+    const uint64_t C = h->cfg.hit_capacity;
+    const uint64_t take = std::min<uint64_t>(end - h->tail, cap);
+    const uint64_t pos = h->tail % C;
+    const uint64_t n1 = std::min<uint64_t>(take, C - pos);
+    CK(h, cudaMemcpyAsync(out, h->d_ring + pos, n1 * sizeof(ifa_hit), cudaMemcpyDeviceToHost, h->drain_stream));
+    if (take > n1)
+        CK(h, cudaMemcpyAsync(out + n1, h->d_ring, (take - n1) * sizeof(ifa_hit), cudaMemcpyDeviceToHost,
+                              h->drain_stream));
+    h->tail += take;
+    unsigned long long *ht = h->h_marks + 2 * ifa_handle::kMarks;
+    *ht = h->tail;
+    CK(h, cudaMemcpyAsync(h->d_head + 2, ht, sizeof(unsigned long long), cudaMemcpyHostToDevice, h->drain_stream));
+    CK(h, cudaStreamSynchronize(h->drain_stream));
+    *n_out = take;
+    return IFA_OK;
+}
+
+// Reset the ring counters on the compute stream (head 0, none dropped, tail 0).
+ifa_status reset_ring(ifa_handle *h) {
+    CK(h, cudaMemsetAsync(h->d_head, 0, 3 * sizeof(unsigned long long), h->stream));
+    CK(h, cudaMemsetAsync(h->d_head + 1, 0xff, sizeof(unsigned long long), h->stream));
+    h->tail = 0;
+    h->done_head = 0;
+    h->done_ovf = ~0ull;
+    h->marks_pending.clear();
+    return IFA_OK;
 }
 
 ifa_status sync_all(ifa_handle *h) {
@@ -325,8 +377,8 @@ ifa_status ifa_create(const ifa_config *cfg, ifa_handle **out) {
     CKC(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
     h->stream = h->own_stream;
     const uint64_t sb = cfg->segment_bytes;
-    h->words_cap = (sb + kHaloCap + 31) / 32 + kWordPad;
-    CKC(cudaMalloc(&h->d_words, h->words_cap * sizeof(uint4)));
+    const uint64_t words = (sb + kHaloCap + 31) / 32 + kWordPad;
+    CKC(refbufs_alloc(h->ref, words, words, words));
     for (int i = 0; i < 2; i++) {
         CKC(cudaMalloc(&h->d_seg[i], sb));
         CKC(cudaMalloc(&h->d_halo[i], kHaloCap));
@@ -334,10 +386,14 @@ ifa_status ifa_create(const ifa_config *cfg, ifa_handle **out) {
         CKC(cudaEventCreateWithFlags(&h->ev_consumed[i], cudaEventDisableTiming));
     }
     if (!cfg->count_only) CKC(cudaMalloc(&h->d_ring, cfg->hit_capacity * sizeof(ifa_hit)));
-    CKC(cudaMalloc(&h->d_head, sizeof(unsigned long long)));
+    CKC(cudaMalloc(&h->d_head, 3 * sizeof(unsigned long long)));
     CKC(cudaMalloc(&h->d_overflow, sizeof(uint32_t)));
     CKC(cudaMalloc(&h->d_digest, 3 * sizeof(unsigned long long)));
-    CKC(cudaMemsetAsync(h->d_head, 0, sizeof(unsigned long long), h->stream));
+    CKC(cudaStreamCreateWithFlags(&h->drain_stream, cudaStreamNonBlocking));
+    CKC(cudaHostAlloc(&h->h_marks, (2 * ifa_handle::kMarks + 1) * sizeof(unsigned long long), cudaHostAllocDefault));
+    for (int i = 0; i < ifa_handle::kMarks; i++)
+        CKC(cudaEventCreateWithFlags(&h->ev_mark[i], cudaEventDisableTiming));
+    if (reset_ring(h) != IFA_OK) return bail(IFA_ERR_CUDA);
     CKC(cudaMemsetAsync(h->d_overflow, 0, sizeof(uint32_t), h->stream));
     CKC(cudaMemsetAsync(h->d_digest, 0, 3 * sizeof(unsigned long long), h->stream));
 #undef CKC
@@ -370,13 +426,18 @@ void ifa_destroy(ifa_handle *h) {
             cudaEventDestroy(ev.first);
             cudaEventDestroy(ev.second);
         }
-    cudaFree(h->d_words);
+    refbufs_free(h->ref);
     cudaFree(h->d_qwords);
     cudaFree(h->d_qmeta);
     cudaFree(h->d_tcA);
     cudaFree(h->d_tc_status);
     cudaFree(h->d_ring);
     cudaFree(h->d_head);
+    if (h->drain_stream) cudaStreamSynchronize(h->drain_stream);
+    cudaFreeHost(h->h_marks);
+    for (int i = 0; i < ifa_handle::kMarks; i++)
+        if (h->ev_mark[i]) cudaEventDestroy(h->ev_mark[i]);
+    if (h->drain_stream) cudaStreamDestroy(h->drain_stream);
     cudaFree(h->d_overflow);
     cudaFree(h->d_digest);
     cudaFree(h->d_qcount);
@@ -515,18 +576,9 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
     const uint64_t nbases = H + len;
     const uint64_t nwords = (nbases + 31) / 32 + kWordPad;
     int launches = 0;
-    CK(h, launch_pack(h->d_halo[h->halo_cur], hlen, H, dsrc, len, h->d_words, nwords, h->stream));
-    launches++;
-    if (n > 1 || H > hlen) {
-        CK(h, launch_mark_pieces(h->d_pieces[slot], n, h->d_words, h->stream));
-        launches++;
-    }
-    Batch b;
-    b.words = h->d_words;
-    b.nbases = nbases;
-    b.halo = H;
-    b.pieces = h->d_pieces[slot];
-    b.npieces = n;
+    CK(h, pack_batch(h->ref, h->d_halo[h->halo_cur], hlen, H, dsrc, len, nwords, h->d_pieces[slot], n,
+                     n > 1 || H > hlen, h->stream, &launches));
+    const Batch b = make_batch(h->ref, nbases, H, h->d_pieces[slot], n);
     QueryTable qt;
     qt.words = h->d_qwords;
     qt.meta = h->d_qmeta;
@@ -585,6 +637,24 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
     h->any_contig = true;
     h->last_contig = lp.contig;
     h->pushed = true;
+    if (!h->cfg.count_only) {
+        // the ring's head after this segment's scan, for ifa_poll_hits
+        if (static_cast<int>(h->marks_pending.size()) == ifa_handle::kMarks) {
+            st = collect_marks(h, false);
+            if (st != IFA_OK) return st;
+            if (static_cast<int>(h->marks_pending.size()) == ifa_handle::kMarks) {
+                CK(h, cudaEventSynchronize(h->ev_mark[h->marks_pending.front()]));
+                st = collect_marks(h, false);
+                if (st != IFA_OK) return st;
+            }
+        }
+        const int k = h->mark_next;
+        h->mark_next = (k + 1) % ifa_handle::kMarks;
+        CK(h, cudaMemcpyAsync(h->h_marks + 2 * k, h->d_head, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                              h->stream));
+        CK(h, cudaEventRecord(h->ev_mark[k], h->stream));
+        h->marks_pending.push_back(k);
+    }
     CK(h, cudaEventRecord(h->ev_consumed[slot], h->stream));
     h->slot_used[slot] = true;
     if (mem == IFA_MEM_HOST_PINNED) CK(h, cudaEventSynchronize(h->ev_copied[slot]));
@@ -666,24 +736,44 @@ ifa_status ifa_drain_hits(ifa_handle *h, ifa_hit *out, uint64_t cap, uint64_t *n
     if (st != IFA_OK && st != IFA_ERR_HIT_OVERFLOW) return st;
     const ifa_status ret = st;
     if (h->cfg.count_only) return ret;
-    unsigned long long head = 0;
-    CK(h, cudaMemcpy(&head, h->d_head, sizeof(head), cudaMemcpyDeviceToHost));
-    const uint64_t total = std::min<uint64_t>(head, h->cfg.hit_capacity);
-    const uint64_t avail = total - h->drained;
-    const uint64_t take = std::min<uint64_t>(avail, cap);
-    if (take) {
-        CK(h, cudaMemcpy(out, h->d_ring + h->drained, take * sizeof(ifa_hit), cudaMemcpyDeviceToHost));
-        h->drained += take;
-    }
-    *n_out = take;
-    const bool left = h->drained < total;
+    // the device is idle: every claim is written
+    unsigned long long ctr[2] = {0, 0};
+    CK(h, cudaMemcpy(ctr, h->d_head, sizeof(ctr), cudaMemcpyDeviceToHost));
+    h->marks_pending.clear();
+    h->done_head = ctr[0];
+    h->done_ovf = ctr[1];
+    const uint64_t end = std::min<uint64_t>(ctr[0], ctr[1]);
+    st = drain_span(h, out, cap, end, n_out);
+    if (st != IFA_OK) return st;
+    const bool left = h->tail < end;
     if (more) *more = left ? 1 : 0;
-    if (!left && total > 0) {
-        CK(h, cudaMemsetAsync(h->d_head, 0, sizeof(unsigned long long), h->stream));
-        CK(h, cudaStreamSynchronize(h->stream));
-        h->drained = 0;
+    if (!left && ctr[1] != ~0ull) {
+        // everything before the first dropped claim is out: skip the claims
+        // after it (dropped or not, they are part of the overflow) and
+        // re-arm the ring
+        h->tail = ctr[0];
+        h->done_ovf = ~0ull;
+        const unsigned long long rearm[2] = {~0ull, ctr[0]};
+        CK(h, cudaMemcpy(h->d_head + 1, rearm, sizeof(rearm), cudaMemcpyHostToDevice));
     }
     return ret;
+}
+
+ifa_status ifa_poll_hits(ifa_handle *h, ifa_hit *out, uint64_t cap, uint64_t *n_out, int *more) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    if (!n_out || (cap && !out)) return fail(h, IFA_ERR_INVALID_ARG, "out/n_out is NULL");
+    *n_out = 0;
+    if (more) *more = 0;
+    if (h->cfg.count_only) return IFA_OK;
+    CK(h, cudaSetDevice(h->dev));
+    ifa_status st = collect_marks(h, false);
+    if (st != IFA_OK) return st;
+    const uint64_t end = std::min<uint64_t>(h->done_head, h->done_ovf);
+    st = drain_span(h, out, cap, end, n_out);
+    if (st != IFA_OK) return st;
+    if (more) *more = h->tail < end ? 1 : 0;
+    return h->done_ovf != ~0ull ? fail(h, IFA_ERR_HIT_OVERFLOW, "hit ring overflowed; some hit tuples were dropped")
+                                : IFA_OK;
 }
 
 ifa_status ifa_get_digest(ifa_handle *h, ifa_digest *d, uint64_t *per_query_counts) {
@@ -708,13 +798,13 @@ ifa_status ifa_reset_results(ifa_handle *h) {
     ifa_status st = sync_all(h);
     if (st != IFA_OK) return st;
     // on the compute stream, so the next pass's kernels see the zeros
-    CK(h, cudaMemsetAsync(h->d_head, 0, sizeof(unsigned long long), h->stream));
+    st = reset_ring(h);
+    if (st != IFA_OK) return st;
     CK(h, cudaMemsetAsync(h->d_overflow, 0, sizeof(uint32_t), h->stream));
     CK(h, cudaMemsetAsync(h->d_digest, 0, 3 * sizeof(unsigned long long), h->stream));
     if (h->d_qcount)
         CK(h, cudaMemsetAsync(h->d_qcount, 0, std::max<size_t>(1, h->qs.size()) * sizeof(unsigned long long),
                               h->stream));
-    h->drained = 0;
     h->open = false;
     h->halo_len = 0;
     h->any_contig = false;

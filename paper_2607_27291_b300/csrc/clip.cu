@@ -24,16 +24,16 @@ constexpr int kClipThreads = 256;
 
 // The 32 bases of the batch starting at x (which may be negative: bases
 // before the batch read as zero words; they are masked by the caller).
-__device__ __forceinline__ uint4 bases32(const uint4 *__restrict__ words, int64_t x) {
+__device__ __forceinline__ uint4 bases32(const Batch &b, int64_t x) {
     if (x <= -32) return make_uint4(0u, 0u, 0u, 0u);
     if (x < 0) {
-        const uint4 w = __ldg(words);
+        const uint4 w = ref_word(b, 0);
         const uint32_t sh = static_cast<uint32_t>(-x);
         return make_uint4(w.x << sh, w.y << sh, w.z << sh, 0u);
     }
     const uint64_t wi = static_cast<uint64_t>(x) >> 5;
     const uint32_t sh = static_cast<uint32_t>(x & 31);
-    const uint4 a = __ldg(words + wi), c = __ldg(words + wi + 1);
+    const uint4 a = ref_word(b, wi), c = ref_word(b, wi + 1);
     return make_uint4(__funnelshift_r(a.x, c.x, sh), __funnelshift_r(a.y, c.y, sh), __funnelshift_r(a.z, c.z, sh),
                       0u);
 }
@@ -51,7 +51,7 @@ __device__ __forceinline__ uint32_t clipped_mismatches(const Batch &b, const uin
         if (hi < j0 + 32u) amask &= (1u << (hi - j0)) - 1u;
         if (!amask) continue;
         const uint4 q = qw[j];
-        const uint4 r = bases32(b.words, p + j0);
+        const uint4 r = bases32(b, p + j0);
         mm += __popc(amask & (~q.z | r.z | (r.x ^ q.x) | (r.y ^ q.y)));
     }
     return mm;

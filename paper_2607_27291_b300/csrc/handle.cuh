@@ -60,16 +60,26 @@ struct ifa_handle {
     int halo_cur = 0;
     uint32_t halo_len = 0;
 
-    uint4 *d_words = nullptr;
-    uint64_t words_cap = 0;
+    ifa::RefBufs ref;  // the packed batch (2-bit words, directory, exceptions)
 
-    // results
+    // results: the device hit ring and its counters d_head = {head (claims),
+    // first dropped claim (~0 when none), tail (drained, written by the host)}
     ifa_hit *d_ring = nullptr;
     unsigned long long *d_head = nullptr;
     uint32_t *d_overflow = nullptr;
     unsigned long long *d_digest = nullptr;
     unsigned long long *d_qcount = nullptr;
-    uint64_t drained = 0;
+    uint64_t tail = 0;                       // hits drained from the ring
+    // per pushed segment, a pinned copy of {head, first dropped claim} taken
+    // on the compute stream after its scan, and an event: once the event has
+    // completed, every claim below that head is written
+    static constexpr int kMarks = 8;
+    unsigned long long *h_marks = nullptr;   // pinned: kMarks x 2, then the tail word for uploads
+    cudaEvent_t ev_mark[kMarks] = {};
+    std::vector<int> marks_pending;          // oldest first
+    int mark_next = 0;
+    uint64_t done_head = 0, done_ovf = ~0ull;  // from the latest completed mark
+    cudaStream_t drain_stream = nullptr;     // ring-to-host copies and tail uploads
 
     // stream position
     bool open = false;

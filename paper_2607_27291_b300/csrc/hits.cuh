@@ -33,6 +33,34 @@ constexpr uint32_t kEventBlock = 128;
 //    its hitting windows and their mismatch counts, staged as 16 bytes.  The
 //    flush expands events into hits with the warp converged: piece lookup,
 //    query id, digest, one slot claim per flush.
+//
+// Claims [base, base + n) of the shared buffer (warp-uniform): the first
+// claim's position in the buffer, and the room left before the first claim
+// that must be dropped (see HitSink).
+struct Claim {
+    unsigned long long pos;   // buffer position of claim `base`
+    unsigned long long room;  // claims base .. base + room - 1 may be stored
+};
+
+__device__ __forceinline__ Claim claim_room(const HitSink &s, unsigned long long base) {
+    Claim c;
+    if (s.tail) {
+        const unsigned long long t = *reinterpret_cast<const volatile unsigned long long *>(s.tail);
+        c.room = base - t < s.capacity ? s.capacity - (base - t) : 0ull;
+        c.pos = base % s.capacity;
+    } else {
+        c.room = base < s.capacity ? s.capacity - base : 0ull;
+        c.pos = base;
+    }
+    return c;
+}
+
+// Record a dropped claim (any lane).
+__device__ __forceinline__ void drop_claim(const HitSink &s, unsigned long long idx) {
+    *s.overflow = 1u;
+    if (s.ovf_at) atomicMin(s.ovf_at, idx);
+}
+
 template <bool MULTI>
 struct WarpHitsT {
     ifa_hit *buf;          // this warp's 32 staged hits (shared memory, 16-byte aligned:
@@ -61,16 +89,24 @@ struct WarpHitsT {
             __syncwarp();
             return;
         }
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(s.head, static_cast<unsigned long long>(n));
+        unsigned long long base = 0, pos = 0, room = 0;
+        if (lane == 0) {
+            base = atomicAdd(s.head, static_cast<unsigned long long>(n));
+            const Claim c = claim_room(s, base);
+            pos = c.pos;
+            room = c.room;
+        }
         base = __shfl_sync(0xffffffffu, base, 0);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        room = __shfl_sync(0xffffffffu, room, 0);
         if (lane < n) {
-            unsigned long long idx = base + lane;
-            if (idx < s.capacity) {
+            if (lane < room) {
+                unsigned long long at = pos + lane;
+                if (at >= s.capacity) at %= s.capacity;   // ring wrap (room <= capacity)
                 const uint4 v = reinterpret_cast<const uint4 *>(buf)[lane];
-                reinterpret_cast<uint4 *>(s.ring)[idx] = v;
-            } else {
-                *s.overflow = 1u;
+                reinterpret_cast<uint4 *>(s.ring)[at] = v;
+            } else if (lane == room) {
+                drop_claim(s, base + lane);   // the first dropped claim of this flush
             }
         }
         n = 0;
@@ -166,7 +202,10 @@ struct WarpHitsT {
         __syncwarp();
         uint32_t hm = ev.w & 0x80808080u;
         const uint32_t nh = __popc(hm);
-        unsigned long long slot = 0;
+        // this lane's claims are offsets off .. off + nh - 1 of the warp's
+        // claim; offsets below `room` are stored, from buffer position `at`
+        unsigned long long at = 0, room = 0;
+        uint32_t off = 0;
         if (!MULTI && !s.count_only) {
             // one claim of global slots for the warp's hits
             uint32_t inc = nh;
@@ -176,9 +215,21 @@ struct WarpHitsT {
                 if (lane >= static_cast<uint32_t>(o)) inc += y;
             }
             const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
-            unsigned long long base = 0;
-            if (lane == 31 && total) base = atomicAdd(s.head, static_cast<unsigned long long>(total));
-            slot = __shfl_sync(0xffffffffu, base, 31) + (inc - nh);
+            unsigned long long base = 0, pos = 0;
+            if (lane == 31 && total) {
+                base = atomicAdd(s.head, static_cast<unsigned long long>(total));
+                const Claim c = claim_room(s, base);
+                pos = c.pos;
+                room = c.room;
+            }
+            base = __shfl_sync(0xffffffffu, base, 31);
+            pos = __shfl_sync(0xffffffffu, pos, 31);
+            room = __shfl_sync(0xffffffffu, room, 31);
+            off = inc - nh;
+            at = pos + off;
+            if (at >= s.capacity) at %= s.capacity;
+            // the lane holding the warp's first claim without room reports it
+            if (room < total && room >= off && room < off + nh) drop_claim(s, base + room);
         }
         if (nh) {
             const uint32_t e = ev.x & 0xffffu, el = ev.x >> 16;
@@ -207,7 +258,7 @@ struct WarpHitsT {
                     dsum += v;
                     dxor ^= v;
                     if (!s.count_only) {
-                        if (slot < s.capacity) {
+                        if (off < room) {
                             ifa_hit h;
                             h.query = q;
                             h.contig = pc.contig;
@@ -215,11 +266,10 @@ struct WarpHitsT {
                             h.strand = static_cast<uint8_t>(strand);
                             h.mismatches = static_cast<uint8_t>(mm);
                             h.clips = 0;
-                            s.ring[slot] = h;
-                        } else {
-                            *s.overflow = 1u;
+                            s.ring[at] = h;
                         }
-                        slot++;
+                        off++;
+                        if (++at == s.capacity) at = 0;
                     }
                 }
             }

@@ -1,15 +1,22 @@
 // ifa_internal.cuh -- device-side layouts shared by the kernels and the host engine.
 //
-// Reference layout in HBM ("packed words"): base i of a batch lives in bit
-// (i & 31) of word i >> 5 of four planes, stored interleaved as one uint4
-// per 32 bases:
-//   .x  hi plane   (code >> 1)
-//   .y  lo plane   (code & 1)
-//   .z  N plane    (1 where the byte is not A/C/G/T)
-//   .w  B plane    (1 at the first base of every contig piece not at base 0)
+// Reference layout in HBM ("2-bit store"): base i of a batch lives in bit
+// (i & 31) of word i >> 5 of two planes, stored interleaved as one uint2 per
+// 32 bases,
+//   hl[w] = {hi plane (code >> 1), lo plane (code & 1)},
 // with code A=0, C=1, T=2, G=3 (the byte's bits 1..2), so the complement of
-// a base is code ^ 2.  One 16-byte load gives a thread all four planes of
-// 32 bases; 0.5 byte per base.
+// a base is code ^ 2.  That is 0.25 byte per base.  Two more planes exist
+// only where they are not zero, in a sparse table:
+//   N plane  1 where the byte is not A/C/G/T (its hi/lo bits are 0),
+//   B plane  1 at the first base of every contig piece not at base 0.
+// A word with a bit in either ("special": N runs and contig starts, a
+// fraction of a percent of the words) has an entry {N mask, B mask} in exc;
+// dir holds one {bitmap, base} per group of 32 words: bit j of the bitmap
+// says word 32 g + j is special, and its entry is
+//   exc[base + popc(bitmap & ((1 << j) - 1))].
+// ref_word() rebuilds the four planes of any word; the scans stage only hl
+// and read dir to send the few blocks with special words down their
+// generic paths.
 //
 // Query table ("entries"): entry e = 2*q + t holds query q on strand t
 // (t = 1: reverse complement, precomputed) as WMAX uint4 words
@@ -86,6 +93,12 @@ struct DevBufs {
     }
 };
 
+// Where hits go.  With `tail` set the buffer is a ring: claim idx (from
+// `head`, which only grows) is stored at idx % capacity while
+// idx - *tail < capacity, *tail being the count the host has drained; a
+// claim that finds no room is dropped, raises `overflow` and lowers
+// *ovf_at (the first dropped claim) so the host never drains past a hole.
+// Without `tail` the buffer is linear: claims below capacity are stored.
 struct HitSink {
     ifa_hit *ring;                 // hit buffer (may be null in count-only mode)
     unsigned long long *head;      // total hits claimed (can exceed capacity)
@@ -97,6 +110,8 @@ struct HitSink {
     // serving: query -> request slot and the slots' rings (null: one shared ring)
     const uint32_t *q2r = nullptr;
     const RingDesc *rings = nullptr;
+    const unsigned long long *tail = nullptr;  // ring mode: hits drained so far (host-written)
+    unsigned long long *ovf_at = nullptr;      // ring mode: first dropped claim (~0 when none)
 };
 
 struct QueryTable {
@@ -108,11 +123,48 @@ struct QueryTable {
 };
 
 struct Batch {
-    const uint4 *words;       // packed planes, >= nbases/32 + 9 words, padding zeroed
+    const uint2 *hl;          // hi/lo planes, >= nbases/32 + 16 words (padding words are N)
+    const uint2 *dir;         // one {special bitmap, exc base} per 32 words, >= hl's words/32 + 2 groups
+    const uint2 *exc;         // {N mask, B mask} of each special word
     uint64_t nbases;          // halo region + segment
     uint32_t halo;            // halo region length H; windows must end at or after base H
     const DevPiece *pieces;
     uint32_t npieces;
+};
+
+// The four planes {hi, lo, N, B} of word w.
+__device__ __forceinline__ uint4 ref_word(const Batch &b, uint64_t w) {
+    const uint2 a = __ldg(b.hl + w);
+    const uint2 d = __ldg(b.dir + (w >> 5));
+    const uint32_t bit = 1u << (w & 31u);
+    uint32_t n = 0, s = 0;
+    if (d.x & bit) {
+        const uint2 x = __ldg(b.exc + d.y + __popc(d.x & (bit - 1u)));
+        n = x.x;
+        s = x.y;
+    }
+    return make_uint4(a.x, a.y, n, s);
+}
+
+// Special bits of words w .. w + n - 1 (n <= 32) from two directory
+// entries g = w >> 5 and g + 1; nonzero when any of them holds an N or a
+// piece start.
+__device__ __forceinline__ uint32_t special_bits(uint32_t d0, uint32_t d1, uint64_t w, uint32_t n) {
+    const uint64_t both = static_cast<uint64_t>(d0) | (static_cast<uint64_t>(d1) << 32);
+    const uint32_t x = static_cast<uint32_t>(both >> (w & 31u));
+    return n >= 32u ? x : x & ((1u << n) - 1u);
+}
+
+// Device buffers of one packed reference (a streamed batch or the store).
+struct RefBufs {
+    uint2 *hl = nullptr;
+    uint2 *nb = nullptr;      // scratch: {N, B} masks of the words being packed
+    uint2 *dir = nullptr;
+    uint2 *exc = nullptr;
+    unsigned long long *exc_n = nullptr;  // [0] entries used, [1] set when an append ran out of room
+    uint64_t words_cap = 0;   // hl words
+    uint64_t nb_cap = 0;      // nb words
+    uint64_t exc_cap = 0;     // exc entries
 };
 
 __host__ __device__ inline uint64_t mix64(uint64_t z) {
@@ -159,9 +211,33 @@ cudaError_t launch_scan_tc(const Batch &b, const uint8_t *tcA, const uint32_t *m
                            uint32_t s, const HitSink &sink, unsigned int *status, cudaStream_t st,
                            uint32_t withhold_first = 0);
 
+// ASCII -> hl words [0, nwords_padded) and their {N, B = 0} masks in nb.
 cudaError_t launch_pack(const uint8_t *halo, uint32_t hlen, uint32_t H, const uint8_t *seg,
-                        uint64_t slen, uint4 *words, uint64_t nwords_padded, cudaStream_t st);
-cudaError_t launch_mark_pieces(const DevPiece *pieces, uint32_t n, uint4 *words, cudaStream_t st);
+                        uint64_t slen, uint2 *hl, uint2 *nb, uint64_t nwords_padded, cudaStream_t st);
+// B bits of the pieces starting among nb's nwords words (nb[0] holds base `first`).
+cudaError_t launch_mark_pieces(const DevPiece *pieces, uint32_t n, uint64_t first, uint64_t nwords, uint2 *nb,
+                               cudaStream_t st);
+// Directory and exception entries of words [w0, w0 + n) from their masks nb[0 .. n); words of
+// w0's group below w0 keep theirs (read back through the old directory entry).  Entries are
+// taken from exc_n[0]; when they would pass exc_cap nothing of a group is written and exc_n[1]
+// is set (grow exc, then run it again: the call is idempotent).
+cudaError_t launch_build_dir(const uint2 *nb, uint64_t w0, uint64_t n, uint2 *dir, uint2 *exc, uint64_t exc_cap,
+                             unsigned long long *exc_n, cudaStream_t st);
+// Directory entries a reference of `words` hi/lo words needs (its groups,
+// the group after the last that k_build_dir writes, and one more that a
+// reader of two neighbouring entries may touch).
+inline uint64_t dir_entries(uint64_t words) { return (words + 31) / 32 + 3; }
+// Allocate hl (words), nb (nb_words), dir and exc (exc_entries) and the
+// two-word entry counter.
+cudaError_t refbufs_alloc(RefBufs &R, uint64_t words, uint64_t nb_words, uint64_t exc_entries);
+void refbufs_free(RefBufs &R);
+// Pack one streamed batch into R: halo region + segment -> words [0, nwords),
+// piece starts marked when `mark`, directory and exceptions built (R.exc_cap
+// >= nwords).  Adds its kernel launches to *launches.
+cudaError_t pack_batch(const RefBufs &R, const uint8_t *halo, uint32_t hlen, uint32_t H, const uint8_t *seg,
+                       uint64_t slen, uint64_t nwords, const DevPiece *pieces, uint32_t npieces, bool mark,
+                       cudaStream_t st, int *launches);
+Batch make_batch(const RefBufs &R, uint64_t nbases, uint32_t halo, const DevPiece *pieces, uint32_t npieces);
 cudaError_t launch_halo_update(const uint8_t *old_halo, uint32_t old_len, const uint8_t *seg,
                                uint64_t slen, uint32_t new_len, uint8_t *new_halo, cudaStream_t st);
 

@@ -7,7 +7,7 @@
 // entry point that takes the caller's input and output buffers and keeps
 // all of its scratch -- the packed reference planes, the encoded query
 // table, the piece table and the per-query counts -- in a file-scope
-// device array of fixed size (about 17 MB).
+// device array of fixed size (about 26 MB).
 //
 // When the array takes its device memory: the array belongs to this file's
 // CUDA module, and the runtime loads a module into a context when it is
@@ -38,10 +38,17 @@ constexpr uint32_t kNaMaxPieces = 1u << 15;    // contigs per call
 constexpr uint32_t kNaWmax = 8;                // words per query entry (255 bp)
 constexpr uint64_t kNaWords = kNaMaxBases / 32 + 16;
 
-// Byte offsets of the parts inside the scratch array (256-aligned each).
+// Byte offsets of the parts inside the scratch array (256-aligned each):
+// the packed reference (2-bit words, their mask scratch, directory,
+// exception entries and counter), the query table, the piece table and the
+// per-query counts.
 constexpr uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
-constexpr uint64_t kOffWords = 0;
-constexpr uint64_t kOffQWords = align256(kOffWords + kNaWords * sizeof(uint4));
+constexpr uint64_t kOffHl = 0;
+constexpr uint64_t kOffNb = align256(kOffHl + kNaWords * sizeof(uint2));
+constexpr uint64_t kOffDir = align256(kOffNb + kNaWords * sizeof(uint2));
+constexpr uint64_t kOffExc = align256(kOffDir + ((kNaWords + 31) / 32 + 3) * sizeof(uint2));
+constexpr uint64_t kOffExcN = align256(kOffExc + kNaWords * sizeof(uint2));
+constexpr uint64_t kOffQWords = align256(kOffExcN + 2 * sizeof(unsigned long long));
 constexpr uint64_t kOffQMeta = align256(kOffQWords + 2ull * kNaMaxQueries * kNaWmax * sizeof(uint4));
 constexpr uint64_t kOffPieces = align256(kOffQMeta + 2ull * kNaMaxQueries * sizeof(uint32_t));
 constexpr uint64_t kOffQCount = align256(kOffPieces + uint64_t(kNaMaxPieces) * sizeof(DevPiece));
@@ -169,7 +176,13 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
         base = g_na_addr[device];
     }
     if (setup_only) return IFA_OK;
-    uint4 *words = reinterpret_cast<uint4 *>(base + kOffWords);
+    RefBufs ref;
+    ref.hl = reinterpret_cast<uint2 *>(base + kOffHl);
+    ref.nb = reinterpret_cast<uint2 *>(base + kOffNb);
+    ref.dir = reinterpret_cast<uint2 *>(base + kOffDir);
+    ref.exc = reinterpret_cast<uint2 *>(base + kOffExc);
+    ref.exc_n = reinterpret_cast<unsigned long long *>(base + kOffExcN);
+    ref.words_cap = ref.nb_cap = ref.exc_cap = kNaWords;
     uint4 *qwords = reinterpret_cast<uint4 *>(base + kOffQWords);
     uint32_t *qmeta = reinterpret_cast<uint32_t *>(base + kOffQMeta);
     DevPiece *dpieces = reinterpret_cast<DevPiece *>(base + kOffPieces);
@@ -206,14 +219,8 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
     ck(cudaMemsetAsync(qc, 0, nq * sizeof(unsigned long long), st));
     ck(cudaMemsetAsync(counters_device, 0, 5 * sizeof(uint64_t), st));
     const uint64_t nwords = (len + 31) / 32 + 16;
-    ck(launch_pack(nullptr, 0, 0, ref_device, len, words, nwords, st));
-    ck(launch_mark_pieces(dpieces, n_pieces, words, st));
-    Batch b;
-    b.words = words;
-    b.nbases = len;
-    b.halo = 0;
-    b.pieces = dpieces;
-    b.npieces = n_pieces;
+    if (e == cudaSuccess) e = pack_batch(ref, nullptr, 0, 0, ref_device, len, nwords, dpieces, n_pieces, true, st, nullptr);
+    const Batch b = make_batch(ref, len, 0, dpieces, n_pieces);
     QueryTable qt;
     qt.words = qwords;
     qt.meta = qmeta;

@@ -1,4 +1,5 @@
-// pack.cu -- reference packing on the device (ASCII -> 2-bit planes + N + piece starts).
+// pack.cu -- reference packing on the device (ASCII -> 2-bit planes, and a
+// sparse table of the words holding an N or a piece start).
 //
 // The reference is streamed as ASCII and never pre-indexed (Methods,
 // "Algorithm Design"); each pushed segment is packed here, in HBM, right
@@ -6,6 +7,11 @@
 // of 32: 'N' padding, then the last <= L_max - 1 bases of a contig that
 // continues from the previous segment) followed by the new segment, which
 // therefore starts on a word boundary and is read with aligned vectors.
+//
+// Three steps: k_pack writes the hi/lo words and every word's N mask into a
+// scratch array; k_mark_pieces adds the piece-start (B) bits there;
+// k_build_dir turns the scratch into the directory (one bitmap per 32 words)
+// and the exception entries of the special words (see ifa_internal.cuh).
 #include "ifa_internal.cuh"
 
 namespace ifa {
@@ -52,7 +58,7 @@ __device__ __forceinline__ void pack4(uint32_t u, uint32_t &h4, uint32_t &l4, ui
 template <bool ALIGNED>
 __global__ void __launch_bounds__(kPackThreads)
 k_pack(const uint8_t *__restrict__ halo, uint32_t hlen, uint32_t H, const uint8_t *__restrict__ seg,
-       uint64_t slen, uint4 *__restrict__ words, uint64_t nwords) {
+       uint64_t slen, uint2 *__restrict__ hl, uint2 *__restrict__ nb, uint64_t nwords) {
     const uint64_t w = static_cast<uint64_t>(blockIdx.x) * kPackThreads + threadIdx.x;
     if (w >= nwords) return;
     uint32_t hi = 0, lo = 0, nn = 0;
@@ -84,17 +90,55 @@ k_pack(const uint8_t *__restrict__ halo, uint32_t hlen, uint32_t H, const uint8_
                 pack_byte(o + b < slen ? seg[o + b] : 'N', b, hi, lo, nn);
         }
     }
-    words[w] = make_uint4(hi, lo, nn, 0u);
+    hl[w] = make_uint2(hi, lo);
+    nb[w] = make_uint2(nn, 0u);
 }
 
-// B plane: a bit at the first base of every piece that does not start the batch.
-__global__ void k_mark_pieces(const DevPiece *__restrict__ pc, uint32_t n, uint4 *__restrict__ words) {
+// B plane: a bit at the first base of every piece that does not start the
+// batch, for the pieces starting among the nwords words from base `first`.
+__global__ void k_mark_pieces(const DevPiece *__restrict__ pc, uint32_t n, uint64_t first, uint64_t nwords,
+                              uint2 *__restrict__ nb) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint64_t p = pc[i].start;
-    if (p == 0) return;
-    uint32_t *w = reinterpret_cast<uint32_t *>(words + (p >> 5)) + 3;
-    atomicOr(w, 1u << (p & 31));
+    if (p == 0 || p < first || p - first >= 32 * nwords) return;
+    atomicOr(&nb[(p - first) >> 5].y, 1u << ((p - first) & 31));
+}
+
+// One warp per group of 32 words: ballot of the special words, one range of
+// exception entries per group (taken from exc_n[0]), the group's entries in
+// word order.  Words of the first group below w0 keep their old masks,
+// read through the old directory entry.  The last group written is one past
+// the words' last group (all zero), so that a reader of two neighbouring
+// entries never meets an unwritten one.
+__global__ void __launch_bounds__(256)
+k_build_dir(const uint2 *__restrict__ nb, uint64_t w0, uint64_t n, uint2 *__restrict__ dir, uint2 *__restrict__ exc,
+            uint64_t exc_cap, unsigned long long *__restrict__ exc_n) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t g0 = w0 >> 5, g_end = ((w0 + n - 1) >> 5) + 2;
+    const uint64_t g = g0 + (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
+    if (g >= g_end) return;  // whole warps: 256 threads = 8 groups
+    const uint64_t w = (g << 5) + lane;
+    uint2 m = make_uint2(0u, 0u);
+    if (w >= w0 && w < w0 + n) {
+        m = nb[w - w0];
+    } else if (w < w0) {
+        const uint2 d = dir[g];
+        if ((d.x >> lane) & 1u) m = exc[d.y + __popc(d.x & ((1u << lane) - 1u))];
+    }
+    __syncwarp();
+    const bool special = (m.x | m.y) != 0u;
+    const uint32_t bits = __ballot_sync(0xffffffffu, special);
+    const uint32_t cnt = __popc(bits);
+    unsigned long long base = 0;
+    if (lane == 0 && cnt) base = atomicAdd(exc_n, static_cast<unsigned long long>(cnt));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base + cnt > exc_cap) {
+        if (lane == 0) exc_n[1] = 1ull;
+        return;
+    }
+    if (special) exc[base + __popc(bits & ((1u << lane) - 1u))] = m;
+    if (lane == 0) dir[g] = make_uint2(bits, static_cast<uint32_t>(base));
 }
 
 __global__ void k_halo_update(const uint8_t *__restrict__ old_halo, uint32_t old_len,
@@ -110,23 +154,85 @@ __global__ void k_halo_update(const uint8_t *__restrict__ old_halo, uint32_t old
 }  // namespace
 
 cudaError_t launch_pack(const uint8_t *halo, uint32_t hlen, uint32_t H, const uint8_t *seg,
-                        uint64_t slen, uint4 *words, uint64_t nwords_padded, cudaStream_t st) {
+                        uint64_t slen, uint2 *hl, uint2 *nb, uint64_t nwords_padded, cudaStream_t st) {
     if (nwords_padded == 0) return cudaSuccess;
     const uint64_t grid = (nwords_padded + kPackThreads - 1) / kPackThreads;
     if ((reinterpret_cast<uintptr_t>(seg) & 15u) == 0)
-        k_pack<true><<<static_cast<unsigned>(grid), kPackThreads, 0, st>>>(halo, hlen, H, seg, slen, words,
+        k_pack<true><<<static_cast<unsigned>(grid), kPackThreads, 0, st>>>(halo, hlen, H, seg, slen, hl, nb,
                                                                            nwords_padded);
     else
-        k_pack<false><<<static_cast<unsigned>(grid), kPackThreads, 0, st>>>(halo, hlen, H, seg, slen, words,
+        k_pack<false><<<static_cast<unsigned>(grid), kPackThreads, 0, st>>>(halo, hlen, H, seg, slen, hl, nb,
                                                                             nwords_padded);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mark_pieces(const DevPiece *pieces, uint32_t n, uint4 *words, cudaStream_t st) {
+cudaError_t launch_mark_pieces(const DevPiece *pieces, uint32_t n, uint64_t first, uint64_t nwords, uint2 *nb,
+                               cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     unsigned grid = (n + 255) / 256;
-    k_mark_pieces<<<grid, 256, 0, st>>>(pieces, n, words);
+    k_mark_pieces<<<grid, 256, 0, st>>>(pieces, n, first, nwords, nb);
     return cudaGetLastError();
+}
+
+cudaError_t launch_build_dir(const uint2 *nb, uint64_t w0, uint64_t n, uint2 *dir, uint2 *exc, uint64_t exc_cap,
+                             unsigned long long *exc_n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t groups = ((w0 + n - 1) >> 5) + 2 - (w0 >> 5);
+    const uint64_t grid = (groups + 7) / 8;
+    k_build_dir<<<static_cast<unsigned>(grid), 256, 0, st>>>(nb, w0, n, dir, exc, exc_cap, exc_n);
+    return cudaGetLastError();
+}
+
+cudaError_t refbufs_alloc(RefBufs &R, uint64_t words, uint64_t nb_words, uint64_t exc_entries) {
+    cudaError_t e = cudaSuccess;
+    auto get = [&](uint2 *&p, uint64_t n) {
+        if (e == cudaSuccess) e = cudaMalloc(&p, (n ? n : 1) * sizeof(uint2));
+    };
+    get(R.hl, words);
+    get(R.nb, nb_words);
+    get(R.dir, dir_entries(words));
+    get(R.exc, exc_entries);
+    if (e == cudaSuccess) e = cudaMalloc(&R.exc_n, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+        R.words_cap = words;
+        R.nb_cap = nb_words;
+        R.exc_cap = exc_entries;
+    }
+    return e;
+}
+
+void refbufs_free(RefBufs &R) {
+    cudaFree(R.hl);
+    cudaFree(R.nb);
+    cudaFree(R.dir);
+    cudaFree(R.exc);
+    cudaFree(R.exc_n);
+    R = RefBufs{};
+}
+
+cudaError_t pack_batch(const RefBufs &R, const uint8_t *halo, uint32_t hlen, uint32_t H, const uint8_t *seg,
+                       uint64_t slen, uint64_t nwords, const DevPiece *pieces, uint32_t npieces, bool mark,
+                       cudaStream_t st, int *launches) {
+    if (nwords > R.words_cap || nwords > R.nb_cap || nwords > R.exc_cap) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(R.exc_n, 0, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = launch_pack(halo, hlen, H, seg, slen, R.hl, R.nb, nwords, st);
+    if (e == cudaSuccess && mark) e = launch_mark_pieces(pieces, npieces, 0, nwords, R.nb, st);
+    // every word takes at most one entry, so exc (nwords entries) cannot run out
+    if (e == cudaSuccess) e = launch_build_dir(R.nb, 0, nwords, R.dir, R.exc, R.exc_cap, R.exc_n, st);
+    if (launches) *launches += mark ? 3 : 2;
+    return e;
+}
+
+Batch make_batch(const RefBufs &R, uint64_t nbases, uint32_t halo, const DevPiece *pieces, uint32_t npieces) {
+    Batch b;
+    b.hl = R.hl;
+    b.dir = R.dir;
+    b.exc = R.exc;
+    b.nbases = nbases;
+    b.halo = halo;
+    b.pieces = pieces;
+    b.npieces = npieces;
+    return b;
 }
 
 cudaError_t launch_halo_update(const uint8_t *old_halo, uint32_t old_len, const uint8_t *seg,

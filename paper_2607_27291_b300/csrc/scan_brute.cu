@@ -9,9 +9,9 @@
 //   mm = nN + sum over words of popc(x)
 // R_* is the lane's window word, cut from two packed words by a funnel
 // shift; Q_* the query word (reverse complement precomputed) in shared
-// memory.  The packed words of the warp's next block are prefetched into a
-// per-warp shared double buffer with cp.async while the current one is
-// scanned.
+// memory.  The hi/lo words of the warp's next block and the two directory
+// entries covering them are prefetched into a per-warp shared double buffer
+// with cp.async while the current one is scanned.
 //
 // Early termination, batched: for maxSubs < 32 the first word alone
 // rejects almost every window (E[mm] = 24 of 32 on random sequence), so
@@ -26,9 +26,10 @@
 // entries ("class M") also AND a care mask and use the threshold
 // maxSubs - nN.
 //
-// Blocks of windows that touch an N, a contig-piece boundary, the batch end
-// or the halo take a generic path that folds in the reference N plane and
-// checks each window stays inside one piece and is owned by this batch.
+// Blocks of windows that touch a special word (an N or a contig-piece
+// start), the batch end or the halo take a generic path that rebuilds the N
+// and piece-start planes and checks each window stays inside one piece and
+// is owned by this batch.
 #include "scan_brute.cuh"
 
 namespace ifa {
@@ -50,10 +51,9 @@ template <int WMAX>
 __global__ void __launch_bounds__(kScanThreads, kScanMinCtas<WMAX>)
 k_scan_brute(Batch b, QueryTable qt, uint32_t e0, uint32_t e1, uint32_t s, uint32_t lmin,
              uint32_t lmax, HitSink sink) {
-    constexpr int NW = Stage<WMAX>::kWords;
     extern __shared__ uint4 smem4[];
     __shared__ __align__(16) ifa_hit wbuf[kScanWarps][32];
-    __shared__ uint4 stage[kScanWarps][2][NW];
+    __shared__ __align__(8) uint2 stage[kScanWarps][2][Stage<WMAX>::kSlots];
     __shared__ uint32_t s_nF, s_nM;
     const uint32_t nent = e1 - e0;
     const Smem m = load_chunk<WMAX>(qt, e0, e1, s, smem4, &s_nF, &s_nM);

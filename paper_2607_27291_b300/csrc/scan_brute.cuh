@@ -11,7 +11,8 @@
 //   mm = nN + sum over words of popc(x)
 // R_* is the lane's window word, cut from two packed words by a funnel
 // shift; Q_* the query word (reverse complement precomputed) in shared
-// memory.  The packed words of the warp's next block are prefetched into a
+// memory.  The hi/lo words of the warp's next block (8 bytes per 32 bases)
+// and the two directory entries that cover them are prefetched into a
 // per-warp shared double buffer with cp.async while the current one is
 // scanned.
 //
@@ -28,9 +29,10 @@
 // entries ("class M") also AND a care mask and use the threshold
 // maxSubs - nN.
 //
-// Blocks of windows that touch an N, a contig-piece boundary, the batch end
-// or the halo take a generic path that folds in the reference N plane and
-// checks each window stays inside one piece and is owned by this batch.
+// Blocks of windows that touch a special word (an N or a contig-piece
+// start, per the directory), the batch end or the halo take a generic path
+// that rebuilds the N and piece-start planes (ref_word) and checks each
+// window stays inside one piece and is owned by this batch.
 #pragma once
 #include "hits.cuh"
 
@@ -75,12 +77,14 @@ __device__ inline Smem carve(uint4 *base, uint32_t nent, int wmax) {
     return m;
 }
 
-// Words of the block starting at word 2*? are staged per warp in shared
-// memory; a block is WIN x 32 windows: lane l owns windows p0 + 32 k + l,
-// k < WIN, and window k's word j is cut from staged words k + j, k + j + 1.
+// Words of a block are staged per warp in shared memory; a block is
+// WIN x 32 windows: lane l owns windows p0 + 32 k + l, k < WIN, and window
+// k's word j is cut from staged words k + j, k + j + 1.  After the kWords
+// hi/lo words come the directory entries of their group and the next.
 template <int WMAX>
 struct Stage {
-    static constexpr int kWords = kWin + WMAX;  // staged words per block
+    static constexpr int kWords = kWin + WMAX;  // staged hi/lo words per block
+    static constexpr int kSlots = kWords + 2;   // + two directory entries
 };
 
 // Generic evaluation of every entry for one window per lane (p = p0 + lane)
@@ -91,10 +95,10 @@ __device__ void generic_window(const Batch &b, const QueryTable &qt, const Smem 
                                const HitSink &sink, WH &wh) {
     const uint64_t w0 = p0 >> 5;
     uint32_t hi[WMAX], lo[WMAX], nw[WMAX], bw[WMAX];
-    uint4 cur = __ldg(b.words + w0);
+    uint4 cur = ref_word(b, w0);
 #pragma unroll
     for (int j = 0; j < WMAX; j++) {
-        const uint4 nx = __ldg(b.words + w0 + j + 1);
+        const uint4 nx = ref_word(b, w0 + j + 1);
         hi[j] = __funnelshift_r(cur.x, nx.x, lane);
         lo[j] = __funnelshift_r(cur.y, nx.y, lane);
         nw[j] = __funnelshift_r(cur.z, nx.z, lane);
@@ -161,7 +165,7 @@ __device__ __forceinline__ uint32_t mad(uint32_t a, uint32_t b, uint32_t c) {
 //    maxSubs.  No byte can carry: a count is at most the query length.
 template <int WMAX, class WH>
 __device__ __forceinline__ void exact_fast(const Batch &b, const QueryTable &qt, const Smem &m,
-                                           const uint4 *R, const uint32_t *hw, const uint32_t *lw,
+                                           const uint2 *R, const uint32_t *hw, const uint32_t *lw,
                                            const uint32_t *mul, uint32_t e, uint32_t e0, uint32_t blk,
                                            uint32_t lane, uint32_t s, const HitSink &sink, WH &wh, uint32_t v,
                                            uint32_t bias) {
@@ -179,7 +183,7 @@ __device__ __forceinline__ void exact_fast(const Batch &b, const QueryTable &qt,
                     h = hw[k + 1];
                     l = lw[k + 1];
                 } else {
-                    const uint4 a = R[k + 1], c = R[k + 2];
+                    const uint2 a = R[k + 1], c = R[k + 2];
                     h = __funnelshift_r(a.x, c.x, lane);
                     l = __funnelshift_r(a.y, c.y, lane);
                 }
@@ -203,7 +207,7 @@ __device__ __forceinline__ void exact_fast(const Batch &b, const QueryTable &qt,
                         h = hw[k + j];
                         l = lw[k + j];
                     } else {
-                        const uint4 a = R[k + j], c = R[k + j + 1];
+                        const uint2 a = R[k + j], c = R[k + j + 1];
                         h = __funnelshift_r(a.x, c.x, lane);
                         l = __funnelshift_r(a.y, c.y, lane);
                     }
@@ -247,7 +251,7 @@ template <int WMAX, bool MASKED, class WH>
 __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt, const Smem &m,
                                            const uint4 *rec, const uint16_t *idx, uint32_t n,
                                            const uint32_t *hw, const uint32_t *lw, const uint32_t *mul,
-                                           const uint4 *R, uint32_t e0, uint32_t blk, uint32_t lane,
+                                           const uint2 *R, uint32_t e0, uint32_t blk, uint32_t lane,
                                            uint32_t s, const HitSink &sink, WH &wh) {
     constexpr uint32_t kHigh = 0x80808080u;
     uint32_t k = 0;
@@ -288,14 +292,15 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
     }
 }
 
-// Stage the words of block `blk` into `dst` (shared) with cp.async: lane i
-// copies word i (16 bytes).
+// Stage block `blk` into `dst` (shared) with cp.async: lane i < NW copies
+// hi/lo word blk * kWin + i (8 bytes), lanes NW and NW + 1 the directory
+// entries of that word's group and the next.
 template <int NW>
-__device__ __forceinline__ void stage_block(const Batch &b, uint64_t blk, uint4 *dst, uint32_t lane) {
-    if (lane < NW) {
-        const uint4 *src = b.words + blk * kWin + lane;
+__device__ __forceinline__ void stage_block(const Batch &b, uint64_t blk, uint2 *dst, uint32_t lane) {
+    if (lane < NW + 2) {
+        const uint2 *src = lane < NW ? b.hl + blk * kWin + lane : b.dir + ((blk * kWin) >> 5) + (lane - NW);
         const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + lane));
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -393,7 +398,7 @@ template <int WMAX, class WH>
 __device__ __forceinline__ void scan_blocks(const Batch &b, const QueryTable &qt, const Smem &m, uint32_t nent,
                                             uint32_t nF, uint32_t nM, uint32_t e0, uint32_t s, uint32_t lmin,
                                             uint32_t lmax, const HitSink &sink, WH &wh,
-                                            uint4 (*stage)[Stage<WMAX>::kWords], const uint32_t *mul,
+                                            uint2 (*stage)[Stage<WMAX>::kSlots], const uint32_t *mul,
                                             uint64_t base, uint64_t blk_end, uint32_t w, uint32_t nw,
                                             uint32_t lane) {
     constexpr int NW = Stage<WMAX>::kWords;
@@ -412,11 +417,9 @@ __device__ __forceinline__ void scan_blocks(const Batch &b, const QueryTable &qt
         else asm volatile("cp.async.commit_group;\n" ::: "memory");
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         __syncwarp();
-        const uint4 *R = stage[it & 1];
+        const uint2 *R = stage[it & 1];
         const uint64_t p0 = blk * (32 * kWin);
-        uint32_t flags = R[0].z | (R[0].w & ~1u);
-#pragma unroll
-        for (int i = 1; i < NW; i++) flags |= R[i].z | R[i].w;
+        const uint32_t flags = special_bits(R[NW].x, R[NW + 1].x, blk * kWin, NW);
         // a uniform maxSubs >= 32 makes word 0 useless as a filter: scan generically
         const bool special = (s != kSPerEntry && s >= 32u) || flags != 0u ||
                              p0 + 32 * kWin - 1 + lmax - 1 >= b.nbases ||

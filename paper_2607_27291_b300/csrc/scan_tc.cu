@@ -23,7 +23,7 @@
 //               (K / 32 per phase) into one of two 256-column accumulators
 //               and commits them to mbarriers;
 //   warp 1      builds the four one-hot strings of the next tile from the
-//               packed planes (double-buffered);
+//               2-bit words and their N / piece-start masks (double-buffered);
 //   warps 2..9  read the accumulator (tcgen05.ld; a warp reads its 32 lanes
 //               = 32 entries and half of the columns, two warps per lane
 //               quarter so that two TMEM loads are in flight per quarter),
@@ -193,7 +193,7 @@ __device__ __forceinline__ bool crosses_piece(const Batch &b, uint64_t p, uint32
         const uint64_t end = (w + 1) << 5 < p + L ? (w + 1) << 5 : p + L;
         const uint32_t n = static_cast<uint32_t>(end - q);
         const uint32_t mask = (n >= 32u ? 0xffffffffu : ((1u << n) - 1u)) << lo;
-        if (__ldg(&b.words[w].w) & mask) return true;
+        if (ref_word(b, w).w & mask) return true;
         q = end;
     }
     return false;
@@ -337,9 +337,9 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                 const uint64_t pt = static_cast<uint64_t>(rt0 + ti) * kTcTile;
                 // the tile's words, loaded lane-parallel before the wait (N past the batch)
                 const uint4 nword = make_uint4(0u, 0u, 0xffffffffu, 0u);
-                const uint4 w0 = (pt >> 5) + lane < nwords ? __ldg(b.words + (pt >> 5) + lane) : nword;
+                const uint4 w0 = (pt >> 5) + lane < nwords ? ref_word(b, (pt >> 5) + lane) : nword;
                 const uint4 w1 = 32u + lane < nw && (pt >> 5) + 32u + lane < nwords
-                                     ? __ldg(b.words + (pt >> 5) + 32u + lane) : nword;
+                                     ? ref_word(b, (pt >> 5) + 32u + lane) : nword;
                 if (lane == 0)
                     while (pi + 1 < b.npieces && b.pieces[pi + 1].start <= pt) pi++;
                 if (v >= 1 && !mbar_wait(smem_u32(&H.empty_b[sbuf]), (v - 1) & 1u, abort)) break;

@@ -20,7 +20,7 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                                             unsigned long long &ncand) {
     for (; blk < blk_end; blk += stride) {
         const uint64_t j = (blk << 5) + lane;
-        const uint4 A = __ldg(b.words + blk), B = __ldg(b.words + blk + 1);
+        const uint4 A = ref_word(b, blk), B = ref_word(b, blk + 1);
         const uint32_t hiw = __funnelshift_r(A.x, B.x, lane);
         const uint32_t low = __funnelshift_r(A.y, B.y, lane);
         const uint32_t nw = __funnelshift_r(A.z, B.z, lane);
@@ -89,12 +89,12 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                             uint32_t x[WMAX + 1];
                             uint32_t bnd = 0;
                             mm = 0;
-                            uint4 cur = __ldg(b.words + w0);
+                            uint4 cur = ref_word(b, w0);
 #pragma unroll
                             for (int w = 0; w < WMAX; w++) {
                                 x[w] = 0;
                                 if (w < static_cast<int>(W)) {
-                                    const uint4 nx = __ldg(b.words + w0 + w + 1);
+                                    const uint4 nx = ref_word(b, w0 + w + 1);
                                     const uint32_t rh = __funnelshift_r(cur.x, nx.x, sh);
                                     const uint32_t rl = __funnelshift_r(cur.y, nx.y, sh);
                                     const uint32_t rn = __funnelshift_r(cur.z, nx.z, sh);

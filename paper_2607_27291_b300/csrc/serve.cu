@@ -397,12 +397,7 @@ ifa_status ifa_serve_step(ifa_handle *h, uint32_t *n_active, uint32_t *n_complet
         w.n_items = w.n_brute_items + w.n_stiles;
         w.queue = S.d_queue;
         w.candidates = S.d_cand;
-        Batch b;
-        b.words = B.d_words;
-        b.nbases = B.nbases;
-        b.halo = 0;
-        b.pieces = B.d_pieces;
-        b.npieces = B.d_pieces_n;
+        const Batch b = make_batch(B.ref, B.nbases, 0, B.d_pieces, B.d_pieces_n);
         const double t1 = now_s();
         SCK(h, cudaMemsetAsync(S.d_queue, 0, sizeof(unsigned int), h->stream));
         SCK(h, launch_batch_kernel(S.wmax, b, w, S.bt, S.ft, S.sink, S.grid, brute::kScanSmemBudget, h->stream));
