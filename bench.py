@@ -63,6 +63,12 @@ def parse():
     ap.add_argument("--sizes", default="16,32,64,512,10000", help="brute-kernels: query-set sizes")
     ap.add_argument("--solo-max-s", type=float, default=180.0,
                     help="serving: wall-time cap of the one-request-at-a-time baseline")
+    ap.add_argument("--max-wall", type=float, default=float("inf"),
+                    help="serving: wall-time cap of the continuous-batching run")
+    ap.add_argument("--burst", type=int, default=0,
+                    help="serving: first serve this many requests arriving at once (capacity)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="sweep: skip the other workloads' keys (latency, indexed, batched, serving)")
     return ap.parse_args()
 
 
@@ -203,8 +209,25 @@ def popc_rate():
 
 
 def pcie_peaks(dev, mb=256, reps=10):
-    """Best-of-`reps` pinned host <-> device copy rates of `mb` MiB (GB/s)."""
+    """Pinned host <-> device copy rates of `mb` MiB (GB/s): the best of `reps`
+    single cudaMemcpyAsync copies from cudaHostAlloc memory and `reps` copies
+    back to back on one stream (the streamed segments' pattern), from the
+    probe library; torch's copy_ between pinned and device tensors beside
+    them, for reference."""
+    import ctypes as C
     import torch
+    lib = C.CDLL(os.path.join(ROOT, "paper_2607_27291_b300", "libifa_probe.so"))
+    f = lib.ifa_probe_copy_rate
+    f.restype = C.c_int
+    f.argtypes = [C.c_int, C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    native = {}
+    for name, to_dev in (("h2d", 1), ("d2h", 0)):
+        best, b2b = C.c_double(), C.c_double()
+        rc = f(dev, mb << 20, to_dev, reps, C.byref(best), C.byref(b2b))
+        if rc:
+            raise RuntimeError("copy probe failed: %d" % rc)
+        native[name + "_gbps"] = best.value
+        native[name + "_gbps_back_to_back"] = b2b.value
     n = mb << 20
     host = torch.empty(n, dtype=torch.uint8).pin_memory()
     devb = torch.empty(n, dtype=torch.uint8, device=f"cuda:{dev}")
@@ -225,10 +248,21 @@ def pcie_peaks(dev, mb=256, reps=10):
                 ms = a.elapsed_time(b)
                 best = ms if best is None else min(best, ms)
         out[name] = n / (best * 1e-3) / 1e9
-    out["bytes"] = n
-    out["how"] = "pinned %d MiB copy, best of %d, CUDA events" % (mb, reps)
+        with torch.cuda.stream(st):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for _ in range(8):
+                fn()
+            b.record(st)
+            b.synchronize()
+        out[name + "_back_to_back"] = 8 * n / (a.elapsed_time(b) * 1e-3) / 1e9
     del host, devb
-    return out
+    native["torch_copy"] = out
+    native["bytes"] = n
+    native["how"] = ("cudaMemcpyAsync of %d MiB between cudaHostAlloc and device memory: best of %d single "
+                     "copies, and %d back to back; CUDA events" % (mb, reps, reps))
+    return native
 
 
 def run_pipe_rates(args):
@@ -259,11 +293,24 @@ def run_pipe_rates(args):
         med = rows[len(rows) // 2]
         rates[name] = {"per_clk_sm": med[0], "ms": med[1], "sm_mhz_from_cycles": med[2],
                        "min": rows[0][0], "max": rows[-1][0]}
+    g = lib.ifa_probe_gather_rate
+    g.restype = C.c_int
+    g.argtypes = [C.c_int, C.c_uint64, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    gathers = {}
+    for mb in (16, 64, 1024):
+        best = None
+        for _ in range(max(1, args.steps)):
+            r, ms = C.c_double(), C.c_double()
+            rc = g(dev, mb << 20, 512, C.byref(r), C.byref(ms))
+            if rc:
+                raise RuntimeError("gather probe failed: %d" % rc)
+            best = r.value if best is None else max(best, r.value)
+        gathers["%d MiB table" % mb] = best
     clk = clocks.stop()
     pcie = pcie_peaks(dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     line = {"workload": "pipe-rates", "metric": "results per SM per clock", "unit": "ops/clk/SM",
-            "rates": rates, "sms": sms, "clocks": clk, "pcie": pcie,
+            "rates": rates, "random_gather_loads_per_s": gathers, "sms": sms, "clocks": clk, "pcie": pcie,
             "config": {"blocks_per_sm": 4, "threads": 256, "chains_per_thread": 8,
                        "instructions_per_thread": 2000 * 16 * 8, "runs": max(1, args.steps)}}
     print(json.dumps(line), flush=True)
@@ -450,26 +497,66 @@ def run_ours(args, rank, world):
     # ---- end to end through pinned host memory
     e2e = None
     if not args.no_e2e:
+        P.ifa_destroy(h)
         del ref_dev
         torch.cuda.empty_cache()
+        # end to end: pinned host ASCII in, every hit out to pinned host
+        # memory through a fixed ring of 64 Mi hits (1 GiB) polled after each
+        # segment, so hits leave while later segments are scanned
+        ring = 1 << 26
+        h = P.ifa_create(device=dev, hit_capacity=ring, segment_bytes=SEG)
+        P.ifa_set_stream(h, stream)
+        P.ifa_load_queries(h, wl.queries)
+        P.ifa_set_mode(h, P.IFA_MODE_BRUTE)
         ref_pin = torch.from_numpy(wl.ref).pin_memory()
-        for s in SUBS:  # warm the pinned path and size the pinned hit buffer
-            one_pass(s, ref_pin, True)
+        dg_hits = max(int(v) for v in hits_per_s.values())
+        out_t = torch.empty((dg_hits + ring) * 16, dtype=torch.uint8).pin_memory()
+        out = out_t.numpy().view(P.HIT_DTYPE)
+
+        def e2e_pass(s):
+            P.ifa_reset_results(h)
+            P.ifa_set_max_subs(h, s)
+            if halo:
+                P.ifa_prime_halo(h, halo[0], halo[1], ref_pin[halo[2] - off:halo[3] - off])
+            got, over_any = 0, False
+            for a, b, pc in segs:
+                P.ifa_push_segment(h, ref_pin[a - off:b - off], pc)
+                n, over, _ = P.ifa_poll_hits(h, out[got:])
+                got += n
+                over_any |= over
+            n_polled = got
+            while True:   # what the last segments left in the ring
+                n, over, more = P.ifa_drain_into(h, out[got:])
+                got += n
+                over_any |= over
+                if not more:
+                    break
+            return got, n_polled, over_any
+
+        for s in SUBS:  # warm the pinned path
+            e2e_pass(s)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         d2h = 0
+        polled = 0
+        overflow = False
         for s in SUBS:
-            n = one_pass(s, ref_pin, True)
+            n, npol, ov = e2e_pass(s)
             d2h += n * 16 + 24
+            polled += npol
+            overflow |= ov
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         dt = allmax(dt, world)
         pk = pcie_peaks(dev)
+        pk_h2d = max(pk["h2d_gbps"], pk["h2d_gbps_back_to_back"])
         h2d = wl.ref.size * len(SUBS) / dt / 1e9
         e2e = {"value": qb_all / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(wl.ref.size) * len(SUBS), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": dt * 1e3, "pcie_h2d_gbps": h2d,
-               "pcie_peak": pk, "pcie_h2d_frac": h2d / pk["h2d_gbps"]}
+               "pcie_peak": pk, "pcie_h2d_frac": h2d / pk_h2d,
+               "hit_ring": {"entries": ring, "bytes": ring * 16, "hits_per_step": (d2h - 24 * len(SUBS)) // 16,
+                            "hits_polled_during_stream": polled, "overflow": overflow}}
     P.ifa_destroy(h)
 
     cpu = None
@@ -519,7 +606,36 @@ def run_ours(args, rank, world):
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
+    if world == 1 and not args.no_extras:
+        line.update(extras(args))
     print(json.dumps(line), flush=True)
+
+
+def extras(args):
+    """The other workloads, each measured once more in the same run: one
+    short query's call latency (1 query, 10 x 1 Mbp), indexed mode (10,000
+    queries vs 1 Gbp at maxSubs 4/8/16), 256 query sets in one persistent
+    launch vs one launch per set (16 Gbp), and continuous-batching serving
+    against a 200 Gbp store in HBM: the trace's first 16 requests at once,
+    served to completion (capacity), then Poisson arrivals at 50/s for 30 s
+    served for at most 45 s (one B300 falls far behind 50/s at 200 Gbp:
+    the line reports the backlog and the throughput while saturated)."""
+    import torch
+    out = {}
+    jobs = (("latency", lambda: latency_result(50, 5)),
+            ("indexed", lambda: indexed_result(int(1e9), 5, 1, brute=False)),
+            ("batched", lambda: batched_result(args, int(16e9), 1)),
+            ("serving", lambda: serving_result(int(2e11), 50.0, 30.0, 64, None, 45.0, burst=16)))
+    for name, fn in jobs:
+        t = time.perf_counter()
+        try:
+            r = fn()
+        except Exception as e:  # keep the headline line if one workload fails
+            r = {"error": "%s: %s" % (type(e).__name__, e)}
+        r["run_s"] = round(time.perf_counter() - t, 1)
+        out[name] = r
+        torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- many sets
@@ -530,12 +646,16 @@ def _store_from_device(P, h, ref_dev, lens):
 
 
 def run_batched(args):
+    print(json.dumps(batched_result(args, int(args.total if args.total != 4e9 else 16e9), args.steps)),
+          flush=True)
+
+
+def batched_result(args, total, steps):
     """Query sets of uneven sizes against a device-resident reference: one
     persistent graph-replayed launch vs one launch per set."""
     import torch
     import paper_2607_27291_b300 as P
     import synth
-    total = int(args.total if args.total != 4e9 else 16e9)
     t = time.perf_counter()
     ref, lens, sets = synth.workload_sets_16gbp(total=total, n_sets=args.sets)
     t_gen = time.perf_counter() - t
@@ -552,7 +672,7 @@ def run_batched(args):
     res = P.ifa_batch_run(h, P.IFA_BATCH_PERSISTENT, len(sets))   # calibrates, plans, captures
     t_plan = time.perf_counter() - t
     runs = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, steps)):
         P.ifa_reset_results(h)
         res = P.ifa_batch_run(h, P.IFA_BATCH_PERSISTENT, len(sets))
         runs.append(float(res["done_ms"].max()))
@@ -577,10 +697,11 @@ def run_batched(args):
         "config": {"reference_bases": int(ref.size), "contigs": int(lens.size), "sets": len(sets),
                    "queries": int(nq.sum()), "set_sizes": "log-uniform 1-5000",
                    "lengths": "18-50", "max_subs": "0-12 per set", "gc": "0.30-0.65 per contig",
-                   "generation_s": round(t_gen, 1), "plan_s": round(t_plan, 1)},
+                   "generation_s": round(t_gen, 1), "plan_s": round(t_plan, 1), "timed_runs": len(runs)},
         "data": "synthetic",
     }
-    print(json.dumps(line), flush=True)
+    del ref
+    return line
 
 
 def serve_trace(P, h, reqs, slices, budget, max_wall):
@@ -633,6 +754,7 @@ def serve_trace(P, h, reqs, slices, budget, max_wall):
                    [wall - r[0] for r in reqs[nxt:]])
     queue = np.array([i["admit_s"] - i["submit_s"] for i in done]) if done else np.zeros(1)
     return {"value": sst["query_bases"] / wall, "hits_drained": drained_hits,
+            "cycle_s": wall / max(1.0, steps / slices),
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "p999": float(np.percentile(lat, 99.9))},
             "queue_s": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
@@ -641,57 +763,115 @@ def serve_trace(P, h, reqs, slices, budget, max_wall):
 
 
 def run_serving(args):
+    total = int(args.total if args.total != 4e9 else 2e11)
+    print(json.dumps(serving_result(total, args.rate, args.duration, args.slices,
+                                    None if args.no_solo else args.solo_max_s, args.max_wall, args.burst)),
+          flush=True)
+
+
+def counter_store(P, h, ref, chunk=256 << 20):
+    """Append a synth.CounterReference to the handle's store, generating
+    each 256 MB chunk straight into device memory (the reference never
+    exists on the host).  Returns (seconds, device bytes the store took)."""
+    import torch
+    from synth.devgen import DeviceFiller
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    t = time.perf_counter()
+    fill = DeviceFiller(ref)
+    P.ifa_ref_reserve(h, ref.total)
+    buf = torch.empty(chunk, dtype=torch.uint8, device="cuda")
+    for a, b, pc in P.segment_pieces(ref.contig_len, chunk):
+        fill.fill(buf[:b - a], a)
+        torch.cuda.synchronize()           # the append runs on the library's own stream
+        P.ifa_ref_append(h, buf[:b - a], pc)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    del buf, fill
+    torch.cuda.empty_cache()
+    free1, _ = torch.cuda.mem_get_info()
+    return dt, free0 - free1
+
+
+def serving_result(total, rate, duration, slices, solo_max_s, max_wall, burst=0):
     """Poisson arrivals of query sets served by continuous batching over a
-    device-resident reference, and the same trace served one request at a
-    time (admission limited to one active request) as the baseline."""
+    device-resident reference, and optionally the same trace served one
+    request at a time (admission limited to one active request).  References
+    of 32 Gbp and more are counter-generated on the device (GC 45 %, 0.05 % N
+    in runs, log-uniform contigs 1 kbp - 10 Mbp); smaller ones come from the
+    host generator of the same recipe.  max_wall bounds the continuous-
+    batching run (requests unfinished then count with their age)."""
     import torch
     import paper_2607_27291_b300 as P
     import synth
-    total = int(args.total if args.total != 4e9 else 1e9)
-    ref, lens, reqs = synth.workload_serving(total, args.rate, args.duration)
-    ref_dev = torch.from_numpy(ref).cuda()
+    reqs = synth.serving_requests(rate, duration)
     h = P.ifa_create(hit_capacity=1024, segment_bytes=256 << 20, minhits_trials=100_000, minhits_seed=1)
-    _store_from_device(P, h, ref_dev, lens)
-    del ref_dev
-    torch.cuda.empty_cache()
-    # warm the planner's MinHits bins and the kernels with one request
-    P.ifa_serve_start(h, args.slices, 64 << 30, 1 << 20)
-    P.ifa_serve_submit(h, reqs[0][1], reqs[0][2], P.IFA_MODE_AUTO)
+    if total >= 32e9:
+        ref = synth.serving_reference(total)
+        build_s, store_bytes = counter_store(P, h, ref)
+        nbases, ncontigs = ref.total, len(ref.contig_len)
+    else:
+        ref_h, lens, _ = synth.workload_serving(total, rate, 0.0)
+        ref_dev = torch.from_numpy(ref_h).cuda()
+        t = time.perf_counter()
+        _store_from_device(P, h, ref_dev, lens)
+        build_s, store_bytes = time.perf_counter() - t, None
+        nbases, ncontigs = int(ref_h.size), int(lens.size)
+        del ref_dev, ref_h
+        torch.cuda.empty_cache()
+    # warm the planner's MinHits bins and the kernels with a one-query request
+    P.ifa_serve_start(h, slices, 64 << 30, 1 << 20)
+    P.ifa_serve_submit(h, reqs[0][1][:1], reqs[0][2], P.IFA_MODE_AUTO)
     while P.ifa_serve_step(h)[0]:
         pass
-    cb = serve_trace(P, h, reqs, args.slices, 64 << 30, float("inf"))
+    burst_r = None
+    if burst:
+        # capacity: the trace's first `burst` requests all arrive at once and
+        # are served together by continuous batching until every one is done
+        burst_r = serve_trace(P, h, [(0.0, qs, s) for _, qs, s in reqs[:burst]], slices, 64 << 30,
+                              float("inf"))
+        burst_r["requests_per_s"] = burst / burst_r["wall_s"]
+    cb = serve_trace(P, h, reqs, slices, 64 << 30, max_wall)
     solo = None
-    if not args.no_solo:
-        solo = serve_trace(P, h, reqs, args.slices, 1, args.solo_max_s)
+    if solo_max_s:
+        solo = serve_trace(P, h, reqs, slices, 1, solo_max_s)
     P.ifa_destroy(h)
-    line = {
+    return {
         "workload": "serving", "metric": "query-base comparisons/s (nominal) and request latency",
         "unit": "query-base comparisons/s", "value": cb["value"],
         "latency_s": cb["latency_s"], "queue_s": cb["queue_s"], "requests": len(reqs),
-        "wall_s": cb["wall_s"], "steps": cb["steps"],
+        "completed": cb["completed"], "wall_s": cb["wall_s"], "steps": cb["steps"],
+        "stopped_at_wall_limit": cb["stopped_at_wall_limit"],
+        "cycle_s": cb["cycle_s"], "sustained_requests_per_s": cb["completed"] / cb["wall_s"],
         "host_plan_s": cb["host_plan_s"], "device_scan_s": cb["device_scan_s"],
         "one_request_at_a_time": solo,
-        "config": {"reference_bases": int(ref.size), "rate_per_s": args.rate,
-                   "duration_s": args.duration, "slices": args.slices,
+        "burst": burst_r,
+        "config": {"reference_bases": nbases, "contigs": ncontigs, "rate_per_s": rate,
+                   "duration_s": duration, "slices": slices, "max_wall_s": max_wall,
+                   "store_build_s": round(build_s, 1), "store_device_bytes": store_bytes,
                    "set_sizes": "log-uniform 1-2000", "lengths": "18-50", "max_subs": "0-8",
                    "gc": 0.45, "n_frac": 0.0005, "mode": "auto by query count",
                    "admission": "HBM budget 64 GiB (continuous batching); baseline: one active request"},
-        "data": "synthetic",
+        "data": "synthetic" + (", reference generated on the device" if total >= 32e9 else ""),
     }
-    print(json.dumps(line), flush=True)
 
 
 def run_indexed(args):
+    print(json.dumps(indexed_result(int(args.total if args.total != 4e9 else 1e9), args.steps, args.warmup,
+                                    brute=True)), flush=True)
+
+
+def indexed_result(total, steps, warmup, brute=True):
     """Indexed mode at scale: 10,000 queries of 20-40 bp against 1 Gbp
     (GC 50 %), maxSubs 4 / 8 / 16, MinHits from a 10^5-trial Monte Carlo on
     Philox seed 1; 5 % of the queries are planted once with exactly maxSubs
     substitutions.  Per maxSubs: a device-resident count-only pass timed with
-    CUDA events, indexed and brute force on the same handle, and the planted
-    windows found (indexed mode's recall, the paper's false-negative rate)."""
+    CUDA events, indexed (and, with `brute`, brute force) on the same handle,
+    and the planted windows found (indexed mode's recall, the paper's
+    false-negative rate)."""
     import torch
     import paper_2607_27291_b300 as P
     import synth
-    total = int(args.total if args.total != 4e9 else 1e9)
     out = {}
     for s in (4, 8, 16):
         wl = synth.workload_1gbp_indexed(total=total, plant_subs=s)
@@ -704,11 +884,13 @@ def run_indexed(args):
         segs = list(P.segment_pieces(wl.contig_len, SEG))
         _, qb = nominal_work(wl)
         res = {}
-        for mode, name in ((P.IFA_MODE_INDEXED, "indexed"), (P.IFA_MODE_BRUTE, "brute")):
+        modes = ((P.IFA_MODE_INDEXED, "indexed"), (P.IFA_MODE_BRUTE, "brute")) if brute else \
+            ((P.IFA_MODE_INDEXED, "indexed"),)
+        for mode, name in modes:
             P.ifa_set_mode(h, mode)
             times = []
-            reps = args.steps if name == "indexed" else 1   # brute force: ~6 s per pass
-            for rep in range(max(1, args.warmup) + reps):
+            reps = steps if name == "indexed" else 1   # brute force: seconds per pass
+            for rep in range(max(1, warmup) + reps):
                 P.ifa_reset_results(h)
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
@@ -718,7 +900,7 @@ def run_indexed(args):
                 b.record(stream)
                 P.ifa_flush(h)
                 b.synchronize()
-                if rep >= max(1, args.warmup):
+                if rep >= max(1, warmup):
                     times.append(a.elapsed_time(b))
             st = P.ifa_get_stats(h)
             dg, _ = P.ifa_get_digest(h)
@@ -765,12 +947,16 @@ def run_indexed(args):
             "config": {"reference_bases": total, "queries": 10000, "lengths": "20-40", "gc": 0.5,
                        "contigs": "log-uniform 10 kbp - 2 Mbp", "minhits_trials": 100000, "philox_seed": 1,
                        "planted": "5 % of queries, exactly maxSubs substitutions", "hits": "count only",
-                       "steps": args.steps, "warmup": max(1, args.warmup), "brute_steps": 1},
+                       "steps": steps, "warmup": max(1, warmup), "brute_steps": 1 if brute else 0},
             "data": "synthetic"}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_latency(args):
+    print(json.dumps(latency_result(args.steps, args.warmup)), flush=True)
+
+
+def latency_result(steps, warmup):
     """One 20 bp query against 10 contigs of 1 Mbp (uniform ACGT), maxSubs 2,
     20 planted hits: latency of one whole call from pinned host ASCII (push,
     scan, drain) and of the device-resident scan alone."""
@@ -786,7 +972,7 @@ def run_latency(args):
     P.ifa_set_mode(h, P.IFA_MODE_BRUTE)
     segs = list(P.segment_pieces(wl.contig_len, 16 << 20))
     e2e, devl, nh = [], [], 0
-    for rep in range(args.warmup + max(args.steps, 50)):
+    for rep in range(warmup + max(steps, 50)):
         for src, acc in ((pin, e2e), (dev, devl)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -795,7 +981,7 @@ def run_latency(args):
                 P.ifa_push_segment(h, src[x:y], pc)
             hits, _ = P.ifa_drain_hits(h)
             dt = time.perf_counter() - t0
-            if rep >= args.warmup:
+            if rep >= warmup:
                 acc.append(dt * 1e3)
             nh = hits.size
     P.ifa_destroy(h)
@@ -809,7 +995,7 @@ def run_latency(args):
                        "input": "ASCII from pinned host memory (e2e) or device memory",
                        "reps": len(e2e)},
             "data": "synthetic"}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_brute_kernels(args):

@@ -62,8 +62,9 @@ typedef enum {
 } ifa_mode;
 
 typedef enum {
-    IFA_BRUTE_AUTO = 0,    /* tensor cores from 32 queries on when eligible and hits are sparse (a random
-                              window of the shortest query passes with probability <= 1e-4) */
+    IFA_BRUTE_AUTO = 0,    /* tensor cores from 32 queries on when eligible (queries of at most 64 bases) and
+                              hits are sparse: the set's mean probability that a random window hits, over
+                              its queries (uniform bases, Binomial(L, 3/4) <= maxSubs), is at most 2e-4 */
     IFA_BRUTE_POPC = 1,    /* bit-plane XOR/OR/popcount kernel */
     IFA_BRUTE_TENSOR = 2   /* one-hot GEMM on the tensor cores; queries of at most 64 bases */
 } ifa_brute_kernel;
@@ -129,7 +130,7 @@ typedef struct {
     uint32_t clip_pct;             /* soft clipping at contig ends (Methods, Algorithm Design): a window may
                                       overhang its contig by up to floor(clip_pct * L / 100) bases, which
                                       count as clips, not mismatches; 0 = off, at most 50 (paper: 25);
-                                      streaming API only */
+                                      streaming and batched calls (serving rejects it) */
     uint32_t exhaustive_fallback;  /* 1: queries with no qualifying k are scanned exhaustively */
     uint32_t auto_crossover;       /* IFA_MODE_AUTO picks indexed from this many queries on */
     uint32_t profile;              /* 1: time every scan kernel with CUDA events (ifa_stats.scan_ns) */
@@ -289,13 +290,20 @@ ifa_status ifa_minhits(int32_t device, const uint32_t *L, const uint32_t *subs, 
  * ifa_get_digest); query ids are global, a set's queries being the range
  * [first_query, first_query + n). */
 
-/* Append len reference bytes to the store (packed on the device, 0.5 byte
- * per base).  pieces: as for ifa_push_segment, in this chunk's coordinates;
+/* Append len reference bytes to the store (packed on the device: 2 bits
+ * per base, plus the sparse table of the words holding an N or a contig
+ * start).  pieces: as for ifa_push_segment, in this chunk's coordinates;
  * a contig may continue into the next append (its piece has last = 0).
  * Every append except the last must hold a multiple of 32 bytes.
  * Errors: INVALID_ARG (pieces, alignment, contig order), OOM, CUDA. */
 ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, const ifa_piece *pieces,
                           uint32_t n_pieces, ifa_mem mem);
+
+/* Make room in the store for `bases` bases in total (bytes already appended
+ * included), so that appends up to that size allocate nothing more; without
+ * it the store grows by half its size whenever an append does not fit.
+ * Errors: OOM, CUDA. */
+ifa_status ifa_ref_reserve(ifa_handle *h, uint64_t bases);
 
 /* Drop the store (frees its device memory). */
 ifa_status ifa_ref_reset(ifa_handle *h);

@@ -98,6 +98,7 @@ _SYMBOLS = {
                               C.c_uint32, C.c_uint64, C.c_void_p]),
     "ifa_last_error": (C.c_char_p, [C.c_void_p]),
     "ifa_ref_append": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32, C.c_int]),
+    "ifa_ref_reserve": (C.c_int, [C.c_void_p, C.c_uint64]),
     "ifa_ref_reset": (C.c_int, [C.c_void_p]),
     "ifa_set_add": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.c_uint32,
                               C.c_uint32, C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
@@ -376,6 +377,10 @@ def ifa_ref_append(h, data, pieces, mem: Optional[int] = None) -> None:
             mem = IFA_MEM_DEVICE if data.is_cuda else (
                 IFA_MEM_HOST_PINNED if data.is_pinned() else IFA_MEM_HOST)
     _check(lib().ifa_ref_append(h, C.c_void_p(ptr), ln, pa.ctypes.data, pa.size, mem), h)
+
+
+def ifa_ref_reserve(h, bases: int) -> None:
+    _check(lib().ifa_ref_reserve(h, int(bases)), h)
 
 
 def ifa_ref_reset(h) -> None:

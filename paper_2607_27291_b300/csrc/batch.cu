@@ -327,7 +327,7 @@ ifa_status build_plan(ifa_handle *h) {
     B.bchunk_e1.clear();
     B.bchunk_lmin.clear();
     B.bchunk_lmax.clear();
-    uint32_t cap = brute::kScanSmemBudget / brute::entry_smem(static_cast<int>(wmax));
+    uint32_t cap = brute::chunk_cap(static_cast<int>(wmax));
     cap = std::min<uint32_t>(cap, 65535) & ~1u;
     if (cap < 2) cap = 2;
     bool any_idx = false;
@@ -619,6 +619,7 @@ ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, con
             return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: contig longer than 2^32 - 1 bases");
     }
     if (at != len) return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: pieces must cover the bytes");
+    const NvtxRange nvtx("ifa_ref_append");
     BCK(h, cudaSetDevice(h->dev));
     BCK(h, cudaStreamSynchronize(h->stream));
     // grow the store (geometric), keeping the packed words and directory
@@ -702,6 +703,8 @@ ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, con
         }
     }
     if (!fresh.empty()) B.pieces.insert(B.pieces.end(), fresh.begin(), fresh.end());
+    // a contig continued from the previous append ends here: its piece is now its last
+    if (B.open && pieces[0].last && !B.pieces.empty()) B.pieces[B.pieces.size() - fresh.size() - 1].last = 1u;
     const ifa_piece &lp = pieces[n - 1];
     B.open = !lp.last;
     B.open_contig = lp.contig;
@@ -712,6 +715,21 @@ ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, con
     B.pieces_dirty = true;
     B.plan_valid = false;
     B.brute_entry_bases_per_s = 0;
+    return IFA_OK;
+}
+
+ifa_status ifa_ref_reserve(ifa_handle *h, uint64_t bases) {
+    if (!h) return IFA_ERR_INVALID_ARG;
+    BCK(h, cudaSetDevice(h->dev));
+    BCK(h, cudaStreamSynchronize(h->stream));
+    BatchState &B = h->batch;
+    const uint64_t want = (std::max<uint64_t>(bases, B.nbases) + 31) / 32 + kStorePad;
+    if (want <= B.ref.words_cap && B.ref.hl) return IFA_OK;
+    const uint64_t old_words = B.nbases / 32;
+    uint64_t hc = B.ref.words_cap, dc = B.ref.words_cap ? dir_entries(B.ref.words_cap) : 0;
+    BCK(h, grow(B.ref.hl, hc, want, old_words, h->stream));
+    BCK(h, grow(B.ref.dir, dc, dir_entries(want), dir_entries(old_words + 1), h->stream));
+    B.ref.words_cap = want;
     return IFA_OK;
 }
 
@@ -763,10 +781,9 @@ ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per
     if (!h) return IFA_ERR_INVALID_ARG;
     BatchState &B = h->batch;
     if (B.nbases == 0 || B.sets.empty()) return bfail(h, IFA_ERR_BAD_STATE, "ifa_batch_run: empty store or no sets");
-    if (h->cfg.clip_pct)
-        return bfail(h, IFA_ERR_INVALID_ARG, "ifa_batch_run: soft clipping (clip_pct) applies to the streaming calls only");
     if (kind != IFA_BATCH_PERSISTENT && kind != IFA_BATCH_PER_SET)
         return bfail(h, IFA_ERR_INVALID_ARG, "ifa_batch_run: unknown kind");
+    const NvtxRange nvtx(kind == IFA_BATCH_PERSISTENT ? "ifa_batch_run persistent" : "ifa_batch_run per set");
     BCK(h, cudaSetDevice(h->dev));
     ifa_status st = calibrate(h);
     if (st != IFA_OK) return st;
@@ -801,6 +818,10 @@ ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per
             if (e == cudaSuccess) {
                 cudaError_t e1 = cudaMemsetAsync(B.d_queue, 0, sizeof(unsigned int), h->stream);
                 cudaError_t e2 = launch_batch(B.wmax, b, B.work, bt, ft, sink, B.grid, smem, h->stream);
+                // soft-clipped windows at the store's contig ends, every set's
+                // entries at their own maxSubs, exhaustively in both modes
+                if (e2 == cudaSuccess && h->cfg.clip_pct)
+                    e2 = launch_clip_scan(b, ft, ft.n_entries, h->cfg.clip_pct, kSPerEntry, h->lmax, sink, h->stream);
                 e = cudaStreamEndCapture(h->stream, &g);
                 if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
             }
@@ -823,6 +844,13 @@ ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per
             if (e == cudaSuccess && S.chosen == IFA_MODE_INDEXED && I.tables_valid && I.targ.n) {
                 e = launch_seed_scan(b, ft, I.targ, I.d_entry_minhits, h->cfg.kmer_step, kSPerEntry, sink,
                                      I.d_candidates ? I.d_candidates : B.d_cand, h->stream);
+                h->stats.kernel_launches += 1;
+            }
+            if (e == cudaSuccess && h->cfg.clip_pct) {
+                uint32_t lmax = 0;
+                for (uint32_t q = S.first; q < S.first + S.n; q++)
+                    lmax = std::max<uint32_t>(lmax, static_cast<uint32_t>(h->qs[q].size()));
+                e = launch_clip_scan(b, ft, 2 * S.n, h->cfg.clip_pct, kSPerEntry, lmax, sink, h->stream, 2 * S.first);
                 h->stats.kernel_launches += 1;
             }
             if (e == cudaSuccess) e = cudaEventCreate(&done[si]);

@@ -506,6 +506,7 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
     if (len == 0 || n == 0 || !ascii || !pieces)
         return fail(h, IFA_ERR_INVALID_ARG, "a segment needs bytes and at least one piece");
     if (len > h->cfg.segment_bytes) return fail(h, IFA_ERR_INVALID_ARG, "segment longer than segment_bytes");
+    const NvtxRange nvtx("ifa_push_segment");
     if (mem != IFA_MEM_HOST && mem != IFA_MEM_HOST_PINNED && mem != IFA_MEM_DEVICE)
         return fail(h, IFA_ERR_INVALID_ARG, "unknown memory kind");
     if (h->qs.empty()) return fail(h, IFA_ERR_BAD_STATE, "no queries loaded");
@@ -732,6 +733,7 @@ ifa_status ifa_drain_hits(ifa_handle *h, ifa_hit *out, uint64_t cap, uint64_t *n
     if (!n_out || (cap && !out)) return fail(h, IFA_ERR_INVALID_ARG, "out/n_out is NULL");
     *n_out = 0;
     if (more) *more = 0;
+    const NvtxRange nvtx("ifa_drain_hits");
     ifa_status st = ifa_flush(h);
     if (st != IFA_OK && st != IFA_ERR_HIT_OVERFLOW) return st;
     const ifa_status ret = st;
@@ -765,6 +767,7 @@ ifa_status ifa_poll_hits(ifa_handle *h, ifa_hit *out, uint64_t cap, uint64_t *n_
     *n_out = 0;
     if (more) *more = 0;
     if (h->cfg.count_only) return IFA_OK;
+    const NvtxRange nvtx("ifa_poll_hits");
     CK(h, cudaSetDevice(h->dev));
     ifa_status st = collect_marks(h, false);
     if (st != IFA_OK) return st;

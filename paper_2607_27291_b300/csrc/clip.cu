@@ -58,7 +58,8 @@ __device__ __forceinline__ uint32_t clipped_mismatches(const Batch &b, const uin
 }
 
 __global__ void __launch_bounds__(kClipThreads)
-k_clip_scan(Batch b, QueryTable qt, uint32_t nent, uint32_t clip_pct, uint32_t s, uint32_t cmax, HitSink sink) {
+k_clip_scan(Batch b, QueryTable qt, uint32_t e_base, uint32_t nent, uint32_t clip_pct, uint32_t s, uint32_t cmax,
+            HitSink sink) {
     __shared__ __align__(16) ifa_hit wbuf[kClipThreads / 32][32];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     WarpHits wh;
@@ -75,7 +76,7 @@ k_clip_scan(Batch b, QueryTable qt, uint32_t nent, uint32_t clip_pct, uint32_t s
         bool has_start = false, has_end = false;
         if (live) {
             piece = static_cast<uint32_t>(pair / nent);
-            e = static_cast<uint32_t>(pair % nent);
+            e = e_base + static_cast<uint32_t>(pair % nent);
             const uint32_t m = qt.meta[e];
             L = meta_L(m);
             C = clip_pct * L / 100u;
@@ -136,13 +137,13 @@ k_clip_scan(Batch b, QueryTable qt, uint32_t nent, uint32_t clip_pct, uint32_t s
 }  // namespace
 
 cudaError_t launch_clip_scan(const Batch &b, const QueryTable &qt, uint32_t nent, uint32_t clip_pct, uint32_t s,
-                             uint32_t lmax, const HitSink &sink, cudaStream_t st) {
+                             uint32_t lmax, const HitSink &sink, cudaStream_t st, uint32_t e_base) {
     const uint32_t cmax = clip_pct * lmax / 100u;
     if (nent == 0 || b.npieces == 0 || cmax == 0) return cudaSuccess;
     const uint64_t npairs = static_cast<uint64_t>(b.npieces) * nent;
     uint64_t grid = (npairs + kClipThreads - 1) / kClipThreads;
     if (grid > 148ull * 16) grid = 148ull * 16;
-    k_clip_scan<<<static_cast<unsigned>(grid), kClipThreads, 0, st>>>(b, qt, nent, clip_pct, s, cmax, sink);
+    k_clip_scan<<<static_cast<unsigned>(grid), kClipThreads, 0, st>>>(b, qt, e_base, nent, clip_pct, s, cmax, sink);
     return cudaGetLastError();
 }
 

@@ -35,7 +35,19 @@
 
 #include "ifa.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace ifa {
+
+// An NVTX range over a host call (segment push, drain, batch run, serving
+// step), so that a timeline (Nsight Systems, ncu's NVTX filters) shows the
+// library's steps; header-only, no cost without a tool attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kWarp = 32;
 constexpr uint32_t kSPerEntry = 0xffffffffu;  // launch threshold: use each entry's own s_e
@@ -200,9 +212,9 @@ __device__ inline uint32_t find_piece(const DevPiece *pc, uint32_t n, uint64_t p
 // ---------------------------------------------------------------- launchers
 // (defined in the .cu files; all enqueue on `st`)
 
-// Soft-clipped windows at contig ends (clip.cu).
+// Soft-clipped windows at contig ends (clip.cu), for entries [e_base, e_base + nent) of qt.
 cudaError_t launch_clip_scan(const Batch &b, const QueryTable &qt, uint32_t nent, uint32_t clip_pct, uint32_t s,
-                             uint32_t lmax, const HitSink &sink, cudaStream_t st);
+                             uint32_t lmax, const HitSink &sink, cudaStream_t st, uint32_t e_base = 0);
 
 // Tensor-core brute-force scan (scan_tc.cu): queries up to 64 bases.
 uint32_t tc_lpad(uint32_t lmax);

@@ -97,8 +97,8 @@ cudaError_t launch_t(const Batch &b, const QueryTable &qt, uint32_t e0, uint32_t
 }  // namespace
 
 uint32_t scan_brute_chunk_entries(uint32_t wmax) {
-    const size_t n = kScanSmemBudget / entry_smem(static_cast<int>(wmax));
-    return static_cast<uint32_t>(n < 65535 ? n : 65535);
+    const uint32_t n = chunk_cap(static_cast<int>(wmax));
+    return n < 65535u ? n : 65535u;
 }
 
 cudaError_t launch_scan_brute(const Batch &b, const QueryTable &qt, uint32_t e0, uint32_t e1,

@@ -55,6 +55,11 @@ __host__ __device__ constexpr size_t entry_smem(int wmax) {
     return wmax * sizeof(uint4) + 2 * sizeof(uint4) + 2 * sizeof(uint32_t) + 2 * sizeof(uint16_t);
 }
 
+// The most entries of one chunk that fit the shared-memory budget.
+__host__ __device__ constexpr uint32_t chunk_cap(int wmax) {
+    return static_cast<uint32_t>(kScanSmemBudget / entry_smem(wmax));
+}
+
 struct Smem {
     uint4 *sq;         // entries x WMAX full words
     uint4 *sM;         // class M: {hi0, lo0, care0, threshold}

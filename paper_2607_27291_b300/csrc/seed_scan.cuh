@@ -89,12 +89,29 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                             uint32_t x[WMAX + 1];
                             uint32_t bnd = 0;
                             mm = 0;
-                            uint4 cur = ref_word(b, w0);
+                            // the window's words w0 .. w0 + W: hi/lo words, and
+                            // the N / piece-start masks only when the directory
+                            // marks one of them special
+                            const uint2 d0 = __ldg(b.dir + (w0 >> 5)), d1 = __ldg(b.dir + (w0 >> 5) + 1);
+                            const bool spec = special_bits(d0.x, d1.x, w0, W + 1) != 0u;
+                            uint4 cur;
+                            if (spec) {
+                                cur = ref_word(b, w0);
+                            } else {
+                                const uint2 h0 = __ldg(b.hl + w0);
+                                cur = make_uint4(h0.x, h0.y, 0u, 0u);
+                            }
 #pragma unroll
                             for (int w = 0; w < WMAX; w++) {
                                 x[w] = 0;
                                 if (w < static_cast<int>(W)) {
-                                    const uint4 nx = ref_word(b, w0 + w + 1);
+                                    uint4 nx;
+                                    if (spec) {
+                                        nx = ref_word(b, w0 + w + 1);
+                                    } else {
+                                        const uint2 h2 = __ldg(b.hl + w0 + w + 1);
+                                        nx = make_uint4(h2.x, h2.y, 0u, 0u);
+                                    }
                                     const uint32_t rh = __funnelshift_r(cur.x, nx.x, sh);
                                     const uint32_t rl = __funnelshift_r(cur.y, nx.y, sh);
                                     const uint32_t rn = __funnelshift_r(cur.z, nx.z, sh);

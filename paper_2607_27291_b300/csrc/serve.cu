@@ -157,7 +157,7 @@ ifa_status build_serve_plan(ifa_handle *h) {
             ids.push_back(2 * q);
             ids.push_back(2 * q + 1);
         }
-    uint32_t cap = brute::kScanSmemBudget / brute::entry_smem(static_cast<int>(wmax));
+    uint32_t cap = brute::chunk_cap(static_cast<int>(wmax));
     cap = std::min<uint32_t>(cap, 65535) & ~1u;
     std::vector<uint32_t> c0, c1, cl, ch;
     for (uint32_t a = 0; a < ids.size(); a += cap) {
@@ -341,6 +341,7 @@ ifa_status ifa_serve_submit(ifa_handle *h, const uint8_t *const *seqs, const uin
 }
 
 ifa_status ifa_serve_step(ifa_handle *h, uint32_t *n_active, uint32_t *n_completed) {
+    const NvtxRange nvtx("ifa_serve_step");
     if (!h) return IFA_ERR_INVALID_ARG;
     ServeState &S = h->serve;
     if (!S.on) return sfail(h, IFA_ERR_BAD_STATE, "ifa_serve_step: call ifa_serve_start first");

@@ -88,7 +88,67 @@ cudaError_t launch(int grid, const uint32_t *in, uint64_t trips, uint32_t *out, 
     return cudaGetLastError();
 }
 
+// Random gathers: every thread loads `per_thread` 32-bit words at
+// independent pseudo-random offsets (a multiplicative hash of its index) of
+// a table of `words` words, summing them so that no load is dead.  The rate
+// of such loads bounds a table lookup per reference position (the seed
+// scan's k-mer offsets).
+__global__ void __launch_bounds__(256) k_gather(const uint32_t *__restrict__ table, uint64_t words,
+                                                uint32_t per_thread, uint32_t *__restrict__ out) {
+    const uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    uint64_t x = t * 0x9E3779B97F4A7C15ull + 1;
+    for (uint32_t i = 0; i < per_thread; i++) {
+        x = x * 6364136223846793005ull + 1442695040888963407ull;   // Knuth's MMIX LCG step
+        acc += __ldg(table + ((x >> 20) % words));
+    }
+    out[t] = acc;
+}
+
 }  // namespace
+
+// Random 32-bit gathers per second from a device table of `table_bytes`
+// (filled once), `per_thread` loads per thread over a grid of 148 x 8
+// blocks; outputs the rate (loads/s) and the kernel's event time.
+extern "C" int ifa_probe_gather_rate(int device, uint64_t table_bytes, uint32_t per_thread, double *loads_per_s,
+                                     double *ms) {
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const uint64_t words = table_bytes / 4;
+    if (words == 0 || per_thread == 0) return 1;
+    const int grid = sms * 8;
+    uint32_t *table = nullptr, *out = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    e = cudaMalloc(&table, words * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&out, static_cast<size_t>(grid) * 256 * 4);
+    if (e == cudaSuccess) e = cudaMemset(table, 1, words * 4);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) {
+        k_gather<<<grid, 256>>>(table, words, per_thread < 64 ? per_thread : 64, out);  // warm-up
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(a);
+    if (e == cudaSuccess) {
+        k_gather<<<grid, 256>>>(table, words, per_thread, out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    if (e == cudaSuccess) {
+        *ms = t;
+        *loads_per_s = static_cast<double>(grid) * 256.0 * per_thread / (t * 1e-3);
+    }
+    cudaFree(table);
+    cudaFree(out);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return e;
+}
 
 // Measure one instruction kind (0 popc, 1 lop3, 2 shf, 3 imad) with
 // `blocks_per_sm` resident blocks of 256 threads on every SM for `trips`
@@ -179,4 +239,53 @@ extern "C" int ifa_probe_pipe_rate(int device, int kind, int blocks_per_sm, uint
     *ms = t_ms;
     *sm_mhz = t_ms > 0.f ? static_cast<double>(busiest) / (t_ms * 1e3) : 0.0;
     return 0;
+}
+
+// Pinned host <-> device copy rate with cudaMemcpyAsync (the call the
+// library streams segments with): `bytes` per copy between cudaHostAlloc
+// memory and device memory, to_device selecting the direction; outputs the
+// best of `reps` single copies and the rate of `reps` copies back to back on
+// one stream, in GB/s.
+extern "C" int ifa_probe_copy_rate(int device, uint64_t bytes, int to_device, int reps, double *best_gbps,
+                                   double *b2b_gbps) {
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return e;
+    if (bytes == 0 || reps < 1) return 1;
+    void *hbuf = nullptr, *dbuf = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    e = cudaHostAlloc(&hbuf, bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(&dbuf, bytes);
+    if (e == cudaSuccess) e = cudaMemset(dbuf, 0, bytes);
+    if (e == cudaSuccess) std::memset(hbuf, 1, bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    const cudaMemcpyKind kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    void *dst = to_device ? dbuf : hbuf;
+    const void *src = to_device ? hbuf : dbuf;
+    float best = 1e30f, t = 0.f;
+    for (int i = 0; i <= reps && e == cudaSuccess; i++) {  // the first copy is a warm-up
+        e = cudaEventRecord(a, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, kind, st);
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        if (e == cudaSuccess && i > 0 && t < best) best = t;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(a, st);
+    for (int i = 0; i < reps && e == cudaSuccess; i++) e = cudaMemcpyAsync(dst, src, bytes, kind, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    if (e == cudaSuccess) {
+        *best_gbps = static_cast<double>(bytes) / (best * 1e-3) / 1e9;
+        *b2b_gbps = static_cast<double>(bytes) * reps / (t * 1e-3) / 1e9;
+    }
+    cudaFreeHost(hbuf);
+    cudaFree(dbuf);
+    if (st) cudaStreamDestroy(st);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return e;
 }

@@ -490,6 +490,11 @@ def workload_serving(total: int, rate: float, duration: float, seed: int = 5):
     10 Mbp).  Returns (ref, lens, [(arrival_s, queries, max_subs)])."""
     lens = contig_lengths(total, 1000, 10_000_000, "loguniform", seed)
     ref, _ = per_contig_reference(lens, 0.45, 0.45, seed, n_frac=0.0005)
+    return ref, lens, serving_requests(rate, duration, seed)
+
+
+def serving_requests(rate: float, duration: float, seed: int = 5):
+    """The serving workload's requests alone: [(arrival_s, queries, max_subs)]."""
     rng = _rng(seed, _S_QUERIES, 8)
     t = 0.0
     arrivals = []
@@ -499,4 +504,127 @@ def workload_serving(total: int, rate: float, duration: float, seed: int = 5):
             break
         arrivals.append(t)
     sets = query_sets(len(arrivals), 1, 2000, 18, 50, 8, seed)
-    return ref, lens, [(a, qs, s) for a, (qs, s) in zip(arrivals, sets)]
+    return [(a, qs, s) for a, (qs, s) in zip(arrivals, sets)]
+
+
+# ------------------------------------------- counter-based reference (any size)
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+
+
+def _splitmix_out(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def gc_thresholds(gc: float):
+    """(t1, t2, t3) of the counter-based generator for a GC fraction."""
+    return (int((1.0 - gc) / 2.0 * 2 ** 32), 1 << 31, min(int((1.0 + gc) / 2.0 * 2 ** 32), 2 ** 32 - 1))
+
+
+def counter_bases(first: int, n: int, seed: int, gc: float) -> np.ndarray:
+    """Bases [first, first + n) of a reference whose base i is drawn from the
+    high 32 bits u of splitmix64's output function at i + seed * 0x9E3779B97F4A7C15
+    (A below t1, C below t2, G below t3, else T; see gc_thresholds).  Any
+    slice is regenerated alone; synth/devgen.cu writes the same bytes on the
+    device."""
+    with np.errstate(over="ignore"):
+        key = np.uint64(seed) * _GOLDEN
+        i = np.arange(first, first + n, dtype=np.uint64) + key
+        u = (_splitmix_out(i) >> np.uint64(32)).astype(np.uint32)
+    t1, t2, t3 = gc_thresholds(gc)
+    code = (u >= np.uint32(t1)).astype(np.uint8)
+    code += u >= np.uint32(t2)
+    code += u >= np.uint32(t3)
+    return _ACGT[code]
+
+
+def n_run_list(total: int, frac: float, seed: int):
+    """Disjoint N-runs (lengths uniform in [10, 1000], uniform positions)
+    covering `frac` of `total` bases: sorted (starts, lengths) arrays."""
+    rng = _rng(seed, _S_NRUNS, 2)
+    target = int(frac * total)
+    starts, lens_ = [], []
+    done = 0
+    occ = _Occupied()
+    while done < target:
+        m = max(64, (target - done) // 400)
+        L = rng.integers(10, 1001, size=m)
+        A = rng.integers(0, max(1, total - 1000), size=m)
+        for a, l in zip(A.tolist(), L.tolist()):
+            if done >= target:
+                break
+            if occ.free(a, a + l):
+                occ.add(a, a + l)
+                starts.append(a)
+                lens_.append(l)
+                done += l
+    order = np.argsort(np.asarray(starts, np.int64))
+    return np.asarray(starts, np.uint64)[order], np.asarray(lens_, np.uint32)[order]
+
+
+@dataclasses.dataclass
+class CounterReference:
+    """A reference defined by counters rather than stored: contig lengths,
+    the GC fraction, the base seed and the N-runs; bases(a, b) gives any
+    slice (host), and synth.devgen fills a device buffer with the same
+    bytes."""
+    contig_len: np.ndarray
+    gc: object                 # a float, or one GC fraction per contig
+    seed: int
+    run_start: np.ndarray
+    run_len: np.ndarray
+
+    @property
+    def total(self) -> int:
+        return int(self.contig_len.sum())
+
+    @property
+    def contig_start(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum(self.contig_len)[:-1]]).astype(np.int64)
+
+    def gc_spans(self, a: int, b: int):
+        """[(lo, hi, gc)] covering [a, b): one span, or one per contig."""
+        if np.isscalar(self.gc):
+            return [(a, b, float(self.gc))]
+        st = self.contig_start
+        i = int(np.searchsorted(st, a, side="right")) - 1
+        out = []
+        while a < b:
+            end = min(b, int(st[i] + self.contig_len[i]))
+            out.append((a, end, float(self.gc[i])))
+            a = end
+            i += 1
+        return out
+
+    def bases(self, a: int, b: int) -> np.ndarray:
+        out = np.concatenate([counter_bases(lo, hi - lo, self.seed, g) for lo, hi, g in self.gc_spans(a, b)])
+        i0 = int(np.searchsorted(self.run_start, a, side="left"))
+        i0 = max(0, i0 - 1)
+        for s_, l_ in zip(self.run_start[i0:].tolist(), self.run_len[i0:].tolist()):
+            if s_ >= b:
+                break
+            lo, hi = max(a, s_), min(b, s_ + l_)
+            if lo < hi:
+                out[lo - a:hi - a] = ord("N")
+        return out
+
+
+def sets_reference(total: int = 16_000_000_000, seed: int = 4) -> CounterReference:
+    """The batched workload's reference recipe, counter-based: log-uniform
+    contigs of 1 kbp - 10 Mbp, each with its own GC drawn uniform in
+    [0.30, 0.65], no N."""
+    lens = contig_lengths(total, 1000, 10_000_000, "loguniform", seed)
+    gc = _rng(seed, _S_GC, 2).uniform(0.30, 0.65, size=len(lens))
+    return CounterReference(lens, gc, seed, np.zeros(0, np.uint64), np.zeros(0, np.uint32))
+
+
+def serving_reference(total: int = 200_000_000_000, seed: int = 5) -> CounterReference:
+    """The serving workload's reference at any size: log-uniform contigs of
+    1 kbp - 10 Mbp, GC 45%, 0.05% N in runs of 10-1000 -- counter-based so
+    that 200 Gbp is built on the device and any slice regenerated on the
+    host."""
+    lens = contig_lengths(total, 1000, 10_000_000, "loguniform", seed)
+    rs, rl = n_run_list(int(lens.sum()), 0.0005, seed)
+    return CounterReference(lens, 0.45, seed, rs, rl)

@@ -134,3 +134,45 @@ def test_per_set_subs_at_query_length():
     assert len([x for x in expect if x[0] == firsts[0]]) == 2 * (3000 - 127) + 2 * (2000 - 127)
     assert not [x for x in expect if x[0] == firsts[1] and x[1] == 0]
     assert tuples(P.sort_hits(hits)) == sorted(expect)
+
+
+def _tuples6(h):
+    return sorted(zip(h["query"].tolist(), h["contig"].tolist(), h["pos"].tolist(),
+                      h["strand"].tolist(), h["mismatches"].tolist(), h["clips"].tolist()))
+
+
+def test_soft_clipping_in_batches():
+    """Soft clipping at contig ends (25 % of the query length) in both batch
+    kinds: every set, brute force or indexed, reports the clipped windows at
+    its own maxSubs (exhaustively, as in streaming), with contigs cut across
+    appends, exactly as the oracle."""
+    wl = synth.small_workload(seed=79, n_queries=2, lmin=12, lmax=40, n_contigs=40, cmin=3,
+                              cmax=3000, plant_ks=[0, 1, 2] * 4)
+    sets = [(synth.random_queries(5, 6, 12, 201), 2, P.IFA_MODE_BRUTE),
+            (synth.random_queries(6, 10, 16, 202), 2, P.IFA_MODE_INDEXED),
+            (wl.queries + synth.random_queries(3, 8, 14, 203), 3, P.IFA_MODE_BRUTE)]
+    got = {}
+    h = P.ifa_create(hit_capacity=1 << 22, segment_bytes=1 << 20, minhits_trials=TRIALS, clip_pct=25)
+    try:
+        _store(h, wl, 1024)
+        firsts = [P.ifa_set_add(h, qs, s, mode)[1] for qs, s, mode in sets]
+        for kind in (P.IFA_BATCH_PERSISTENT, P.IFA_BATCH_PER_SET):
+            P.ifa_reset_results(h)
+            P.ifa_batch_run(h, kind, len(sets))
+            hits, over = P.ifa_drain_hits(h)
+            assert not over
+            got[kind] = _tuples6(hits)
+    finally:
+        P.ifa_destroy(h)
+    expect = []
+    for (qs, s, mode), first in zip(sets, firsts):
+        if mode == P.IFA_MODE_BRUTE:
+            e = oracle.brute(qs, wl.ref, wl.contig_len, s, clip_pct=25)
+        else:
+            plan = [oracle.choose_k(len(q), s, trials=TRIALS) for q in qs]
+            e = oracle.indexed(qs, wl.ref, wl.contig_len, s, [p[1] for p in plan], [p[2] for p in plan],
+                               [1 if p[0] < 0 else 0 for p in plan], clip_pct=25)
+        expect.extend(_tuples6(_shift(e, first)))
+    assert any(x[5] for x in expect)                 # clipped hits are in the case
+    assert got[P.IFA_BATCH_PERSISTENT] == sorted(expect)
+    assert got[P.IFA_BATCH_PER_SET] == sorted(expect)

@@ -196,3 +196,20 @@ def test_1mbp_x10_planted():
     for p in wl.plants:
         assert (p.query, p.contig, p.pos, p.strand, p.k) in have
     assert stats["windows"] == 2 * 10 * (1_000_000 - 20 + 1)
+
+
+@pytest.mark.parametrize("s", [12, 16])
+def test_candidates_staged_across_fast_and_generic_blocks(s):
+    """At high maxSubs a third of the hot loop's groups fire and leave
+    candidate events in the warp's staging buffer; blocks holding an N or a
+    contig start (frequent here) take the generic path and may flush that
+    buffer.  Every hit must still equal the oracle's."""
+    wl = synth.small_workload(seed=83, n_queries=10, lmin=30, lmax=40, n_contigs=300, cmin=20,
+                              cmax=12000, n_frac=0.01, plant_ks=[0, 4, 8, 12, 16] * 4)
+    got, over, dig, counts, _ = gpu_scan(wl.queries, wl.ref, wl.contig_len, s, seg_bytes=1 << 19,
+                                         brute_kernel=P.IFA_BRUTE_POPC, hit_capacity=1 << 22)
+    exp = oracle.brute(wl.queries, wl.ref, wl.contig_len, s, threads=8)
+    assert not over and exp.size > 100
+    assert tuples(got) == tuples(exp)
+    assert dig == oracle.digest(exp)
+    assert counts.tolist() == np.bincount(exp["query"], minlength=len(wl.queries)).tolist()

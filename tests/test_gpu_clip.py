@@ -86,15 +86,13 @@ def test_tensor_kernel_with_clipping():
     assert tuples6(got) == tuples6(exp)
 
 
-def test_batching_and_serving_reject_clipping():
+def test_serving_rejects_clipping():
+    """Batching applies soft clipping (tests/test_gpu_batch.py); the serving
+    loop does not, and says so."""
     h = P.ifa_create(hit_capacity=1024, segment_bytes=1 << 16, clip_pct=25)
     try:
         ref = np.frombuffer(b"ACGT" * 64, np.uint8).copy()
         P.ifa_ref_append(h, ref, [(0, 0, 0, 256, True)])
-        P.ifa_set_add(h, [b"ACGTACGTAC"], 1, P.IFA_MODE_BRUTE)
-        with pytest.raises(P.IfaError) as ei:
-            P.ifa_batch_run(h, P.IFA_BATCH_PERSISTENT, 1)
-        assert ei.value.status == P.IFA_ERR_INVALID_ARG
         with pytest.raises(P.IfaError) as ei:
             P.ifa_serve_start(h, 4, 1 << 30, 1024)
         assert ei.value.status == P.IFA_ERR_INVALID_ARG

@@ -148,3 +148,130 @@ def test_1gbp_plan_matches_oracle(wl1g):
                 assert (k[i], m[i], ex[i]) == (kk, mm, 1 if st < 0 else 0)
     finally:
         P.ifa_destroy(h)
+
+
+# ------------------------------- device-resident stores past 2^32 bases
+
+def _append_counter_contigs(h, ref, keep=None, chunk=256 << 20):
+    """Append the contigs of a synth.CounterReference (those with keep[i],
+    default all) to the handle's store, each 256 MB chunk generated on the
+    device; contig ids stay the reference's."""
+    import torch
+    from synth.devgen import DeviceFiller
+    lens = ref.contig_len
+    keep = np.ones(len(lens), bool) if keep is None else keep
+    ids = np.nonzero(keep)[0]
+    klens = lens[ids]
+    ost = ref.contig_start[ids]                                  # original starts
+    rst = np.concatenate([[0], np.cumsum(klens)[:-1]]).astype(np.int64)   # starts in the store
+    fill = DeviceFiller(ref)
+    P.ifa_ref_reserve(h, int(klens.sum()))
+    buf = torch.empty(chunk, dtype=torch.uint8, device="cuda")
+    for ra, rb, pc in P.segment_pieces(klens, chunk, contig_ids=ids):
+        j = int(np.searchsorted(rst, ra, side="right")) - 1
+        x = ra
+        while x < rb:
+            end = min(rb, int(rst[j] + klens[j]))
+            fill.fill(buf[x - ra:end - ra], int(ost[j] + (x - rst[j])))
+            x = end
+            j += 1
+        torch.cuda.synchronize()
+        P.ifa_ref_append(h, buf[:rb - ra], pc)
+    torch.cuda.synchronize()
+
+
+def _sets(n, seed):
+    sets = synth.query_sets(n, 1, 5000, 18, 50, 12, seed)
+    return [(qs, s, P.IFA_MODE_BRUTE if len(qs) < 150 else P.IFA_MODE_INDEXED) for qs, s in sets]
+
+
+def _batch_digest(ref, sets, keep=None):
+    h = P.ifa_create(count_only=1, segment_bytes=256 << 20, minhits_trials=TRIALS_1G, minhits_seed=1)
+    try:
+        _append_counter_contigs(h, ref, keep)
+        for qs, s, mode in sets:
+            P.ifa_set_add(h, qs, s, mode)
+        res = P.ifa_batch_run(h, P.IFA_BATCH_PERSISTENT, len(sets))
+        assert [int(m) for m in res["mode"]] == [m for _, _, m in sets]
+        return P.ifa_get_digest(h, sum(len(qs) for qs, _, _ in sets))
+    finally:
+        P.ifa_destroy(h)
+
+
+def test_16gbp_store_batch_digest_difference():
+    """The batched workload's store (16 Gbp: past 2^32 bases, so store
+    offsets need 64 bits), 32 query sets (sizes log-uniform 1-5000, 18-50 bp,
+    maxSubs 0-12; brute force below 150 queries, indexed above) in one
+    persistent launch, count only.  Dropping three sampled contigs -- the
+    two shortest and the shortest one starting past base 2^32 -- must change
+    the digest and the per-query counts by exactly the oracle's hits on
+    them."""
+    ref = synth.sets_reference(16_000_000_000)
+    assert ref.total > (1 << 32)
+    st = ref.contig_start
+    far = np.nonzero(st > (1 << 32) + (1 << 20))[0]
+    sample = sorted(set(np.argsort(ref.contig_len)[:2].tolist()) |
+                    {int(far[np.argmin(ref.contig_len[far])])})
+    sets = _sets(32, 4)
+    full, cfull = _batch_digest(ref, sets)
+    keep = np.ones(len(ref.contig_len), bool)
+    keep[sample] = False
+    rest, crest = _batch_digest(ref, sets, keep)
+    diff = (full[0] - rest[0], (full[1] - rest[1]) % (1 << 64), full[2] ^ rest[2])
+    sub = np.concatenate([ref.bases(int(st[c]), int(st[c] + ref.contig_len[c])) for c in sample])
+    lens = ref.contig_len[sample]
+    parts, first = [], 0
+    for qs, s, mode in sets:
+        if mode == P.IFA_MODE_BRUTE:
+            e = oracle.brute(qs, sub, lens, s, contig_ids=sample, threads=16)
+        else:
+            by_len = {L: oracle.choose_k(L, s, trials=TRIALS_1G, seed=1) for L in {len(q) for q in qs}}
+            plan = [by_len[len(q)] for q in qs]
+            e = oracle.indexed(qs, sub, lens, s, [p[1] for p in plan], [p[2] for p in plan],
+                               [1 if p[0] < 0 else 0 for p in plan], contig_ids=sample, threads=16)
+        e = e.copy()
+        e["query"] += first
+        parts.append(e)
+        first += len(qs)
+    exp = np.concatenate(parts)
+    assert diff == oracle.digest(exp)
+    assert (cfull - crest).tolist() == np.bincount(exp["query"], minlength=first).tolist()
+
+
+def test_200gbp_serving_store_sampled_parity():
+    """The serving workload's store at its stated size: 200 Gbp generated on
+    the device into the 2-bit store (about 50 GB of HBM).  Two requests
+    served by continuous batching for a full cycle; their hits on sampled
+    contigs (the three shortest and five seeded others up to 200 kbp,
+    regenerated on the host) equal the oracle's, and their digests count
+    every hit drained."""
+    import torch
+    ref = synth.serving_reference(200_000_000_000)
+    h = P.ifa_create(hit_capacity=1024, segment_bytes=256 << 20, minhits_trials=TRIALS_1G, minhits_seed=1)
+    try:
+        free0, _ = torch.cuda.mem_get_info()
+        _append_counter_contigs(h, ref)
+        used = free0 - torch.cuda.mem_get_info()[0]
+        assert used < 0.27 * ref.total                   # 2 bits per base plus the sparse tables
+        rq = [(synth.random_queries(4, 24, 30, 91), 3), (synth.random_queries(3, 28, 34, 92), 5)]
+        P.ifa_serve_start(h, 16, 8 << 30, 1 << 22)
+        ids = [P.ifa_serve_submit(h, qs, s, P.IFA_MODE_AUTO) for qs, s in rq]
+        while P.ifa_serve_step(h)[0]:     # both are admitted at the first step
+            pass
+        rng = np.random.default_rng(17)
+        small = np.nonzero(ref.contig_len <= 200_000)[0]
+        sample = sorted(set(np.argsort(ref.contig_len)[:3].tolist()) |
+                        set(rng.choice(small, size=5, replace=False).tolist()))
+        st = ref.contig_start
+        sub = np.concatenate([ref.bases(int(st[c]), int(st[c] + ref.contig_len[c])) for c in sample])
+        for rid, (qs, s) in zip(ids, rq):
+            info = P.ifa_serve_poll(h, rid)
+            assert info["state"] == 2 and not info["overflowed"]
+            hits, over = P.ifa_serve_drain(h, rid, 1 << 22)
+            assert not over and hits.size == info["digest"][0] == info["hits"]
+            mine = P.sort_hits(hits[np.isin(hits["contig"], sample)])
+            exp = oracle.brute(qs, sub, ref.contig_len[sample], s, contig_ids=sample, threads=16)
+            assert tuples(mine) == tuples(exp)
+        P.ifa_serve_stop(h)
+    finally:
+        P.ifa_destroy(h)
