@@ -208,6 +208,15 @@ def popc_rate():
     raise RuntimeError("no popc_per_clk_sm line in " + PIPE_RATES_MD)
 
 
+def gather_rate():
+    """Random 32-bit gathers per second from an L2-resident table, from the
+    committed microbenchmark record (bench.py --workload pipe-rates)."""
+    for line in open(PIPE_RATES_MD):
+        if line.strip().startswith("random_gather_l2_per_s:"):
+            return float(line.split(":", 1)[1])
+    raise RuntimeError("no random_gather_l2_per_s line in " + PIPE_RATES_MD)
+
+
 def pcie_peaks(dev, mb=256, reps=10):
     """Pinned host <-> device copy rates of `mb` MiB (GB/s): the best of `reps`
     single cudaMemcpyAsync copies from cudaHostAlloc memory and `reps` copies
@@ -908,6 +917,19 @@ def indexed_result(total, steps, warmup, brute=True):
             res[name] = {"ms": ms, "effective_qbase_per_s": qb / (ms * 1e-3), "hits": dg[0],
                          "candidates": st["candidates"],
                          "candidates_per_s": st["candidates"] / (ms * 1e-3)}
+            if name == "indexed":
+                # roofline: random L2 accesses -- one k-mer lookup per position
+                # and seeded table, one candidate window per verification --
+                # against the measured random-gather rate
+                kq, _, exq = P.ifa_get_query_plan(h, len(wl.queries))
+                tables = len({int(k) for k, x in zip(kq, exq) if not x})
+                acc = float(wl.ref.size) * tables + float(st["candidates"])
+                peak = gather_rate()
+                res[name]["roofline"] = {"bound": "l2 random access", "achieved": acc / (ms * 1e-3),
+                                         "peak": peak, "unit": "accesses/s", "frac": acc / (ms * 1e-3) / peak,
+                                         "tables": tables,
+                                         "peak_basis": "random 32-bit gathers from an L2-resident table, "
+                                                       "profiles/int_pipe_rates.md"}
         P.ifa_destroy(h)
         del dev
         torch.cuda.empty_cache()

@@ -229,6 +229,11 @@ void free_plan(BatchState &B) {
     B.graph = nullptr;
     B.graph_stream = nullptr;
     B.plan_valid = false;
+    B.tc_rows = 0;
+    B.d_tcA = nullptr;
+    B.d_tcmeta = nullptr;
+    B.d_tcids = nullptr;
+    B.d_tcstatus = nullptr;
 }
 
 template <typename T>
@@ -319,6 +324,50 @@ ifa_status build_plan(ifa_handle *h) {
         if (S.chosen == IFA_MODE_INDEXED)
             for (uint32_t q = S.first; q < S.first + S.n; q++) idx_in[q] = 1;
 
+    // brute-force sets the tensor cores scan: the streaming rule per set
+    // (queries of at most 64 bases, 32 queries or more, sparse hits), or
+    // every eligible one when the config forces the tensor cores
+    std::vector<uint8_t> on_tc(B.sets.size(), 0);
+    uint32_t tc_lmax = 0;
+    for (size_t si = 0; si < B.sets.size(); si++) {
+        const QuerySet &S = B.sets[si];
+        if (S.chosen != IFA_MODE_BRUTE || h->cfg.brute_kernel == IFA_BRUTE_POPC) continue;
+        uint32_t lmax = 0;
+        for (uint32_t q = S.first; q < S.first + S.n; q++) lmax = std::max<uint32_t>(lmax, h->qs[q].size());
+        const bool pick = h->cfg.brute_kernel == IFA_BRUTE_TENSOR ? tc_eligible(lmax)
+                                                                  : tc_auto_choice(h->qs, S.first, S.n, S.s);
+        if (pick) {
+            on_tc[si] = 1;
+            tc_lmax = std::max(tc_lmax, lmax);
+        }
+    }
+    // the tensor-core operand: each such set's queries, padded with empty
+    // ones to whole 128-row tiles (2 rows per query)
+    std::vector<std::string> tc_qs;
+    std::vector<uint32_t> tc_ids, tc_meta;
+    B.set_tc_row0.assign(B.sets.size(), 0);
+    B.set_tc_rows.assign(B.sets.size(), 0);
+    for (size_t si = 0; si < B.sets.size(); si++) {
+        if (!on_tc[si]) continue;
+        const QuerySet &S = B.sets[si];
+        B.set_tc_row0[si] = static_cast<uint32_t>(tc_ids.size());
+        for (uint32_t q = S.first; q < S.first + S.n; q++) {
+            tc_qs.push_back(h->qs[q]);
+            for (uint32_t t = 0; t < 2; t++) {
+                tc_ids.push_back(2 * q + t);
+                tc_meta.push_back(h->qmeta_host[2 * q + t]);
+            }
+        }
+        while (tc_ids.size() % 128) {
+            tc_qs.emplace_back();
+            tc_ids.insert(tc_ids.end(), {0u, 0u});
+            tc_meta.insert(tc_meta.end(), {0u, 0u});
+        }
+        B.set_tc_rows[si] = static_cast<uint32_t>(tc_ids.size()) - B.set_tc_row0[si];
+    }
+    B.tc_rows = static_cast<uint32_t>(tc_ids.size());
+    B.tc_lpad = B.tc_rows ? tc_lpad(tc_lmax) : 0;
+
     // compact brute table, set by set so each set's entries are contiguous
     std::vector<uint32_t> ids;
     B.set_bchunk_lo.assign(B.sets.size(), 0);
@@ -334,7 +383,7 @@ ifa_status build_plan(ifa_handle *h) {
     for (size_t si = 0; si < B.sets.size(); si++) {
         const QuerySet &S = B.sets[si];
         const uint32_t start = static_cast<uint32_t>(ids.size());
-        for (uint32_t q = S.first; q < S.first + S.n; q++) {
+        for (uint32_t q = S.first; q < S.first + S.n && !on_tc[si]; q++) {
             const bool brute = S.chosen == IFA_MODE_BRUTE || plan_all.plan_exhaustive[q];
             if (S.chosen == IFA_MODE_INDEXED && !plan_all.plan_exhaustive[q]) any_idx = true;
             if (!brute) continue;
@@ -388,6 +437,20 @@ ifa_status build_plan(ifa_handle *h) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(d_cl, B.bchunk_lmin.data(), nb, hd, h->stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync(d_ch, B.bchunk_lmax.data(), nb, hd, h->stream);
         }
+    }
+    if (e == cudaSuccess && B.tc_rows) {
+        std::vector<uint8_t> op;
+        tc_operand(tc_qs, B.tc_lpad, op);
+        B.d_tcA = plan_alloc<uint8_t>(h, op.size(), e);
+        B.d_tcmeta = plan_alloc<uint32_t>(h, B.tc_rows, e);
+        B.d_tcids = plan_alloc<uint32_t>(h, B.tc_rows, e);
+        B.d_tcstatus = plan_alloc<unsigned int>(h, 2, e);
+        const cudaMemcpyKind hd = cudaMemcpyHostToDevice;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.d_tcA, op.data(), op.size(), hd, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.d_tcmeta, tc_meta.data(), B.tc_rows * sizeof(uint32_t), hd, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.d_tcids, tc_ids.data(), B.tc_rows * sizeof(uint32_t), hd, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.d_tcstatus, 0, 2 * sizeof(unsigned int), h->stream);
+        if (e == cudaSuccess) e = tc_prepare();   // kernel attributes, outside any stream capture
     }
     if (e != cudaSuccess) return bfail(h, IFA_ERR_CUDA, std::string("batch plan: ") + cudaGetErrorString(e));
 
@@ -818,6 +881,10 @@ ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per
             if (e == cudaSuccess) {
                 cudaError_t e1 = cudaMemsetAsync(B.d_queue, 0, sizeof(unsigned int), h->stream);
                 cudaError_t e2 = launch_batch(B.wmax, b, B.work, bt, ft, sink, B.grid, smem, h->stream);
+                // the tensor-core sets, every row at its own maxSubs
+                if (e2 == cudaSuccess && B.tc_rows)
+                    e2 = launch_scan_tc(b, B.d_tcA, B.d_tcmeta, B.tc_rows, B.tc_lpad, kSPerEntry, sink,
+                                        B.d_tcstatus, h->stream, 0, B.d_tcids);
                 // soft-clipped windows at the store's contig ends, every set's
                 // entries at their own maxSubs, exhaustively in both modes
                 if (e2 == cudaSuccess && h->cfg.clip_pct)
@@ -834,6 +901,12 @@ ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per
     } else {
         for (size_t si = 0; si < B.sets.size() && e == cudaSuccess; si++) {
             const QuerySet &S = B.sets[si];
+            if (B.set_tc_rows[si]) {
+                const size_t r0 = B.set_tc_row0[si];
+                e = launch_scan_tc(b, B.d_tcA + r0 * 4u * B.tc_lpad, B.d_tcmeta + r0, B.set_tc_rows[si], B.tc_lpad,
+                                   kSPerEntry, sink, B.d_tcstatus, h->stream, 0, B.d_tcids + r0);
+                h->stats.kernel_launches += 1;
+            }
             for (uint32_t c = B.set_bchunk_lo[si]; c < B.set_bchunk_hi[si] && e == cudaSuccess; c++) {
                 int launches = 0;
                 e = launch_scan_brute(b, bt, B.bchunk_e0[c], B.bchunk_e1[c], kSPerEntry, B.bchunk_lmin[c],
@@ -881,6 +954,11 @@ ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per
     cudaEventDestroy(start);
     cudaEventDestroy(stop);
     if (e != cudaSuccess) return bfail(h, IFA_ERR_CUDA, std::string("ifa_batch_run: ") + cudaGetErrorString(e));
+    if (B.tc_rows) {
+        unsigned int tcs = 0;
+        BCK(h, cudaMemcpy(&tcs, B.d_tcstatus, sizeof(tcs), cudaMemcpyDeviceToHost));
+        if (tcs) return bfail(h, IFA_ERR_TIMEOUT, "ifa_batch_run: a tensor-core pipeline wait gave up; results incomplete");
+    }
     return IFA_OK;
 }
 

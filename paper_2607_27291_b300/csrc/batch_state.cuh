@@ -68,6 +68,14 @@ struct BatchState {
     uint32_t b_entries = 0;
     std::vector<uint32_t> bchunk_e0, bchunk_e1, bchunk_lmin, bchunk_lmax;
     std::vector<uint32_t> set_bchunk_lo, set_bchunk_hi;  // per set: its brute chunks
+    // brute-force sets on the tensor cores: one one-hot operand of every such
+    // set's entries, each set padded to whole 128-row tiles (rows of length
+    // 0), with the rows' metas and entry ids
+    uint32_t tc_rows = 0, tc_lpad = 0;
+    std::vector<uint32_t> set_tc_row0, set_tc_rows;    // per set: its rows (0 rows: popcount kernel)
+    uint8_t *d_tcA = nullptr;
+    uint32_t *d_tcmeta = nullptr, *d_tcids = nullptr;
+    unsigned int *d_tcstatus = nullptr;                // [0] a wait gave up, [1] work counter
     IndexedState merged;                  // all indexed sets together
     std::vector<std::unique_ptr<IndexedState>> per_set;  // each indexed set alone (per-set runs)
     BatchWork work{};

@@ -284,17 +284,6 @@ double random_window_hit_rate(uint32_t L, uint32_t s) {
     return sum;
 }
 
-// Mean of that probability over the query set: the expected share of
-// (entry, window) pairs that are hits on a random reference.
-double mean_window_hit_rate(const ifa_handle *h) {
-    if (h->qs.empty()) return 0.0;
-    double rate[kTcMaxQueryBases + 1];
-    for (uint32_t L = 0; L <= kTcMaxQueryBases; L++) rate[L] = random_window_hit_rate(L, h->max_subs);
-    double sum = 0.0;
-    for (const auto &q : h->qs) sum += q.size() <= kTcMaxQueryBases ? rate[q.size()] : 1.0;
-    return sum / static_cast<double>(h->qs.size());
-}
-
 // Above this mean hit rate the popcount kernel's per-hit path wins
 // (256 Mbp, 2048 queries: tensor cores 1.35-1.6x faster at a mean rate of
 // 0.7-0.8e-4, 0.6x at 1.3e-3).
@@ -303,11 +292,31 @@ constexpr double kTcAutoMaxHitRate = 2e-4;
 bool use_tensor_cores(const ifa_handle *h) {
     if (!h->d_tcA) return false;
     if (h->cfg.brute_kernel == IFA_BRUTE_TENSOR) return true;
-    return h->cfg.brute_kernel == IFA_BRUTE_AUTO && 2 * h->qs.size() >= kTcAutoEntries &&
-           mean_window_hit_rate(h) <= kTcAutoMaxHitRate;
+    return h->cfg.brute_kernel == IFA_BRUTE_AUTO &&
+           tc_auto_choice(h->qs, 0, static_cast<uint32_t>(h->qs.size()), h->max_subs);
 }
 
 }  // namespace
+
+namespace ifa {
+// Mean of that probability over the queries: the expected share of (entry,
+// window) pairs that are hits on a random reference.
+double mean_window_hit_rate(const std::vector<std::string> &qs, uint32_t first, uint32_t n, uint32_t s) {
+    if (n == 0) return 0.0;
+    double rate[kTcMaxQueryBases + 1];
+    for (uint32_t L = 0; L <= kTcMaxQueryBases; L++) rate[L] = random_window_hit_rate(L, s);
+    double sum = 0.0;
+    for (uint32_t q = first; q < first + n; q++)
+        sum += qs[q].size() <= kTcMaxQueryBases ? rate[qs[q].size()] : 1.0;
+    return sum / static_cast<double>(n);
+}
+
+bool tc_auto_choice(const std::vector<std::string> &qs, uint32_t first, uint32_t n, uint32_t s) {
+    uint32_t lmax = 0;
+    for (uint32_t q = first; q < first + n; q++) lmax = std::max<uint32_t>(lmax, static_cast<uint32_t>(qs[q].size()));
+    return tc_eligible(lmax) && 2 * n >= kTcAutoEntries && mean_window_hit_rate(qs, first, n, s) <= kTcAutoMaxHitRate;
+}
+}  // namespace ifa
 
 // ------------------------------------------------------------------------ API
 

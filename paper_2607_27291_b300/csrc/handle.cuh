@@ -117,6 +117,11 @@ cudaError_t launch_batch_kernel(uint32_t wmax, const Batch &b, const BatchWork &
 int batch_kernel_grid(uint32_t wmax);
 void encode_entry(const std::string &q, bool rc, uint32_t wmax, uint32_t s_e, uint4 *out, uint32_t *meta);
 void tc_operand(const std::vector<std::string> &qs, uint32_t lpad, std::vector<uint8_t> &out);
+// Mean over queries [first, first + n) of the probability that a random
+// window (uniform bases) hits at maxSubs s; and whether the tensor-core
+// kernel should scan such a brute-force query set (the automatic rule).
+double mean_window_hit_rate(const std::vector<std::string> &qs, uint32_t first, uint32_t n, uint32_t s);
+bool tc_auto_choice(const std::vector<std::string> &qs, uint32_t first, uint32_t n, uint32_t s);
 // Free the serving state.
 void serve_release(ifa_handle *h);
 }  // namespace ifa

@@ -219,9 +219,14 @@ cudaError_t launch_clip_scan(const Batch &b, const QueryTable &qt, uint32_t nent
 // Tensor-core brute-force scan (scan_tc.cu): queries up to 64 bases.
 uint32_t tc_lpad(uint32_t lmax);
 bool tc_eligible(uint32_t lmax);
+// Set the tensor-core kernel's attributes on the current device (once;
+// before a stream capture that launches it).
+cudaError_t tc_prepare();
+// ids (may be null: identity) maps operand row e to the entry id it scans;
+// rows of length 0 (padding) never hit.
 cudaError_t launch_scan_tc(const Batch &b, const uint8_t *tcA, const uint32_t *meta, uint32_t nent, uint32_t lpad,
                            uint32_t s, const HitSink &sink, unsigned int *status, cudaStream_t st,
-                           uint32_t withhold_first = 0);
+                           uint32_t withhold_first = 0, const uint32_t *ids = nullptr);
 
 // ASCII -> hl words [0, nwords_padded) and their {N, B = 0} masks in nb.
 cudaError_t launch_pack(const uint8_t *halo, uint32_t hlen, uint32_t H, const uint8_t *seg,

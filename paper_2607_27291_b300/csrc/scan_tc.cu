@@ -221,7 +221,8 @@ __device__ __noinline__ void emit_chunk(const Batch &b, const HitSink &sink, War
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__ meta, uint32_t nent,
+k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__ meta,
+          const uint32_t *__restrict__ ids, uint32_t nent,
           uint32_t lpad, uint32_t s, uint32_t n_rt, uint32_t rt_per_item, uint32_t n_rchunks, uint32_t n_items,
           HitSink sink, unsigned int *status, unsigned int *work, uint32_t withhold_first) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -279,7 +280,8 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                 if (e < nent) {
                     const uint32_t m = __ldg(meta + e);
                     L = meta_L(m);
-                    t = static_cast<float>(L) - static_cast<float>(entry_s(m, s));
+                    // a row of length 0 pads a tile (batched sets): it never hits
+                    t = L ? static_cast<float>(L) - static_cast<float>(entry_s(m, s)) : 3.0e38f;
                 }
                 H.thr[r] = t;
                 H.len[r] = L;
@@ -391,6 +393,9 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
             const uint32_t half = (warp - 2u) / 4u;
             const uint32_t row = 32u * quarter + lane;
             const uint32_t e = mt * kTcM + row;
+            // the row's entry id (its query and strand): ids map the operand's
+            // rows to the handle's entries when the operand holds a subset
+            const uint32_t id = ids && e < nent ? __ldg(ids + e) : e;
             const float thr = H.thr[row];
             const __half2 thr2 = __float2half2_rn(thr < 60000.0f ? thr : 60000.0f);
             const uint32_t L = H.len[row];
@@ -464,19 +469,19 @@ k_scan_tc(Batch b, const uint8_t *__restrict__ tcA, const uint32_t *__restrict__
                                     const float mt_c = (col & 1u) ? __high2float(v2) : __low2float(v2);
                                     const uint32_t pos =
                                         static_cast<uint32_t>(tpc.contig_off + (p0 + 4u * col - tpc.start));
-                                    wh.emit(sink, lane, has, e >> 1, tpc.contig, pos, e & 1u,
+                                    wh.emit(sink, lane, has, id >> 1, tpc.contig, pos, id & 1u,
                                             L - static_cast<uint32_t>(mt_c), &H.discard);
                                     row_hits += has ? 1u : 0u;
                                 }
                             } else {
-                                emit_chunk(b, sink, wh, mine2, thr, L, e, p0, lane);
+                                emit_chunk(b, sink, wh, mine2, thr, L, id, p0, lane);
                             }
                         }
                     }
                 }
                 if (!ok) break;
             }
-            if (row_hits && e < nent) atomicAdd(&sink.qcount[e >> 1], static_cast<unsigned long long>(row_hits));
+            if (row_hits && e < nent) atomicAdd(&sink.qcount[id >> 1], static_cast<unsigned long long>(row_hits));
         }
         gtile += ntiles;
         __syncthreads();
@@ -521,22 +526,30 @@ void tc_operand(const std::vector<std::string> &qs, uint32_t lpad, std::vector<u
     }
 }
 
+namespace {
+int g_tc_sms[64] = {0};   // per device: SMs, once the kernel's attributes are set
+}
+
+cudaError_t tc_prepare() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || g_tc_sms[dev & 63]) return e;
+    e = cudaFuncSetAttribute(k_scan_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kTcSmem));
+    if (e != cudaSuccess) return e;
+    return cudaDeviceGetAttribute(&g_tc_sms[dev & 63], cudaDevAttrMultiProcessorCount, dev);
+}
+
 cudaError_t launch_scan_tc(const Batch &b, const uint8_t *tcA, const uint32_t *meta, uint32_t nent, uint32_t lpad,
                            uint32_t s, const HitSink &sink, unsigned int *status, cudaStream_t st,
-                           uint32_t withhold_first) {
+                           uint32_t withhold_first, const uint32_t *ids) {
     // status[0]: wait gave up (bit 0); status[1]: the launch's work counter
     if (nent == 0 || b.nbases == 0) return cudaSuccess;
     if (lpad == 0 || lpad > kTcMaxLpad || (lpad & 7u)) return cudaErrorInvalidValue;
-    static int sms[64] = {0};
+    cudaError_t pe = tc_prepare();
+    if (pe != cudaSuccess) return pe;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (sms[dev & 63] == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_scan_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(kTcSmem));
-        if (e != cudaSuccess) return e;
-        cudaDeviceGetAttribute(&sms[dev & 63], cudaDevAttrMultiProcessorCount, dev);
-    }
-    const uint32_t grid_max = static_cast<uint32_t>(sms[dev & 63]);
+    const uint32_t grid_max = static_cast<uint32_t>(g_tc_sms[dev & 63]);
     const uint32_t n_mt = (nent + kTcM - 1) / kTcM;
     const uint32_t n_rt = static_cast<uint32_t>((b.nbases + kTcTile - 1) / kTcTile);
     // about 24 items per CTA, each a run of reference tiles for one entry tile,
@@ -551,8 +564,8 @@ cudaError_t launch_scan_tc(const Batch &b, const uint8_t *tcA, const uint32_t *m
     const uint32_t grid = n_items < grid_max ? n_items : grid_max;
     cudaError_t e = cudaMemsetAsync(status + 1, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    k_scan_tc<<<grid, kTcThreads, kTcSmem, st>>>(b, tcA, meta, nent, lpad, s, n_rt, rt_per_item, n_rchunks, n_items,
-                                                 sink, status, status + 1, withhold_first);
+    k_scan_tc<<<grid, kTcThreads, kTcSmem, st>>>(b, tcA, meta, ids, nent, lpad, s, n_rt, rt_per_item, n_rchunks,
+                                                 n_items, sink, status, status + 1, withhold_first);
     return cudaGetLastError();
 }
 

@@ -176,3 +176,40 @@ def test_soft_clipping_in_batches():
     assert any(x[5] for x in expect)                 # clipped hits are in the case
     assert got[P.IFA_BATCH_PERSISTENT] == sorted(expect)
     assert got[P.IFA_BATCH_PER_SET] == sorted(expect)
+
+
+@pytest.mark.parametrize("kernel", [P.IFA_BRUTE_AUTO, P.IFA_BRUTE_TENSOR])
+def test_tensor_core_sets_in_batches(kernel):
+    """Brute-force sets on the tensor cores inside a batch: with the
+    automatic rule a 96-query set of 24-40 bp at maxSubs 3 (sparse hits)
+    goes to the tensor cores and the others stay on the popcount kernel;
+    forced, every brute-force set of queries up to 64 bases does.  Sets
+    share one operand (each padded to whole 128-row tiles, per-row maxSubs);
+    both batch kinds must give the oracle's hits."""
+    wl = synth.small_workload(seed=89, n_queries=3, lmin=24, lmax=40, n_contigs=30, cmin=50,
+                              cmax=9000, plant_ks=[0, 1, 2, 3] * 4)
+    sets = [(synth.random_queries(96, 24, 40, 301) + wl.queries[:1], 3, P.IFA_MODE_BRUTE),
+            (synth.random_queries(5, 12, 20, 302), 2, P.IFA_MODE_BRUTE),
+            (synth.random_queries(40, 18, 60, 303) + wl.queries[1:], 5, P.IFA_MODE_BRUTE),
+            (synth.random_queries(8, 20, 30, 304), 2, P.IFA_MODE_INDEXED)]
+    got = {}
+    h = P.ifa_create(hit_capacity=1 << 22, segment_bytes=1 << 20, minhits_trials=TRIALS, brute_kernel=kernel)
+    try:
+        _store(h, wl, 4096)
+        firsts = [P.ifa_set_add(h, qs, s, mode)[1] for qs, s, mode in sets]
+        for kind in (P.IFA_BATCH_PERSISTENT, P.IFA_BATCH_PER_SET):
+            P.ifa_reset_results(h)
+            res = P.ifa_batch_run(h, kind, len(sets))
+            hits, over = P.ifa_drain_hits(h)
+            assert not over
+            got[kind] = (tuples(P.sort_hits(hits)), res["hits"].tolist())
+    finally:
+        P.ifa_destroy(h)
+    expect, per_set = [], []
+    for (qs, s, mode), first in zip(sets, firsts):
+        e = _oracle_set(wl, qs, s, mode)
+        expect.extend(tuples(_shift(e, first)))
+        per_set.append(e.size)
+    assert got[P.IFA_BATCH_PERSISTENT][0] == sorted(expect)
+    assert got[P.IFA_BATCH_PER_SET][0] == sorted(expect)
+    assert got[P.IFA_BATCH_PERSISTENT][1] == per_set == got[P.IFA_BATCH_PER_SET][1]
