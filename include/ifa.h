@@ -130,7 +130,8 @@ typedef struct {
     uint32_t clip_pct;             /* soft clipping at contig ends (Methods, Algorithm Design): a window may
                                       overhang its contig by up to floor(clip_pct * L / 100) bases, which
                                       count as clips, not mismatches; 0 = off, at most 50 (paper: 25);
-                                      streaming and batched calls (serving rejects it) */
+                                      streaming, batched and serving calls (serving takes the value
+                                      current at ifa_serve_start) */
     uint32_t exhaustive_fallback;  /* 1: queries with no qualifying k are scanned exhaustively */
     uint32_t auto_crossover;       /* IFA_MODE_AUTO picks indexed from this many queries on */
     uint32_t profile;              /* 1: time every scan kernel with CUDA events (ifa_stats.scan_ns) */
@@ -348,7 +349,7 @@ ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per
  * active with it.  Hit query ids are relative to the request. */
 
 typedef struct {
-    uint32_t state;        /* 0 queued, 1 active, 2 complete, 3 drained */
+    uint32_t state;        /* 0 queued, 1 active, 2 complete, 3 drained, 4 cancelled */
     uint32_t mode;         /* IFA_MODE_BRUTE or IFA_MODE_INDEXED as run */
     uint32_t queries;
     uint32_t slices_done;
@@ -362,6 +363,9 @@ typedef struct {
 
 /* Start serving over the store: n_slices slices, an HBM budget (bytes) for
  * admitted requests' rings and plan entries, ring_hits hits per request.
+ * The handle's clip_pct at this call applies to the whole session: the
+ * clipped windows of a contig are scanned in the slice holding the contig's
+ * first piece, for every request active there.
  * BAD_STATE when the store is empty.  Ends any previous serving session. */
 ifa_status ifa_serve_start(ifa_handle *h, uint32_t n_slices, uint64_t hbm_budget_bytes, uint64_t ring_hits);
 
@@ -372,7 +376,9 @@ ifa_status ifa_serve_submit(ifa_handle *h, const uint8_t *const *seqs, const uin
 
 /* Admit what fits, scan the next slice for all active requests, retire
  * the ones that are complete.  Waits for the slice.  *n_active and
- * *n_completed (may be NULL) receive the counts after the step. */
+ * *n_completed (may be NULL) receive the counts after the step.
+ * OOM when a request's ring cannot be allocated: that request and the ones
+ * after it stay queued holding nothing (cancel it, or retry the step). */
 ifa_status ifa_serve_step(ifa_handle *h, uint32_t *n_active, uint32_t *n_completed);
 
 /* State, timing and digest of one request. */
@@ -381,6 +387,14 @@ ifa_status ifa_serve_poll(ifa_handle *h, uint32_t request_id, ifa_request_info *
 /* Copy a complete request's hits (up to cap) to out and free its ring;
  * HIT_OVERFLOW (with the data) when its ring dropped hits. */
 ifa_status ifa_serve_drain(ifa_handle *h, uint32_t request_id, ifa_hit *out, uint64_t cap, uint64_t *n_out);
+
+/* Cancel a queued, active or complete request: its ring is freed, its
+ * budget returned and its hits discarded (state 4).  An active request
+ * leaves the scan from the next ifa_serve_step on; the others active with
+ * it are unaffected.  Nothing of it is in flight: ifa_serve_step waits for
+ * its slice.  BAD_STATE for a drained or already cancelled request,
+ * INVALID_ARG for an unknown id. */
+ifa_status ifa_serve_cancel(ifa_handle *h, uint32_t request_id);
 
 /* Slices scanned, nominal query-base comparisons done, host seconds spent
  * building plans and seconds spent waiting for slices, since

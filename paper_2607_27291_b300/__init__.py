@@ -112,6 +112,7 @@ _SYMBOLS = {
     "ifa_serve_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "ifa_serve_stop": (C.c_int, [C.c_void_p]),
+    "ifa_serve_cancel": (C.c_int, [C.c_void_p, C.c_uint32]),
     "ifa_scan_brute_noalloc": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
                                          C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32,
                                          C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p,
@@ -457,6 +458,10 @@ def ifa_serve_stats(h) -> dict:
     ss = C.c_double()
     _check(lib().ifa_serve_stats(h, C.byref(n), C.byref(qb), C.byref(ps), C.byref(ss)), h)
     return {"slices": n.value, "query_bases": qb.value, "plan_s": ps.value, "scan_s": ss.value}
+
+
+def ifa_serve_cancel(h, rid: int) -> None:
+    _check(lib().ifa_serve_cancel(h, rid), h)
 
 
 def ifa_serve_stop(h) -> None:

@@ -49,7 +49,7 @@ ifa_status bfail(ifa_handle *h, ifa_status st, const std::string &msg) {
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
         if (e_ != cudaSuccess)                                                             \
-            return bfail((h), e_ == cudaErrorMemoryAllocation ? IFA_ERR_OOM : IFA_ERR_CUDA, \
+            return bfail((h), cuda_status(e_),                                               \
                          std::string(#call) + ": " + cudaGetErrorString(e_));              \
     } while (0)
 

@@ -137,6 +137,8 @@ struct ServeState {
     DevBufs pool;
     uint32_t wmax = 1;
     uint32_t nq = 0;
+    uint32_t lmax = 0;               // longest active query (soft-clip count bound)
+    uint32_t clip_pct = 0;           // soft clipping, fixed at ifa_serve_start
     QueryTable ft{};
     QueryTable bt{};
     uint32_t b_entries = 0;

@@ -35,7 +35,7 @@ ifa_status fail(ifa_handle *h, ifa_status st, const std::string &msg) {
 
 ifa_status fail_cuda(ifa_handle *h, const char *what, cudaError_t e) {
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);
-    return fail(h, e == cudaErrorMemoryAllocation ? IFA_ERR_OOM : IFA_ERR_CUDA, m);
+    return fail(h, cuda_status(e), m);
 }
 
 #define CK(h, call)                                           \

@@ -14,6 +14,8 @@
 // its new bases (the rule for every window): left windows of contigs that
 // start in the batch's visible bases, right windows of contigs that end in
 // it.  The aligned bases then always lie in the batch (halo included).
+// The serving loop scans the whole store as one batch, a range of its
+// pieces per slice, and sends each hit to its request's own ring (MULTI).
 #include "hits.cuh"
 
 namespace ifa {
@@ -57,14 +59,17 @@ __device__ __forceinline__ uint32_t clipped_mismatches(const Batch &b, const uin
     return mm;
 }
 
+// Pairs (piece, entry) for pieces [p_lo, p_hi) of b and entries
+// [e_base, e_base + nent) of qt.
+template <bool MULTI>
 __global__ void __launch_bounds__(kClipThreads)
-k_clip_scan(Batch b, QueryTable qt, uint32_t e_base, uint32_t nent, uint32_t clip_pct, uint32_t s, uint32_t cmax,
-            HitSink sink) {
+k_clip_scan(Batch b, QueryTable qt, uint32_t e_base, uint32_t nent, uint32_t p_lo, uint32_t p_hi,
+            uint32_t clip_pct, uint32_t s, uint32_t cmax, HitSink sink) {
     __shared__ __align__(16) ifa_hit wbuf[kClipThreads / 32][32];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    WarpHits wh;
+    WarpHitsT<MULTI> wh;
     wh.init(wbuf[warp]);
-    const uint64_t npairs = static_cast<uint64_t>(b.npieces) * nent;
+    const uint64_t npairs = static_cast<uint64_t>(p_hi - p_lo) * nent;
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     // every lane of a warp runs the same number of rounds (emit is warp-wide)
     const uint64_t first = static_cast<uint64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u);
@@ -75,7 +80,7 @@ k_clip_scan(Batch b, QueryTable qt, uint32_t e_base, uint32_t nent, uint32_t cli
         int64_t cs = 0, ce = 0;
         bool has_start = false, has_end = false;
         if (live) {
-            piece = static_cast<uint32_t>(pair / nent);
+            piece = p_lo + static_cast<uint32_t>(pair / nent);
             e = e_base + static_cast<uint32_t>(pair % nent);
             const uint32_t m = qt.meta[e];
             L = meta_L(m);
@@ -137,13 +142,20 @@ k_clip_scan(Batch b, QueryTable qt, uint32_t e_base, uint32_t nent, uint32_t cli
 }  // namespace
 
 cudaError_t launch_clip_scan(const Batch &b, const QueryTable &qt, uint32_t nent, uint32_t clip_pct, uint32_t s,
-                             uint32_t lmax, const HitSink &sink, cudaStream_t st, uint32_t e_base) {
+                             uint32_t lmax, const HitSink &sink, cudaStream_t st, uint32_t e_base, uint32_t p_lo,
+                             uint32_t p_hi) {
     const uint32_t cmax = clip_pct * lmax / 100u;
-    if (nent == 0 || b.npieces == 0 || cmax == 0) return cudaSuccess;
-    const uint64_t npairs = static_cast<uint64_t>(b.npieces) * nent;
+    if (p_hi > b.npieces) p_hi = b.npieces;
+    if (nent == 0 || p_lo >= p_hi || cmax == 0) return cudaSuccess;
+    const uint64_t npairs = static_cast<uint64_t>(p_hi - p_lo) * nent;
     uint64_t grid = (npairs + kClipThreads - 1) / kClipThreads;
     if (grid > 148ull * 16) grid = 148ull * 16;
-    k_clip_scan<<<static_cast<unsigned>(grid), kClipThreads, 0, st>>>(b, qt, e_base, nent, clip_pct, s, cmax, sink);
+    if (sink.rings)
+        k_clip_scan<true><<<static_cast<unsigned>(grid), kClipThreads, 0, st>>>(b, qt, e_base, nent, p_lo, p_hi,
+                                                                               clip_pct, s, cmax, sink);
+    else
+        k_clip_scan<false><<<static_cast<unsigned>(grid), kClipThreads, 0, st>>>(b, qt, e_base, nent, p_lo, p_hi,
+                                                                                clip_pct, s, cmax, sink);
     return cudaGetLastError();
 }
 

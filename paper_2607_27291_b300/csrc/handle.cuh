@@ -7,6 +7,7 @@
 #include "batch_state.cuh"
 #include "ifa_internal.cuh"
 #include "indexed.cuh"
+#include "status.cuh"
 
 namespace ifa {
 struct Chunk {

@@ -212,9 +212,12 @@ __device__ inline uint32_t find_piece(const DevPiece *pc, uint32_t n, uint64_t p
 // ---------------------------------------------------------------- launchers
 // (defined in the .cu files; all enqueue on `st`)
 
-// Soft-clipped windows at contig ends (clip.cu), for entries [e_base, e_base + nent) of qt.
+// Soft-clipped windows at contig ends (clip.cu), for entries [e_base, e_base + nent) of qt
+// and pieces [p_lo, min(p_hi, b.npieces)) of b; a sink with rings sends each
+// hit to its request's ring (serving).
 cudaError_t launch_clip_scan(const Batch &b, const QueryTable &qt, uint32_t nent, uint32_t clip_pct, uint32_t s,
-                             uint32_t lmax, const HitSink &sink, cudaStream_t st, uint32_t e_base = 0);
+                             uint32_t lmax, const HitSink &sink, cudaStream_t st, uint32_t e_base = 0,
+                             uint32_t p_lo = 0, uint32_t p_hi = 0xffffffffu);
 
 // Tensor-core brute-force scan (scan_tc.cu): queries up to 64 bases.
 uint32_t tc_lpad(uint32_t lmax);

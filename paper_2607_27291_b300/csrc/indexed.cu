@@ -28,6 +28,7 @@
 #include "hits.cuh"
 #include "indexed.cuh"
 #include "seed_scan.cuh"
+#include "status.cuh"
 
 namespace ifa {
 
@@ -216,7 +217,7 @@ ifa_status minhits_compute(const uint32_t *L, const uint32_t *subs, const uint32
     cudaFree(dO);
     if (e != cudaSuccess) {
         err = std::string("MinHits on the device: ") + cudaGetErrorString(e);
-        return e == cudaErrorMemoryAllocation ? IFA_ERR_OOM : IFA_ERR_CUDA;
+        return cuda_status(e);
     }
     return IFA_OK;
 }
@@ -417,7 +418,7 @@ ifa_status indexed_tables_len(IndexedState &S, const std::vector<uint32_t> &qlen
     if (e != cudaSuccess) {
         err = std::string("indexed tables: ") + cudaGetErrorString(e);
         S.free_tables();
-        return e == cudaErrorMemoryAllocation ? IFA_ERR_OOM : IFA_ERR_CUDA;
+        return cuda_status(e);
     }
     S.tables_valid = true;
     return IFA_OK;

@@ -11,7 +11,8 @@
 // when it wraps back to t; its hit ring stays on the device until drained.
 // A request's hits do not depend on what else is active: windows are
 // owned by the slice of their start (brute force) or of their first seed
-// (indexed), and every slice is scanned once per request.
+// (indexed), soft-clipped windows by the slice holding their piece's first
+// base, and every slice is scanned once per request.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -38,7 +39,7 @@ ifa_status sfail(ifa_handle *h, ifa_status st, const std::string &msg) {
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
         if (e_ != cudaSuccess)                                                             \
-            return sfail((h), e_ == cudaErrorMemoryAllocation ? IFA_ERR_OOM : IFA_ERR_CUDA, \
+            return sfail((h), cuda_status(e_),                                               \
                          std::string(#call) + ": " + cudaGetErrorString(e_));              \
     } while (0)
 
@@ -111,6 +112,7 @@ ifa_status build_serve_plan(ifa_handle *h) {
     const uint32_t nq = static_cast<uint32_t>(nqs);
     S.wmax = wmax;
     S.nq = nq;
+    S.lmax = 0;
     std::vector<uint4> words(static_cast<size_t>(2) * nq * wmax, make_uint4(0, 0, 0, 0));
     std::vector<uint32_t> meta(2 * static_cast<size_t>(nq));
     std::vector<uint8_t> seeded(nq, 0);
@@ -128,6 +130,7 @@ ifa_status build_serve_plan(ifa_handle *h) {
             const uint32_t q = q0 + i;
             q2r.push_back(static_cast<uint32_t>(slot));
             qlen.push_back(static_cast<uint32_t>(r.qs[i].size()));
+            S.lmax = std::max<uint32_t>(S.lmax, qlen.back());
             for (uint32_t t = 0; t < 2; t++) {
                 const size_t src = (2 * static_cast<size_t>(i) + t) * r.w, dst = (2 * static_cast<size_t>(q) + t) * wmax;
                 std::copy(r.words.begin() + src, r.words.begin() + src + r.w, words.begin() + dst);
@@ -279,12 +282,11 @@ ifa_status ifa_serve_start(ifa_handle *h, uint32_t n_slices, uint64_t hbm_budget
     if (!h) return IFA_ERR_INVALID_ARG;
     if (n_slices == 0 || ring_hits == 0) return sfail(h, IFA_ERR_INVALID_ARG, "ifa_serve_start: n_slices and ring_hits must be > 0");
     if (h->batch.nbases == 0) return sfail(h, IFA_ERR_BAD_STATE, "ifa_serve_start: the reference store is empty");
-    if (h->cfg.clip_pct)
-        return sfail(h, IFA_ERR_INVALID_ARG, "ifa_serve_start: soft clipping (clip_pct) applies to the streaming calls only");
     SCK(h, cudaSetDevice(h->dev));
     serve_release(h);
     ServeState &S = h->serve;
     S.on = true;
+    S.clip_pct = h->cfg.clip_pct;
     S.n_slices = n_slices;
     S.budget = hbm_budget_bytes;
     S.used = 0;
@@ -351,14 +353,31 @@ ifa_status ifa_serve_step(ifa_handle *h, uint32_t *n_active, uint32_t *n_complet
     while (admitted < S.pending.size()) {
         Request &r = S.reqs[S.pending[admitted]];
         if (S.used + r.bytes > S.budget && !S.active.empty()) break;
-        SCK(h, cudaMalloc(&r.d_ring, r.cap * sizeof(ifa_hit)));
-        SCK(h, cudaMalloc(&r.d_counters, 5 * sizeof(unsigned long long)));
-        SCK(h, cudaMemsetAsync(r.d_counters, 0, 5 * sizeof(unsigned long long), h->stream));
         {
+            // a failed allocation leaves the request queued with nothing held
+            // (the ones admitted before it stay admitted)
+            const auto unwind = [&]() {
+                cudaFree(r.d_ring);
+                cudaFree(r.d_counters);
+                r.d_ring = nullptr;
+                r.d_counters = nullptr;
+                S.pending.erase(S.pending.begin(), S.pending.begin() + admitted);
+            };
+            cudaError_t e = cudaMalloc(&r.d_ring, r.cap * sizeof(ifa_hit));
+            if (e == cudaSuccess) e = cudaMalloc(&r.d_counters, 5 * sizeof(unsigned long long));
+            if (e == cudaSuccess) e = cudaMemsetAsync(r.d_counters, 0, 5 * sizeof(unsigned long long), h->stream);
+            if (e != cudaSuccess) {
+                unwind();
+                return sfail(h, cuda_status(e),
+                             std::string("ifa_serve_step: request ring: ") + cudaGetErrorString(e));
+            }
             const double tp = now_s();
             const ifa_status pst = prepare_request(h, r);
             S.plan_s += now_s() - tp;
-            if (pst != IFA_OK) return pst;
+            if (pst != IFA_OK) {
+                unwind();
+                return pst;
+            }
         }
         r.state = 1;
         r.t_admit = now_s() - S.t0;
@@ -402,9 +421,27 @@ ifa_status ifa_serve_step(ifa_handle *h, uint32_t *n_active, uint32_t *n_complet
         const double t1 = now_s();
         SCK(h, cudaMemsetAsync(S.d_queue, 0, sizeof(unsigned int), h->stream));
         SCK(h, launch_batch_kernel(S.wmax, b, w, S.bt, S.ft, S.sink, S.grid, brute::kScanSmemBudget, h->stream));
+        h->stats.kernel_launches += 1;
+        if (S.clip_pct) {
+            // soft-clipped windows of the pieces whose first base is in this
+            // slice, every active entry exhaustively at its own maxSubs
+            const auto first_at = [&B](uint64_t x) {
+                return static_cast<uint32_t>(
+                    std::lower_bound(B.pieces.begin(), B.pieces.end(), x,
+                                     [](const DevPiece &p, uint64_t v) { return p.start < v; }) -
+                    B.pieces.begin());
+            };
+            const uint32_t p_lo = first_at(w.s_block0 * 32);
+            const uint32_t p_hi = S.slice + 1 == S.n_slices ? static_cast<uint32_t>(B.pieces.size())
+                                                             : first_at(w.s_block_end * 32);
+            if (p_lo < p_hi) {
+                SCK(h, launch_clip_scan(b, S.ft, S.ft.n_entries, S.clip_pct, kSPerEntry, S.lmax, S.sink, h->stream, 0,
+                                        p_lo, p_hi));
+                h->stats.kernel_launches += 1;
+            }
+        }
         SCK(h, cudaStreamSynchronize(h->stream));
         S.scan_s += now_s() - t1;
-        h->stats.kernel_launches += 1;
         S.slices_run++;
         const double slice_bases = static_cast<double>(ns) * 32.0;
         // retire the requests that have now seen every slice
@@ -469,6 +506,34 @@ ifa_status ifa_serve_drain(ifa_handle *h, uint32_t id, ifa_hit *out, uint64_t ca
     S.used -= r.bytes;
     r.state = 3;
     return r.final_counters[1] ? IFA_ERR_HIT_OVERFLOW : IFA_OK;
+}
+
+ifa_status ifa_serve_cancel(ifa_handle *h, uint32_t id) {
+    if (!h) return IFA_ERR_INVALID_ARG;
+    ServeState &S = h->serve;
+    if (!S.on) return sfail(h, IFA_ERR_BAD_STATE, "ifa_serve_cancel: call ifa_serve_start first");
+    if (id >= S.reqs.size()) return sfail(h, IFA_ERR_INVALID_ARG, "ifa_serve_cancel: unknown request");
+    Request &r = S.reqs[id];
+    if (r.state >= 3) return sfail(h, IFA_ERR_BAD_STATE, "ifa_serve_cancel: request already drained or cancelled");
+    SCK(h, cudaSetDevice(h->dev));
+    if (r.state == 0) {
+        S.pending.erase(std::find(S.pending.begin(), S.pending.end(), id));
+    } else {
+        if (r.state == 1) {
+            S.active.erase(std::find(S.active.begin(), S.active.end(), id));
+            S.dirty = true;   // the merged plan drops its entries
+        }
+        // the stream is idle between steps; free only after any queued work
+        SCK(h, cudaStreamSynchronize(h->stream));
+        cudaFree(r.d_ring);
+        cudaFree(r.d_counters);
+        r.d_ring = nullptr;
+        r.d_counters = nullptr;
+        S.used -= r.bytes;
+    }
+    r.state = 4;
+    r.t_done = now_s() - S.t0;
+    return IFA_OK;
 }
 
 ifa_status ifa_serve_stats(ifa_handle *h, uint64_t *slices_run, double *query_bases, double *plan_seconds,

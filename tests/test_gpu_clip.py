@@ -1,8 +1,8 @@
 """Soft clipping at contig ends (Methods, Algorithm Design) on the GPU: the
-clipped windows of every contig end, in brute-force and indexed mode and
-with either brute-force kernel, match the oracle tuple for tuple (clips
-included), with contigs cut across segments and contigs shorter than the
-queries."""
+clipped windows of every contig end, in brute-force and indexed mode, with
+either brute-force kernel and in the serving loop, match the oracle tuple
+for tuple (clips included), with contigs cut across segments and contigs
+shorter than the queries."""
 import numpy as np
 import pytest
 
@@ -86,15 +86,57 @@ def test_tensor_kernel_with_clipping():
     assert tuples6(got) == tuples6(exp)
 
 
-def test_serving_rejects_clipping():
-    """Batching applies soft clipping (tests/test_gpu_batch.py); the serving
-    loop does not, and says so."""
-    h = P.ifa_create(hit_capacity=1024, segment_bytes=1 << 16, clip_pct=25)
+def _serve(wl, requests, n_slices, pct, arrive):
+    """Serve requests [(queries, s, mode)], request i submitted before step
+    arrive[i]; returns each request's (sorted hits, info)."""
+    h = P.ifa_create(hit_capacity=1024, segment_bytes=1 << 20, minhits_trials=10_000, clip_pct=pct)
     try:
-        ref = np.frombuffer(b"ACGT" * 64, np.uint8).copy()
-        P.ifa_ref_append(h, ref, [(0, 0, 0, 256, True)])
-        with pytest.raises(P.IfaError) as ei:
-            P.ifa_serve_start(h, 4, 1 << 30, 1024)
-        assert ei.value.status == P.IFA_ERR_INVALID_ARG
+        for a, b, pc in P.segment_pieces(wl.contig_len, 1 << 12):
+            P.ifa_ref_append(h, wl.ref[a:b], pc)
+        P.ifa_serve_start(h, n_slices, 1 << 40, 1 << 16)
+        ids, step = {}, 0
+        while True:
+            for i, t in enumerate(arrive):
+                if t == step:
+                    ids[i] = P.ifa_serve_submit(h, *requests[i])
+            P.ifa_serve_step(h)
+            step += 1
+            infos = {i: P.ifa_serve_poll(h, r) for i, r in ids.items()}
+            if len(ids) == len(requests) and all(v["state"] == 2 for v in infos.values()):
+                break
+            assert step < 100
+        out = []
+        for i in range(len(requests)):
+            hits, over = P.ifa_serve_drain(h, ids[i], 1 << 16)
+            assert not over
+            out.append((P.sort_hits(hits), infos[i]))
+        P.ifa_serve_stop(h)
+        return out
     finally:
         P.ifa_destroy(h)
+
+
+@pytest.mark.parametrize("n_slices,pct", [(1, 25), (7, 25), (13, 50)])
+def test_serving_clipped_windows_match_oracle(n_slices, pct):
+    """Requests joining at different slices, in both modes, each find every
+    clipped window once: contigs cut across appends (pieces continued) and
+    contigs shorter than the queries included."""
+    wl = _workload(160 + n_slices, pct)
+    trials = 10_000
+    requests = [(wl.queries[:3], 3, P.IFA_MODE_BRUTE), (wl.queries[3:], 5, P.IFA_MODE_INDEXED),
+                (wl.queries, 2, P.IFA_MODE_BRUTE)]
+    got = _serve(wl, requests, n_slices, pct, [0, 1, 3])
+    clipped = 0
+    for (qs, s, mode), (hits, info) in zip(requests, got):
+        if mode == P.IFA_MODE_BRUTE:
+            exp = oracle.brute(qs, wl.ref, wl.contig_len, s, clip_pct=pct)
+        else:
+            plan = [oracle.choose_k(len(q), s, trials=trials) for q in qs]
+            exh = [1 if (st < 0 or any(c not in b"ACGTacgt" for c in q)) else 0
+                   for (st, _, _), q in zip(plan, qs)]
+            exp = oracle.indexed(qs, wl.ref, wl.contig_len, s, [p[1] for p in plan], [p[2] for p in plan], exh,
+                                 clip_pct=pct)
+        clipped += int((exp["clips"] != 0).sum())
+        assert tuples6(hits) == tuples6(exp)
+        assert info["digest"] == oracle.digest(exp)
+    assert clipped > 0
