@@ -767,6 +767,9 @@ def serve_trace(P, h, reqs, slices, budget, max_wall):
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "p999": float(np.percentile(lat, 99.9))},
             "queue_s": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
+            "modes": {"brute": sum(1 for i in infos if i["mode"] == P.IFA_MODE_BRUTE),
+                      "indexed": sum(1 for i in infos if i["mode"] == P.IFA_MODE_INDEXED),
+                      "not_admitted": sum(1 for i in infos if i["mode"] == P.IFA_MODE_AUTO)},
             "completed": len(done), "requests": len(reqs), "wall_s": wall, "steps": steps,
             "stopped_at_wall_limit": cut, "host_plan_s": sst["plan_s"], "device_scan_s": sst["scan_s"]}
 
@@ -859,7 +862,7 @@ def serving_result(total, rate, duration, slices, solo_max_s, max_wall, burst=0)
                    "duration_s": duration, "slices": slices, "max_wall_s": max_wall,
                    "store_build_s": round(build_s, 1), "store_device_bytes": store_bytes,
                    "set_sizes": "log-uniform 1-2000", "lengths": "18-50", "max_subs": "0-8",
-                   "gc": 0.45, "n_frac": 0.0005, "mode": "auto by query count",
+                   "gc": 0.45, "n_frac": 0.0005, "mode": "auto by measured rates",
                    "admission": "HBM budget 64 GiB (continuous batching); baseline: one active request"},
         "data": "synthetic" + (", reference generated on the device" if total >= 32e9 else ""),
     }

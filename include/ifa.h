@@ -56,7 +56,7 @@ typedef enum {
 } ifa_status;
 
 typedef enum {
-    IFA_MODE_AUTO = 0,     /* indexed when the query count reaches the config's crossover */
+    IFA_MODE_AUTO = 0,     /* the mode with the smaller predicted time (see ifa_config.auto_crossover) */
     IFA_MODE_BRUTE = 1,    /* every window of every contig, both strands */
     IFA_MODE_INDEXED = 2   /* query k-mer seeds + min-hits threshold + verification */
 } ifa_mode;
@@ -133,7 +133,12 @@ typedef struct {
                                       streaming, batched and serving calls (serving takes the value
                                       current at ifa_serve_start) */
     uint32_t exhaustive_fallback;  /* 1: queries with no qualifying k are scanned exhaustively */
-    uint32_t auto_crossover;       /* IFA_MODE_AUTO picks indexed from this many queries on */
+    uint32_t auto_crossover;       /* IFA_MODE_AUTO in the streaming and serving calls: 0 (default) picks
+                                      the mode with the smaller predicted time from rates measured on the
+                                      device (once per handle and maxSubs on 16 Mbp of random sequence when
+                                      streaming; once per session on the store when serving); n > 0 picks
+                                      indexed from n queries on (the paper's rule; its crossover lies
+                                      between 100 and 200).  Batches always use measured rates. */
     uint32_t profile;              /* 1: time every scan kernel with CUDA events (ifa_stats.scan_ns) */
     uint32_t brute_kernel;         /* brute-force kernel: 0 automatic, 1 popcount, 2 tensor cores
                                       (one-hot e4m3 GEMM; queries of at most 64 bases) */
@@ -153,6 +158,9 @@ typedef struct {
     uint64_t candidates;      /* indexed mode: candidate windows verified */
     uint64_t scan_launches;   /* scan kernels timed (config.profile = 1) */
     uint64_t scan_ns;         /* their summed device time, from CUDA events on the compute stream */
+    uint32_t mode;            /* the streaming pass's mode: IFA_MODE_BRUTE or IFA_MODE_INDEXED
+                                 (IFA_MODE_AUTO before the first segment) */
+    uint32_t reserved;
 } ifa_stats;
 
 /* Fill *cfg with the defaults (paper defaults where it gives one).
@@ -369,8 +377,10 @@ typedef struct {
  * BAD_STATE when the store is empty.  Ends any previous serving session. */
 ifa_status ifa_serve_start(ifa_handle *h, uint32_t n_slices, uint64_t hbm_budget_bytes, uint64_t ring_hits);
 
-/* Queue one request; IFA_MODE_AUTO picks indexed from auto_crossover
- * queries on (the paper's rule by query count). *request_id may be NULL. */
+/* Queue one request.  IFA_MODE_AUTO is resolved when the request is
+ * admitted (ifa_request_info.mode reads IFA_MODE_AUTO until then): by the
+ * measured-rate model when auto_crossover is 0, else indexed from
+ * auto_crossover queries on.  *request_id may be NULL. */
 ifa_status ifa_serve_submit(ifa_handle *h, const uint8_t *const *seqs, const uint32_t *lens, uint32_t n,
                             uint32_t max_subs, ifa_mode mode, uint32_t *request_id);
 
@@ -387,6 +397,18 @@ ifa_status ifa_serve_poll(ifa_handle *h, uint32_t request_id, ifa_request_info *
 /* Copy a complete request's hits (up to cap) to out and free its ring;
  * HIT_OVERFLOW (with the data) when its ring dropped hits. */
 ifa_status ifa_serve_drain(ifa_handle *h, uint32_t request_id, ifa_hit *out, uint64_t cap, uint64_t *n_out);
+
+/* Bounds-checked builds.  A library compiled with -DIFA_BOUNDS_CHECK
+ * (libifa_bc.so beside libifa.so) checks the index of every read of the
+ * packed reference (hi/lo words, directory, exception table) against its
+ * allocation.  The first read out of range on a device is recorded in a
+ * device word as kind << 56 | index (kind 1 word, 2 directory entry,
+ * 3 exception entry), the read returns an all-N word and nothing traps;
+ * ifa_flush then fails with IFA_ERR_CUDA naming it.  This call waits for
+ * the device, stores that word in *first (0: none) and *enabled = 1; with
+ * reset != 0 it clears the word.  Default builds store *enabled = 0 and
+ * *first = 0 and touch no device. */
+ifa_status ifa_bounds_check(int device, uint64_t *first, uint32_t *enabled, int reset);
 
 /* Cancel a queued, active or complete request: its ring is freed, its
  * budget returned and its hits discarded (state 4).  An active request

@@ -56,7 +56,8 @@ class ifa_stats(C.Structure):
     _fields_ = [("segments", C.c_uint64), ("bases", C.c_uint64), ("h2d_bytes", C.c_uint64),
                 ("windows", C.c_uint64), ("query_bases", C.c_uint64),
                 ("kernel_launches", C.c_uint64), ("candidates", C.c_uint64),
-                ("scan_launches", C.c_uint64), ("scan_ns", C.c_uint64)]
+                ("scan_launches", C.c_uint64), ("scan_ns", C.c_uint64),
+                ("mode", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class ifa_sam_info(C.Structure):
@@ -113,6 +114,7 @@ _SYMBOLS = {
                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "ifa_serve_stop": (C.c_int, [C.c_void_p]),
     "ifa_serve_cancel": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "ifa_bounds_check": (C.c_int, [C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32), C.c_int]),
     "ifa_scan_brute_noalloc": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
                                          C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32,
                                          C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p,
@@ -458,6 +460,15 @@ def ifa_serve_stats(h) -> dict:
     ss = C.c_double()
     _check(lib().ifa_serve_stats(h, C.byref(n), C.byref(qb), C.byref(ps), C.byref(ss)), h)
     return {"slices": n.value, "query_bases": qb.value, "plan_s": ps.value, "scan_s": ss.value}
+
+
+def ifa_bounds_check(device: int = 0, reset: bool = False) -> Tuple[bool, int]:
+    """(built with bounds checks, first out-of-range read as kind << 56 |
+    index or 0)."""
+    first = C.c_uint64()
+    enabled = C.c_uint32()
+    _check(lib().ifa_bounds_check(int(device), C.byref(first), C.byref(enabled), 1 if reset else 0))
+    return bool(enabled.value), int(first.value)
 
 
 def ifa_serve_cancel(h, rid: int) -> None:

@@ -14,6 +14,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(HERE, "libifa.so")
+# the same library with every read of the packed reference bounds-checked
+# (-DIFA_BOUNDS_CHECK: a device error word, no trap); select it with IFA_LIB
+BC_LIB_PATH = os.path.join(HERE, "libifa_bc.so")
 # the integer-pipe issue-rate microbenchmark (a measurement tool, not the aligner)
 PROBE_SRC = os.path.join(HERE, "probe", "pipe_rates.cu")
 PROBE_LIB = os.path.join(HERE, "libifa_probe.so")
@@ -41,9 +44,9 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=(), out: str = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(), out: str = None, objs: str = None) -> str:
     lib_path = out or LIB_PATH
-    build_dir = BUILD_DIR if out is None else out + ".objs"
+    build_dir = objs or (BUILD_DIR if out is None else out + ".objs")
     os.makedirs(build_dir, exist_ok=True)
     srcs = _sources()
     hdrs = _headers()
@@ -82,6 +85,10 @@ def build(force: bool = False, verbose: bool = False, extra=(), out: str = None)
             raise RuntimeError("probe build failed")
         os.replace(tmp, PROBE_LIB)
     return lib_path
+
+
+def build_bounds_check(force: bool = False) -> str:
+    return build(force=force, extra=["-DIFA_BOUNDS_CHECK"], out=BC_LIB_PATH, objs=os.path.join(BUILD_DIR, "bc"))
 
 
 if __name__ == "__main__":

@@ -64,6 +64,7 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
     extern __shared__ uint4 smem4[];
     __shared__ __align__(16) ifa_hit wbuf[kBWarps][32];
     __shared__ __align__(8) uint2 stage[kBWarps][2][Stage<WMAX>::kSlots];
+    __shared__ uint16_t cq[kBWarps][kQRows][32];
     __shared__ uint32_t s_nF, s_nM, s_item;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
@@ -105,7 +106,7 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
             const uint64_t lo = w.b_block0 + static_cast<uint64_t>(tile) * w.tile_bblocks;
             const uint64_t hi = lo + w.tile_bblocks < w.b_block_end ? lo + w.tile_bblocks : w.b_block_end;
             scan_blocks<WMAX>(b, bt, m, nent, s_nF, s_nM, e0, kSPerEntry, lmin, lmax, sink, wh, stage[warp], mul,
-                              lo, hi, warp, kBWarps, lane);
+                              lo, hi, warp, kBWarps, lane, cq[warp]);
         }
         __syncthreads();
     }
@@ -248,12 +249,6 @@ T *plan_alloc(ifa_handle *h, size_t n, cudaError_t &e) {
     return static_cast<T *>(p);
 }
 
-// Expected random seed hits per reference base of one query entry: its
-// k-mer count over 4^k (both strands are separate entries).
-double seed_rate(uint32_t L, uint32_t k, uint32_t step) {
-    if (k == 0 || k > L) return 0;
-    return static_cast<double>((L - k) / step + 1) / std::pow(4.0, static_cast<double>(k));
-}
 
 }  // namespace
 
@@ -289,32 +284,11 @@ ifa_status build_plan(ifa_handle *h) {
     }
 
     // autotuner: brute force or indexed per AUTO set, from measured rates
-    const double bases = static_cast<double>(B.nbases);
     for (QuerySet &S : B.sets) {
         if (S.mode == IFA_MODE_BRUTE) { S.chosen = IFA_MODE_BRUTE; continue; }
         if (S.mode == IFA_MODE_INDEXED) { S.chosen = IFA_MODE_INDEXED; continue; }
-        double brute_s = 2.0 * S.n * bases / std::max(1.0, B.brute_entry_bases_per_s);
-        double cand = 0;
-        std::vector<uint32_t> ks;
-        bool any_seeded = false;
-        for (uint32_t q = S.first; q < S.first + S.n; q++) {
-            if (plan_all.plan_exhaustive.empty() || plan_all.plan_exhaustive[q]) {
-                cand += 0;
-                continue;
-            }
-            any_seeded = true;
-            cand += 2.0 * bases * seed_rate(static_cast<uint32_t>(h->qs[q].size()), plan_all.plan_k[q], h->cfg.kmer_step);
-            ks.push_back(plan_all.plan_k[q]);
-        }
-        std::sort(ks.begin(), ks.end());
-        ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
-        double exh = 0;  // exhaustive queries of an indexed set are scanned by brute force anyway
-        for (uint32_t q = S.first; q < S.first + S.n; q++)
-            if (plan_all.plan_exhaustive.empty() || plan_all.plan_exhaustive[q]) exh += 2.0 * bases;
-        exh /= std::max(1.0, B.brute_entry_bases_per_s);
-        const double idx_s = bases * ks.size() / std::max(1.0, B.seed_pos_per_s) +
-                             cand / std::max(1.0, B.cand_per_s) + exh;
-        S.chosen = (!any_seeded || brute_s <= idx_s) ? IFA_MODE_BRUTE : IFA_MODE_INDEXED;
+        const ModeCost c = predict_cost(B.rates, h->qs, S.first, S.n, plan_all, h->cfg.kmer_step);
+        S.chosen = (!c.seeded || c.brute_s <= c.idx_s) ? IFA_MODE_BRUTE : IFA_MODE_INDEXED;
     }
 
     // queries that run indexed (seeded ones go to the merged tables; their
@@ -519,114 +493,15 @@ ifa_status build_plan(ifa_handle *h) {
 }
 
 // Measure the autotuner's three rates on a slice of the store (once per
-// handle), with a count-only sink so no result is touched.
+// handle), with count-only sinks so no result is touched.
 ifa_status calibrate(ifa_handle *h) {
     BatchState &B = h->batch;
-    if (B.brute_entry_bases_per_s > 0) return IFA_OK;
-    ifa_status st = upload_queries(h);
+    if (B.rates.valid()) return IFA_OK;
+    ifa_status st = sync_pieces(h);
     if (st != IFA_OK) return st;
-    st = sync_pieces(h);
-    if (st != IFA_OK) return st;
-    const uint32_t nq = static_cast<uint32_t>(h->qs.size());
-    Batch b = store_batch(B);
-    b.nbases = std::min<uint64_t>(B.nbases, 32ull << 20);
-    unsigned long long *scratch = nullptr;
-    BCK(h, cudaMalloc(&scratch, (4 + nq) * sizeof(unsigned long long)));
-    HitSink sink;
-    sink.ring = nullptr;
-    sink.head = scratch;
-    sink.capacity = 0;
-    sink.digest = scratch + 1;
-    sink.overflow = reinterpret_cast<uint32_t *>(scratch + 3);
-    sink.qcount = scratch + 4;
-    sink.count_only = 1;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    QueryTable qt;
-    qt.words = h->d_qwords;
-    qt.meta = h->d_qmeta;
-    qt.ids = nullptr;
-    qt.n_entries = 2 * nq;
-    qt.wmax = h->wmax;
-    float ms = 0;
-    // brute force: up to 256 entries (one shared-memory chunk), per-entry thresholds
-    const uint32_t ne = std::min<uint32_t>(std::min<uint32_t>(2 * nq, 256), scan_brute_chunk_entries(h->wmax) & ~1u);
-    uint32_t lo = 255, hi = 0;
-    for (uint32_t i = 0; i < ne; i++) {
-        lo = std::min(lo, meta_L(h->qmeta_host[i]));
-        hi = std::max(hi, meta_L(h->qmeta_host[i]));
-    }
-    cudaError_t e = cudaSuccess;
-    for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
-        cudaEventRecord(e0, h->stream);
-        e = launch_scan_brute(b, qt, 0, ne, kSPerEntry, lo, hi, sink, h->stream, nullptr);
-        cudaEventRecord(e1, h->stream);
-        cudaEventSynchronize(e1);
-    }
-    cudaEventElapsedTime(&ms, e0, e1);
-    B.brute_entry_bases_per_s = ne * static_cast<double>(b.nbases) / std::max(1e-6, ms * 1e-3);
-    // seed scan with a one-query table: positions per second per table
-    IndexedState one;
-    std::vector<uint8_t> in(nq, 0);
-    std::vector<uint32_t> svec(nq, 0);
-    for (uint32_t q = 0; q < nq; q++) svec[q] = q < h->qs_s.size() ? h->qs_s[q] : 0u;
-    uint32_t pick = 0;
-    while (pick < nq && h->qs[pick].size() < 8) pick++;
-    double pos_rate = 1e11, cand_rate = 1e10;
-    if (pick < nq && e == cudaSuccess) {
-        in[pick] = 1;
-        st = indexed_plan_q(one, h->qs, svec, in, h->cfg, h->stream, h->err);
-        if (st == IFA_OK) st = indexed_tables(one, h->qs, h->qmeta_host, h->qwords_host, h->wmax, h->cfg, h->stream, h->err);
-        if (st == IFA_OK && one.targ.n) {
-            cudaMalloc(&one.d_candidates, sizeof(unsigned long long));
-            cudaMemsetAsync(one.d_candidates, 0, sizeof(unsigned long long), h->stream);
-            for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
-                cudaEventRecord(e0, h->stream);
-                e = launch_seed_scan(b, qt, one.targ, one.d_entry_minhits, h->cfg.kmer_step, kSPerEntry, sink,
-                                     one.d_candidates, h->stream);
-                cudaEventRecord(e1, h->stream);
-                cudaEventSynchronize(e1);
-            }
-            cudaEventElapsedTime(&ms, e0, e1);
-            pos_rate = b.nbases / std::max(1e-6, ms * 1e-3);
-            // candidates: a dense table (every query of the handle at k = 8)
-            IndexedState dense;
-            std::vector<uint8_t> all(nq, 0);
-            for (uint32_t q = 0; q < nq && q < 4096; q++) all[q] = h->qs[q].size() >= 8;
-            ifa_config c8 = h->cfg;
-            c8.k_list[0] = 8;
-            c8.n_k = 1;
-            c8.minhits_num = 1;
-            c8.minhits_den = 1;  // deterministic bound: no Monte Carlo
-            st = indexed_plan_q(dense, h->qs, svec, all, c8, h->stream, h->err);
-            if (st == IFA_OK) st = indexed_tables(dense, h->qs, h->qmeta_host, h->qwords_host, h->wmax, c8, h->stream, h->err);
-            if (st == IFA_OK && dense.targ.n) {
-                cudaMalloc(&dense.d_candidates, sizeof(unsigned long long));
-                cudaMemsetAsync(dense.d_candidates, 0, sizeof(unsigned long long), h->stream);
-                cudaEventRecord(e0, h->stream);
-                e = launch_seed_scan(b, qt, dense.targ, dense.d_entry_minhits, 1, kSPerEntry, sink,
-                                     dense.d_candidates, h->stream);
-                cudaEventRecord(e1, h->stream);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&ms, e0, e1);
-                unsigned long long nc = 0;
-                cudaMemcpy(&nc, dense.d_candidates, sizeof(nc), cudaMemcpyDeviceToHost);
-                const double t = ms * 1e-3 - b.nbases / pos_rate;
-                if (nc > 1000 && t > 0) cand_rate = nc / t;
-            }
-            dense.release();
-        }
-        one.release();
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(scratch);
-    if (st != IFA_OK) return st;
-    if (e != cudaSuccess) return bfail(h, IFA_ERR_CUDA, std::string("calibration: ") + cudaGetErrorString(e));
-    B.seed_pos_per_s = pos_rate;
-    B.cand_per_s = cand_rate;
-    return IFA_OK;
+    std::vector<uint32_t> svec(h->qs.size(), 0);
+    for (size_t q = 0; q < svec.size(); q++) svec[q] = q < h->qs_s.size() ? h->qs_s[q] : 0u;
+    return rates_on_store(h, store_batch(B), h->qs, svec, B.rates);
 }
 
 }  // namespace
@@ -777,7 +652,7 @@ ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, con
     B.nbases += len;
     B.pieces_dirty = true;
     B.plan_valid = false;
-    B.brute_entry_bases_per_s = 0;
+    B.rates = Rates{};
     return IFA_OK;
 }
 
@@ -812,7 +687,7 @@ ifa_status ifa_ref_reset(ifa_handle *h) {
     B.pieces_dirty = true;
     B.open = false;
     B.any_contig = false;
-    B.brute_entry_bases_per_s = 0;
+    B.rates = Rates{};
     return IFA_OK;
 }
 

@@ -11,6 +11,20 @@
 
 namespace ifa {
 
+// Measured rates of the two modes' work (autotune.cu).
+struct Rates {
+    double brute = 0;   // brute-force entry x base evaluations per second
+    double pos = 0;     // seed scan: reference positions x tables per second
+    double cand = 0;    // verified candidates per second
+    bool valid() const { return brute > 0; }
+};
+
+// Predicted seconds per reference base of a query set in each mode.
+struct ModeCost {
+    double brute_s = 0, idx_s = 0;
+    bool seeded = false;   // some query has a seed plan (else indexed = brute force)
+};
+
 struct QuerySet {
     uint32_t first = 0, n = 0;      // global query ids [first, first + n)
     uint32_t s = 0;                 // maxSubs (capped at 255)
@@ -88,9 +102,7 @@ struct BatchState {
     cudaStream_t graph_stream = nullptr;
 
     // autotuner measurements (per handle)
-    double brute_entry_bases_per_s = 0;  // entry x base evaluations per second
-    double seed_pos_per_s = 0;           // positions x tables per second
-    double cand_per_s = 0;               // verified candidates per second
+    Rates rates;
 };
 
 }  // namespace ifa
@@ -152,6 +164,7 @@ struct ServeState {
     uint64_t slices_run = 0;
     double scanned_query_bases = 0;   // nominal comparisons done by completed slices
     double plan_s = 0, scan_s = 0;    // host time building plans, time waiting for slices
+    Rates rates;                      // measured on the store at the first automatic request
 };
 
 }  // namespace ifa

@@ -140,9 +140,32 @@ ifa_status ensure_pieces(ifa_handle *h, int slot, uint32_t n) {
     return IFA_OK;
 }
 
-ifa_mode resolve_mode(const ifa_handle *h) {
-    if (h->mode != IFA_MODE_AUTO) return h->mode;
-    return h->qs.size() >= h->cfg.auto_crossover ? IFA_MODE_INDEXED : IFA_MODE_BRUTE;
+// The mode of the streaming pass: the explicit one; for IFA_MODE_AUTO the
+// paper's rule by query count when auto_crossover > 0, else the measured-
+// rate model (rates taken once per handle and maxSubs on the calibration
+// sequence, before the stream's first segment is scanned).
+ifa_status resolve_mode(ifa_handle *h, ifa_mode *out) {
+    if (h->mode != IFA_MODE_AUTO) {
+        *out = h->mode;
+        return IFA_OK;
+    }
+    if (h->cfg.auto_crossover) {
+        *out = h->qs.size() >= h->cfg.auto_crossover ? IFA_MODE_INDEXED : IFA_MODE_BRUTE;
+        return IFA_OK;
+    }
+    if (h->auto_mode == IFA_MODE_AUTO || h->auto_s != h->max_subs) {
+        Rates r;
+        ifa_status st = rates_on_random(h, h->qs, std::vector<uint32_t>(h->qs.size(), h->max_subs), r);
+        if (st != IFA_OK) return st;
+        ifa_mode m = IFA_MODE_BRUTE;
+        st = choose_mode(h, r, h->qs, h->max_subs, &m);
+        if (st != IFA_OK) return st;
+        h->auto_rates = r;
+        h->auto_s = h->max_subs;
+        h->auto_mode = m;
+    }
+    *out = h->auto_mode;
+    return IFA_OK;
 }
 
 HitSink make_sink(const ifa_handle *h) {
@@ -340,7 +363,7 @@ ifa_status ifa_config_default(ifa_config *cfg) {
     cfg->minhits_seed = 1;
     cfg->clip_pct = 0;
     cfg->exhaustive_fallback = 0;
-    cfg->auto_crossover = 150;  // paper: crossover between 100 and 200 queries (RefSeq)
+    cfg->auto_crossover = 0;    // measured rates (the paper's count rule: 150, between its 100 and 200)
     return IFA_OK;
 }
 
@@ -484,6 +507,7 @@ ifa_status ifa_load_queries(ifa_handle *h, const uint8_t *const *seqs, const uin
         h->lmax = std::max(h->lmax, lens[i]);
     }
     h->qdirty = true;
+    h->auto_mode = IFA_MODE_AUTO;   // the automatic choice is redone for the new set
     cudaFree(h->d_qcount);
     h->d_qcount = nullptr;
     CK(h, cudaMalloc(&h->d_qcount, std::max<size_t>(1, h->qs.size()) * sizeof(unsigned long long)));
@@ -543,7 +567,10 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
     CK(h, cudaSetDevice(h->dev));
     ifa_status st = upload_queries(h);
     if (st != IFA_OK) return st;
-    const ifa_mode mode = resolve_mode(h);
+    ifa_mode mode = IFA_MODE_BRUTE;
+    st = resolve_mode(h, &mode);
+    if (st != IFA_OK) return st;
+    h->mode_run = mode;
     if (mode == IFA_MODE_INDEXED) {
         st = indexed_prepare(h->idx, h->qs, h->qmeta_host, h->qwords_host, h->wmax, h->cfg, h->max_subs,
                              h->stream, h->err);
@@ -731,9 +758,43 @@ ifa_status ifa_flush(ifa_handle *h) {
         CK(h, cudaMemcpy(&tcs, h->d_tc_status, sizeof(tcs), cudaMemcpyDeviceToHost));
         if (tcs) return fail(h, IFA_ERR_TIMEOUT, "tensor-core scan: a pipeline wait gave up; results incomplete");
     }
+#ifdef IFA_BOUNDS_CHECK
+    if (unsigned long long *bw = bounds_word()) {
+        unsigned long long v = 0;
+        CK(h, cudaMemcpy(&v, bw, sizeof(v), cudaMemcpyDeviceToHost));
+        if (v) {
+            char m[128];
+            std::snprintf(m, sizeof m, "bounds check: read of kind %llu at index %llu out of range; results invalid",
+                          v >> 56, v & ((1ull << 56) - 1));
+            return fail(h, IFA_ERR_CUDA, m);
+        }
+    }
+#endif
     uint32_t ov = 0;
     CK(h, cudaMemcpy(&ov, h->d_overflow, sizeof(ov), cudaMemcpyDeviceToHost));
     if (ov) return fail(h, IFA_ERR_HIT_OVERFLOW, "hit buffer overflowed; some hit tuples were dropped");
+    return IFA_OK;
+}
+
+ifa_status ifa_bounds_check(int device, uint64_t *first, uint32_t *enabled, int reset) {
+    if (!first || !enabled) return fail(nullptr, IFA_ERR_INVALID_ARG, "NULL argument");
+    *first = 0;
+#ifdef IFA_BOUNDS_CHECK
+    *enabled = 1;
+    cudaError_t e = cudaSetDevice(device);
+    unsigned long long *bw = e == cudaSuccess ? bounds_word() : nullptr;
+    if (e == cudaSuccess && !bw) e = cudaErrorSymbolNotFound;
+    unsigned long long v = 0;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&v, bw, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && reset) e = cudaMemset(bw, 0, sizeof(v));
+    if (e != cudaSuccess) return fail_cuda(nullptr, "ifa_bounds_check", e);
+    *first = v;
+#else
+    (void)device;
+    (void)reset;
+    *enabled = 0;
+#endif
     return IFA_OK;
 }
 
@@ -840,6 +901,7 @@ ifa_status ifa_get_stats(ifa_handle *h, ifa_stats *s) {
     if (st != IFA_OK) return st;
     *s = h->stats;
     s->candidates = h->idx.candidates_host(h->stream);
+    s->mode = h->mode_run;
     return IFA_OK;
 }
 

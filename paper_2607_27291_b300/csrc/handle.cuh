@@ -92,6 +92,12 @@ struct ifa_handle {
 
     uint32_t max_subs = 0;
     ifa_mode mode = IFA_MODE_BRUTE;
+    // IFA_MODE_AUTO by measured rates: rates on the calibration sequence
+    // (per maxSubs, auto_s) and the mode they gave for the loaded queries
+    ifa::Rates auto_rates;
+    uint32_t auto_s = 0xffffffffu;
+    ifa_mode auto_mode = IFA_MODE_AUTO;
+    ifa_mode mode_run = IFA_MODE_AUTO;   // the mode the current pass runs in
     ifa_stats stats{};
 
     // optional per-launch timing of the scan kernels (config.profile)
@@ -123,6 +129,28 @@ void tc_operand(const std::vector<std::string> &qs, uint32_t lpad, std::vector<u
 // kernel should scan such a brute-force query set (the automatic rule).
 double mean_window_hit_rate(const std::vector<std::string> &qs, uint32_t first, uint32_t n, uint32_t s);
 bool tc_auto_choice(const std::vector<std::string> &qs, uint32_t first, uint32_t n, uint32_t s);
+
+// The measured-rate choice of IFA_MODE_AUTO (autotune.cu).
+// Expected random seed hits per reference base of one entry of length L.
+double seed_hits_per_base(uint32_t L, uint32_t k, uint32_t step);
+// Cost of queries [first, first + n) of qs under rates r and seed plan
+// `plan` (indexed by query; plan_exhaustive empty = no plan).
+ModeCost predict_cost(const Rates &r, const std::vector<std::string> &qs, uint32_t first, uint32_t n,
+                      const IndexedState &plan, uint32_t step);
+// Measure the rates on batch b with (up to 128 of) the queries qs at
+// maxSubs svec; count-only sinks, so no result of the handle changes.
+ifa_status measure_rates(ifa_handle *h, const Batch &b, const std::vector<std::string> &qs,
+                         const std::vector<uint32_t> &svec, Rates &out);
+// The mode with the smaller predicted time for qs at maxSubs s.
+ifa_status choose_mode(ifa_handle *h, const Rates &r, const std::vector<std::string> &qs, uint32_t s,
+                       ifa_mode *mode);
+// Rates measured on 16 Mbp of uniform random bases packed on the device
+// (the streaming calls, and stores smaller than that), or on a slice of
+// the store.
+ifa_status rates_on_random(ifa_handle *h, const std::vector<std::string> &qs, const std::vector<uint32_t> &svec,
+                           Rates &out);
+ifa_status rates_on_store(ifa_handle *h, const Batch &store, const std::vector<std::string> &qs,
+                          const std::vector<uint32_t> &svec, Rates &out);
 // Free the serving state.
 void serve_release(ifa_handle *h);
 }  // namespace ifa

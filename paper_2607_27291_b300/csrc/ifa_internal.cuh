@@ -142,16 +142,41 @@ struct Batch {
     uint32_t halo;            // halo region length H; windows must end at or after base H
     const DevPiece *pieces;
     uint32_t npieces;
+    // allocated sizes of hl, dir and exc, and the device word that records
+    // the first out-of-range read (read only by IFA_BOUNDS_CHECK builds)
+    uint64_t nwords, ndir, nexc;
+    unsigned long long *bounds;
 };
+
+// Bounds-checked builds (-DIFA_BOUNDS_CHECK): every read of the packed
+// reference checks its index; the first one out of range is recorded as
+// kind << 56 | index in b.bounds (kinds below) and reads as an all-N word,
+// so no window through it hits.  The host reports the word
+// (ifa_bounds_check); nothing traps.  Default builds compile no check.
+enum BoundsKind : uint32_t { kBoundsWord = 1, kBoundsDir = 2, kBoundsExc = 3 };
+#ifdef IFA_BOUNDS_CHECK
+__device__ __forceinline__ bool in_range(const Batch &b, uint32_t kind, uint64_t i, uint64_t n) {
+    if (i < n) return true;
+    if (b.bounds)
+        atomicCAS(b.bounds, 0ull, (static_cast<unsigned long long>(kind) << 56) | (i & ((1ull << 56) - 1)));
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_range(const Batch &, uint32_t, uint64_t, uint64_t) { return true; }
+#endif
 
 // The four planes {hi, lo, N, B} of word w.
 __device__ __forceinline__ uint4 ref_word(const Batch &b, uint64_t w) {
+    if (!in_range(b, kBoundsWord, w, b.nwords) || !in_range(b, kBoundsDir, w >> 5, b.ndir))
+        return make_uint4(0u, 0u, 0xffffffffu, 0u);
     const uint2 a = __ldg(b.hl + w);
     const uint2 d = __ldg(b.dir + (w >> 5));
     const uint32_t bit = 1u << (w & 31u);
     uint32_t n = 0, s = 0;
     if (d.x & bit) {
-        const uint2 x = __ldg(b.exc + d.y + __popc(d.x & (bit - 1u)));
+        const uint64_t xi = d.y + __popc(d.x & (bit - 1u));
+        if (!in_range(b, kBoundsExc, xi, b.nexc)) return make_uint4(0u, 0u, 0xffffffffu, 0u);
+        const uint2 x = __ldg(b.exc + xi);
         n = x.x;
         s = x.y;
     }
@@ -258,6 +283,9 @@ cudaError_t pack_batch(const RefBufs &R, const uint8_t *halo, uint32_t hlen, uin
                        uint64_t slen, uint64_t nwords, const DevPiece *pieces, uint32_t npieces, bool mark,
                        cudaStream_t st, int *launches);
 Batch make_batch(const RefBufs &R, uint64_t nbases, uint32_t halo, const DevPiece *pieces, uint32_t npieces);
+// The device word of the first out-of-range read on the current device
+// (IFA_BOUNDS_CHECK builds; nullptr otherwise).
+unsigned long long *bounds_word();
 cudaError_t launch_halo_update(const uint8_t *old_halo, uint32_t old_len, const uint8_t *seg,
                                uint64_t slen, uint32_t new_len, uint8_t *new_halo, cudaStream_t st);
 

@@ -232,8 +232,32 @@ Batch make_batch(const RefBufs &R, uint64_t nbases, uint32_t halo, const DevPiec
     b.halo = halo;
     b.pieces = pieces;
     b.npieces = npieces;
+    b.nwords = R.words_cap;
+    b.ndir = R.words_cap ? dir_entries(R.words_cap) : 0;
+    b.nexc = R.exc_cap;
+    b.bounds = bounds_word();
     return b;
 }
+
+#ifdef IFA_BOUNDS_CHECK
+namespace {
+__device__ unsigned long long g_bounds_word;   // zero-initialised when the module loads
+}
+
+unsigned long long *bounds_word() {
+    static unsigned long long *word[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (!word[dev & 63]) {
+        void *a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_bounds_word) == cudaSuccess) word[dev & 63] = static_cast<unsigned long long *>(a);
+        else (void)cudaGetLastError();
+    }
+    return word[dev & 63];
+}
+#else
+unsigned long long *bounds_word() { return nullptr; }
+#endif
 
 cudaError_t launch_halo_update(const uint8_t *old_halo, uint32_t old_len, const uint8_t *seg,
                                uint64_t slen, uint32_t new_len, uint8_t *new_halo, cudaStream_t st) {

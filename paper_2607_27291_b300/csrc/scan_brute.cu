@@ -54,6 +54,7 @@ k_scan_brute(Batch b, QueryTable qt, uint32_t e0, uint32_t e1, uint32_t s, uint3
     extern __shared__ uint4 smem4[];
     __shared__ __align__(16) ifa_hit wbuf[kScanWarps][32];
     __shared__ __align__(8) uint2 stage[kScanWarps][2][Stage<WMAX>::kSlots];
+    __shared__ uint16_t cq[kScanWarps][kQRows][32];
     __shared__ uint32_t s_nF, s_nM;
     const uint32_t nent = e1 - e0;
     const Smem m = load_chunk<WMAX>(qt, e0, e1, s, smem4, &s_nF, &s_nM);
@@ -65,7 +66,7 @@ k_scan_brute(Batch b, QueryTable qt, uint32_t e0, uint32_t e1, uint32_t s, uint3
     lane_multipliers(mul);
     const uint64_t nblk = (b.nbases + 32 * kWin - 1) / (32 * kWin);
     scan_blocks<WMAX>(b, qt, m, nent, s_nF, s_nM, e0, s, lmin, lmax, sink, wh, stage[warp], mul, 0, nblk,
-                      blockIdx.x * kScanWarps + warp, gridDim.x * kScanWarps, lane);
+                      blockIdx.x * kScanWarps + warp, gridDim.x * kScanWarps, lane, cq[warp]);
     wh.finish(sink, lane);
     __syncthreads();
     flush_counts(qt, m, nent, e0, sink);

@@ -42,12 +42,29 @@ namespace brute {
 
 constexpr int kScanThreads = 256;
 constexpr int kScanWarps = kScanThreads / kWarp;
-constexpr size_t kScanSmemBudget = 40 * 1024;  // dynamic; + static (hit staging, word staging) < 48 KB
 #ifndef IFA_SCAN_GROUP
 #define IFA_SCAN_GROUP 4
 #endif
 constexpr int kGroup = IFA_SCAN_GROUP;          // entries per warp vote in the hot loop
 constexpr int kWin = 4;                         // windows per lane (32 * kWin per warp step)
+// Candidate queue (per warp, one column per lane): entries whose word 0
+// passes in a lane wait there as 16-bit record indices until the block ends
+// (or a column is nearly full), then every lane recounts its own candidates
+// at once.  0 = the warp-wide exact path per fired entry instead.
+#ifndef IFA_SCAN_QUEUE
+#define IFA_SCAN_QUEUE 8
+#endif
+constexpr int kQDepth = IFA_SCAN_QUEUE;
+constexpr uint32_t kQClassM = 0x8000u;          // queued index of a class-M record
+static_assert(kQDepth == 0 || kQDepth >= kGroup, "a queue column holds at least one group");
+constexpr int kQRows = kQDepth > 0 ? kQDepth : 1;  // shared rows per warp
+
+// Static shared memory of a scan kernel (streaming or persistent, 8 warps)
+// at the widest entries: hit staging, word staging (kWin + 8 words and two
+// directory entries, double buffered), the candidate queue, a few counters.
+// The dynamic query chunk gets the rest of 48 KB, whole kilobytes.
+constexpr size_t kScanStaticSmem = kScanWarps * (32 * 16 + 2 * (kWin + 8 + 2) * 8 + kQRows * 32 * 2) + 64;
+constexpr size_t kScanSmemBudget = (48 * 1024 - kScanStaticSmem) / 1024 * 1024;
 
 // Per-entry shared memory: WMAX uint4 words, a class-M word-0 record, a
 // class-F word-0 record, meta, count, and two 16-bit index slots.
@@ -173,7 +190,7 @@ __device__ __forceinline__ void exact_fast(const Batch &b, const QueryTable &qt,
                                            const uint2 *R, const uint32_t *hw, const uint32_t *lw,
                                            const uint32_t *mul, uint32_t e, uint32_t e0, uint32_t blk,
                                            uint32_t lane, uint32_t s, const HitSink &sink, WH &wh, uint32_t v,
-                                           uint32_t bias) {
+                                           uint32_t bias, bool act = true) {
     const uint32_t meta = m.meta[e];
     const uint4 *qw = m.sq + static_cast<size_t>(e) * WMAX;
     uint32_t hm, d;
@@ -231,7 +248,7 @@ __device__ __forceinline__ void exact_fast(const Batch &b, const QueryTable &qt,
             for (int k = 0; k < kWin; k++) hm |= (((d >> (8 * k)) & 0xffu) <= se ? 0x80u : 0u) << (8 * k);
         }
     }
-    wh.event(b, qt.ids, e0, m.cnt, sink, lane, hm != 0u, e, d, blk, hm);
+    wh.event(b, qt.ids, e0, m.cnt, sink, lane, act && hm != 0u, e, d, blk, hm);
 }
 
 // Entry word-0 records: {hi0, lo0, bias, -} (class F) or
@@ -252,13 +269,52 @@ __device__ __forceinline__ uint32_t packed_counts(const uint4 &q, const uint32_t
     return v;
 }
 
+// Recount the queued candidates of the lane's windows in this block: row r
+// of every column at once, each lane its own (entry, class), then one event
+// per lane.  Leaves the queue empty (all lanes, warp converged).
+template <int WMAX, class WH>
+__device__ __forceinline__ void drain_queue(const Batch &b, const QueryTable &qt, const Smem &m, uint16_t (*cq)[32],
+                                            uint32_t &qn, const uint32_t *hw, const uint32_t *lw,
+                                            const uint32_t *mul, const uint2 *R, uint32_t e0, uint32_t blk,
+                                            uint32_t lane, uint32_t s, const HitSink &sink, WH &wh) {
+    const uint32_t rows = __reduce_max_sync(0xffffffffu, qn);
+#pragma unroll 1
+    for (uint32_t r = 0; r < rows; r++) {
+        // a lane without an r-th candidate reads no record (a class may be
+        // empty) and runs the path on entry 0 of the chunk, emitting nothing
+        const bool act = r < qn;
+        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t e = 0, bias = 0, care = 0;
+        if (act) {
+            const uint32_t c = cq[r][lane];
+            const uint32_t k = c & (kQClassM - 1u);
+            if (c & kQClassM) {
+                q = m.sM[k];   // {hi0, lo0, care0, bias}
+                e = m.midx[k];
+                care = q.z;
+                bias = q.w;
+            } else {
+                q = m.sF[k];   // {hi0, lo0, bias, -}: care all ones
+                e = m.fidx[k];
+                care = 0xffffffffu;
+                bias = q.z;
+            }
+        }
+        const uint32_t v = packed_counts<true>(make_uint4(q.x, q.y, care, bias), hw, lw, mul);
+        exact_fast<WMAX>(b, qt, m, R, hw, lw, mul, e, e0, blk, lane, s, sink, wh, v, bias, act);
+    }
+    qn = 0;
+}
+
 template <int WMAX, bool MASKED, class WH>
 __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt, const Smem &m,
                                            const uint4 *rec, const uint16_t *idx, uint32_t n,
                                            const uint32_t *hw, const uint32_t *lw, const uint32_t *mul,
                                            const uint2 *R, uint32_t e0, uint32_t blk, uint32_t lane,
-                                           uint32_t s, const HitSink &sink, WH &wh) {
+                                           uint32_t s, const HitSink &sink, WH &wh, uint16_t (*cq)[32],
+                                           uint32_t &qn) {
     constexpr uint32_t kHigh = 0x80808080u;
+    constexpr uint32_t cls = MASKED ? kQClassM : 0u;
     uint32_t k = 0;
     for (; k + kGroup <= n; k += kGroup) {
         uint32_t v[kGroup];
@@ -267,7 +323,17 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
         uint32_t acc = v[0];
 #pragma unroll
         for (int i = 1; i < kGroup; i++) acc &= v[i];
-        if (__any_sync(0xffffffffu, (acc & kHigh) != kHigh)) {
+        if constexpr (kQDepth > 0) {
+            if (__any_sync(0xffffffffu, (acc & kHigh) != kHigh)) {
+                // queue the lane's passing entries; drain while a column
+                // could not take another group
+#pragma unroll
+                for (int i = 0; i < kGroup; i++)
+                    if ((v[i] & kHigh) != kHigh) cq[qn++][lane] = static_cast<uint16_t>((k + i) | cls);
+                if (__any_sync(0xffffffffu, qn > static_cast<uint32_t>(kQDepth - kGroup)))
+                    drain_queue<WMAX>(b, qt, m, cq, qn, hw, lw, mul, R, e0, blk, lane, s, sink, wh);
+            }
+        } else if (__any_sync(0xffffffffu, (acc & kHigh) != kHigh)) {
             // which of the group's entries fired in any lane; one (not
             // unrolled) copy of the exact path walks them
             uint32_t fired = 0;
@@ -291,9 +357,16 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
     for (; k < n; k++) {
         const uint4 q = rec[k];
         const uint32_t v = packed_counts<MASKED>(q, hw, lw, mul);
-        if (__any_sync(0xffffffffu, (v & kHigh) != kHigh))
-            exact_fast<WMAX>(b, qt, m, R, hw, lw, mul, idx[k], e0, blk, lane, s, sink, wh, v,
-                             MASKED ? q.w : q.z);
+        if (__any_sync(0xffffffffu, (v & kHigh) != kHigh)) {
+            if constexpr (kQDepth > 0) {
+                if ((v & kHigh) != kHigh) cq[qn++][lane] = static_cast<uint16_t>(k | cls);
+                if (__any_sync(0xffffffffu, qn > static_cast<uint32_t>(kQDepth - kGroup)))
+                    drain_queue<WMAX>(b, qt, m, cq, qn, hw, lw, mul, R, e0, blk, lane, s, sink, wh);
+            } else {
+                exact_fast<WMAX>(b, qt, m, R, hw, lw, mul, idx[k], e0, blk, lane, s, sink, wh, v,
+                                 MASKED ? q.w : q.z);
+            }
+        }
     }
 }
 
@@ -303,9 +376,16 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
 template <int NW>
 __device__ __forceinline__ void stage_block(const Batch &b, uint64_t blk, uint2 *dst, uint32_t lane) {
     if (lane < NW + 2) {
-        const uint2 *src = lane < NW ? b.hl + blk * kWin + lane : b.dir + ((blk * kWin) >> 5) + (lane - NW);
-        const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + lane));
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+        const uint64_t i = lane < NW ? blk * kWin + lane : ((blk * kWin) >> 5) + (lane - NW);
+        if (lane < NW ? in_range(b, kBoundsWord, i, b.nwords) : in_range(b, kBoundsDir, i, b.ndir)) {
+            const uint2 *src = lane < NW ? b.hl + i : b.dir + i;
+            const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + lane));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+        } else {
+            // out of range (checked builds): a directory entry marking every
+            // word special sends the block down the generic path
+            dst[lane] = make_uint2(lane < NW ? 0u : 0xffffffffu, 0u);
+        }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -405,7 +485,7 @@ __device__ __forceinline__ void scan_blocks(const Batch &b, const QueryTable &qt
                                             uint32_t lmax, const HitSink &sink, WH &wh,
                                             uint2 (*stage)[Stage<WMAX>::kSlots], const uint32_t *mul,
                                             uint64_t base, uint64_t blk_end, uint32_t w, uint32_t nw,
-                                            uint32_t lane) {
+                                            uint32_t lane, uint16_t (*cq)[32]) {
     constexpr int NW = Stage<WMAX>::kWords;
     static_assert(32 * kWin == kEventBlock, "events address blocks of 32 x kWin windows");
     wh.flush(sink, lane);  // the staging buffer now takes events
@@ -444,8 +524,13 @@ __device__ __forceinline__ void scan_blocks(const Batch &b, const QueryTable &qt
             lw[k] = __funnelshift_r(R[k].y, R[k + 1].y, lane);
         }
         const uint32_t bi = static_cast<uint32_t>(blk);
-        scan_class<WMAX, false>(b, qt, m, m.sF, m.fidx, nF, hw, lw, mul, R, e0, bi, lane, s, sink, wh);
-        scan_class<WMAX, true>(b, qt, m, m.sM, m.midx, nM, hw, lw, mul, R, e0, bi, lane, s, sink, wh);
+        uint32_t qn = 0;  // this lane's queued candidates
+        scan_class<WMAX, false>(b, qt, m, m.sF, m.fidx, nF, hw, lw, mul, R, e0, bi, lane, s, sink, wh, cq, qn);
+        scan_class<WMAX, true>(b, qt, m, m.sM, m.midx, nM, hw, lw, mul, R, e0, bi, lane, s, sink, wh, cq, qn);
+        if constexpr (kQDepth > 0) {
+            if (__any_sync(0xffffffffu, qn != 0u))
+                drain_queue<WMAX>(b, qt, m, cq, qn, hw, lw, mul, R, e0, bi, lane, s, sink, wh);
+        }
         __syncwarp();
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");

@@ -92,7 +92,11 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                             // the window's words w0 .. w0 + W: hi/lo words, and
                             // the N / piece-start masks only when the directory
                             // marks one of them special
-                            const uint2 d0 = __ldg(b.dir + (w0 >> 5)), d1 = __ldg(b.dir + (w0 >> 5) + 1);
+                            // (checked builds: an out-of-range entry reads as all special,
+                            // and ref_word checks the words)
+                            const bool dok = in_range(b, kBoundsDir, (w0 >> 5) + 1, b.ndir);
+                            const uint2 d0 = dok ? __ldg(b.dir + (w0 >> 5)) : make_uint2(0xffffffffu, 0u);
+                            const uint2 d1 = dok ? __ldg(b.dir + (w0 >> 5) + 1) : make_uint2(0xffffffffu, 0u);
                             const bool spec = special_bits(d0.x, d1.x, w0, W + 1) != 0u;
                             uint4 cur;
                             if (spec) {

@@ -73,6 +73,19 @@ uint64_t request_bytes(const ServeState &S, const Request &r) {
 // Encoding and (indexed requests) per-query plan of one request, made once.
 ifa_status prepare_request(ifa_handle *h, Request &r) {
     if (r.prepared) return IFA_OK;
+    if (r.mode == IFA_MODE_AUTO) {
+        // rates measured once per session on the store, with the first
+        // automatic request's queries
+        ServeState &S = h->serve;
+        if (!S.rates.valid()) {
+            const BatchState &B = h->batch;
+            const Batch b = make_batch(B.ref, B.nbases, 0, B.d_pieces, B.d_pieces_n);
+            const ifa_status st = rates_on_store(h, b, r.qs, std::vector<uint32_t>(r.qs.size(), r.s), S.rates);
+            if (st != IFA_OK) return st;
+        }
+        const ifa_status st = choose_mode(h, S.rates, r.qs, r.s, &r.mode);
+        if (st != IFA_OK) return st;
+    }
     uint32_t lmax = 1;
     for (const auto &q : r.qs) lmax = std::max<uint32_t>(lmax, static_cast<uint32_t>(q.size()));
     r.w = 1;
@@ -331,8 +344,11 @@ ifa_status ifa_serve_submit(ifa_handle *h, const uint8_t *const *seqs, const uin
         r.qs.emplace_back(reinterpret_cast<const char *>(seqs[i]), lens[i]);
     }
     r.s = std::min<uint32_t>(max_subs, 255);
-    // automatic mode: the paper's rule, by query count (Discussion)
-    r.mode = mode == IFA_MODE_AUTO ? (n >= h->cfg.auto_crossover ? IFA_MODE_INDEXED : IFA_MODE_BRUTE) : mode;
+    // automatic mode: the paper's rule by query count (Discussion) when a
+    // crossover is configured, else measured rates at admission
+    r.mode = mode;
+    if (mode == IFA_MODE_AUTO && h->cfg.auto_crossover)
+        r.mode = n >= h->cfg.auto_crossover ? IFA_MODE_INDEXED : IFA_MODE_BRUTE;
     r.t_submit = now_s() - S.t0;
     r.cap = S.ring_cap;
     r.bytes = request_bytes(S, r);

@@ -35,6 +35,19 @@ def test_library_exports_every_declared_symbol():
     assert sorted(P.exported_symbols()) == names
 
 
+def test_bounds_checked_library_exports_the_same_symbols():
+    """libifa_bc.so (-DIFA_BOUNDS_CHECK) is the same ABI: every declared
+    function, nothing else of the ifa_ prefix."""
+    from paper_2607_27291_b300 import build as b
+    assert os.path.exists(b.BC_LIB_PATH)
+    lib = C.CDLL(b.BC_LIB_PATH)
+    for n in _declared():
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", b.BC_LIB_PATH], capture_output=True, text=True).stdout
+    exported = sorted({w for w in re.findall(r"\b(ifa_[a-z_]+)\b", out)})
+    assert exported == _declared()
+
+
 def test_struct_layout_matches_header():
     src = r'''
 #include <stdio.h>
@@ -68,7 +81,10 @@ def test_defaults_are_the_papers():
     assert (cfg.minhits_num, cfg.minhits_den) == (g["minhits_probability"]["num"],
                                                   g["minhits_probability"]["den"])
     assert cfg.minhits_trials == g["minhits_trials"]["value"]
-    assert g["crossover_queries"]["low"] <= cfg.auto_crossover <= g["crossover_queries"]["high"]
+    # IFA_MODE_AUTO defaults to measured rates; the paper's count rule is
+    # the configured alternative (tests/test_gpu_auto.py sets it from the
+    # paper's 100-200 range)
+    assert cfg.auto_crossover == 0
     assert cfg.clip_pct == 0 and cfg.kmer_step == 1 and cfg.mask_width == 0
 
 

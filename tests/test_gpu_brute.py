@@ -213,3 +213,30 @@ def test_candidates_staged_across_fast_and_generic_blocks(s):
     assert tuples(got) == tuples(exp)
     assert dig == oracle.digest(exp)
     assert counts.tolist() == np.bincount(exp["query"], minlength=len(wl.queries)).tolist()
+
+
+@pytest.mark.parametrize("lens,s", [((44, 60), 22), ((18, 22), 11), ((30, 34), 16)])
+def test_candidate_queue_fills_within_a_block(lens, s):
+    """Word 0 passes in a fifth of the windows or more here, so a lane
+    queues several of the 36 entries within one block of 128 windows and the
+    warp drains its candidate queue before the block ends (class F entries,
+    class M entries with an N or a partial first word, an AT-rich stretch
+    that passes everywhere).  Every hit must equal the oracle's."""
+    rng = np.random.default_rng(1000 + s)
+    wl = synth.small_workload(seed=300 + s, n_queries=16, lmin=lens[0], lmax=lens[1], n_contigs=40, cmin=50,
+                              cmax=60000, n_frac=0.002, plant_ks=[0, s // 2, s] * 4)
+    ref = wl.ref
+    a = int(rng.integers(0, len(ref) - 20000))
+    ref[a:a + 20000] = rng.choice(np.frombuffer(b"AT", np.uint8), 20000)
+    qs = list(wl.queries)
+    qs[3] = qs[3][:5] + b"N" + qs[3][6:]
+    qs[7] = bytes(rng.choice(np.frombuffer(b"AT", np.uint8), len(qs[7])))
+    qs.append(bytes(rng.choice(np.frombuffer(b"AAT", np.uint8), lens[1])))
+    qs.append(b"N" + bytes(rng.choice(np.frombuffer(b"ACGT", np.uint8), lens[0] - 1)))
+    got, over, dig, counts, _ = gpu_scan(qs, ref, wl.contig_len, s, seg_bytes=1 << 19,
+                                         brute_kernel=P.IFA_BRUTE_POPC, hit_capacity=1 << 23)
+    exp = oracle.brute(qs, ref, wl.contig_len, s, threads=8)
+    assert not over and exp.size > 1000
+    assert tuples(got) == tuples(exp)
+    assert dig == oracle.digest(exp)
+    assert counts.tolist() == np.bincount(exp["query"], minlength=len(qs)).tolist()

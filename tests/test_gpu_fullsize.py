@@ -267,6 +267,7 @@ def test_200gbp_serving_store_sampled_parity():
         for rid, (qs, s) in zip(ids, rq):
             info = P.ifa_serve_poll(h, rid)
             assert info["state"] == 2 and not info["overflowed"]
+            assert info["mode"] == P.IFA_MODE_BRUTE      # the measured rates pick brute force for 3-4 queries
             hits, over = P.ifa_serve_drain(h, rid, 1 << 22)
             assert not over and hits.size == info["digest"][0] == info["hits"]
             mine = P.sort_hits(hits[np.isin(hits["contig"], sample)])
