@@ -300,7 +300,7 @@ ifa_status indexed_tables(IndexedState &S, const std::vector<std::string> &qs,
 ifa_status indexed_tables_len(IndexedState &S, const std::vector<uint32_t> &qlen,
                               const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,
                               uint32_t wmax, const ifa_config &cfg, cudaStream_t st, std::string &err) {
-    enum : size_t { kWords, kEmh, kEnts, kFirst, kKeys, kPv, kSums, kExWords, kExMeta, kExIds, kTab0 };
+    enum : size_t { kWords, kEmh, kEnts, kFirst, kKeys, kPv, kSums, kExWords, kExMeta, kExIds, kMeta, kTab0 };
     S.free_tables();
     S.wmax = wmax;
     S.step = cfg.kmer_step;
@@ -332,6 +332,8 @@ ifa_status indexed_tables_len(IndexedState &S, const std::vector<uint32_t> &qlen
     if (!ks.empty()) {
         const uint4 *d_words = static_cast<const uint4 *>(S.bufs.get(kWords, qwords.size() * sizeof(uint4), e));
         put(const_cast<uint4 *>(d_words), qwords.data(), qwords.size() * sizeof(uint4));
+        uint32_t *d_meta = static_cast<uint32_t *>(S.bufs.get(kMeta, qmeta.size() * sizeof(uint32_t), e));
+        put(d_meta, qmeta.data(), qmeta.size() * sizeof(uint32_t));
         S.targ.n = static_cast<uint32_t>(ks.size());
         for (size_t ti = 0; ti < ks.size() && e == cudaSuccess; ti++) {
             const uint32_t k = ks[ti];
@@ -363,14 +365,14 @@ ifa_status indexed_tables_len(IndexedState &S, const std::vector<uint32_t> &qlen
                                       : static_cast<uint32_t *>(S.bufs.get(kTab0 + 4 * ti + 1, nbw * sizeof(uint32_t), e));
             uint32_t *d_rank = direct ? nullptr
                                       : static_cast<uint32_t *>(S.bufs.get(kTab0 + 4 * ti + 2, nbw * sizeof(uint32_t), e));
-            uint32_t *d_post = static_cast<uint32_t *>(
-                S.bufs.get(kTab0 + 4 * ti + 3, std::max<size_t>(np, 1) * sizeof(uint32_t), e));
+            uint2 *d_post = static_cast<uint2 *>(S.bufs.get(kTab0 + 4 * ti + 3, std::max<size_t>(np, 1) * sizeof(uint2), e));
             put(d_ents, ents.data(), ents.size() * sizeof(uint32_t));
             put(d_first, first.data(), first.size() * sizeof(uint32_t));
             if (e == cudaSuccess)
                 ck(launch_postings(d_words, wmax, d_ents, d_first, static_cast<uint32_t>(ents.size()), k, care,
                                    cfg.kmer_step, d_keys, d_pv, st));
-            if (e == cudaSuccess) ck(build_table(k, direct, d_keys, d_pv, np, d_off, d_bits, d_rank, d_post, d_sums, st));
+            if (e == cudaSuccess)
+                ck(build_table(k, direct, d_keys, d_pv, d_meta, np, d_off, d_bits, d_rank, d_post, d_sums, st));
             KTableDev &T = S.targ.t[ti];
             T.k = k;
             T.care = care;

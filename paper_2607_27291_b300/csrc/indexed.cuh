@@ -26,7 +26,7 @@ struct KTableDev {
     const uint32_t *off;   // direct: 4^k + 1 words; ranked: present keys + 1
     const uint32_t *rank;  // ranked: keys present before each bitmap word
     const uint32_t *bits;  // ranked: presence bitmap of 4^k bits
-    const uint32_t *post;  // postings grouped by key
+    const uint2 *post;     // postings grouped by key: {entry << 8 | offset, the entry's meta word}
 };
 
 struct KTablesArg {
@@ -111,8 +111,8 @@ cudaError_t device_scan(const uint32_t *in, uint32_t *out, uint64_t n, bool popc
 cudaError_t launch_postings(const uint4 *words, uint32_t wmax, const uint32_t *ents, const uint32_t *first,
                             uint32_t nents, uint32_t k, uint32_t care, uint32_t step, uint32_t *keys,
                             uint32_t *pv, cudaStream_t st);
-cudaError_t build_table(uint32_t k, bool direct, uint32_t *keys, const uint32_t *pv, uint32_t np, uint32_t *off,
-                        uint32_t *bits, uint32_t *rank, uint32_t *post, uint32_t *sums, cudaStream_t st);
+cudaError_t build_table(uint32_t k, bool direct, uint32_t *keys, const uint32_t *pv, const uint32_t *meta, uint32_t np,
+                        uint32_t *off, uint32_t *bits, uint32_t *rank, uint2 *post, uint32_t *sums, cudaStream_t st);
 
 ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
                            const std::vector<uint32_t> &qmeta, const std::vector<uint4> &qwords,

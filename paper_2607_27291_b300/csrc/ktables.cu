@@ -155,10 +155,13 @@ __global__ void k_count(const uint32_t *__restrict__ keys, uint32_t np, uint32_t
     if (i < np) atomicAdd(off + keys[i] + 2, 1u);
 }
 
-__global__ void k_place(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ pv, uint32_t np,
-                        uint32_t *__restrict__ off, uint32_t *__restrict__ post) {
+// Each posting carries its entry's meta word, so verification reads no
+// second random word per candidate.
+__global__ void k_place(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ pv,
+                        const uint32_t *__restrict__ meta, uint32_t np, uint32_t *__restrict__ off,
+                        uint2 *__restrict__ post) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < np) post[atomicSub(off + keys[i] + 2, 1u) - 1u] = pv[i];
+    if (i < np) post[atomicSub(off + keys[i] + 2, 1u) - 1u] = make_uint2(pv[i], meta[pv[i] >> 8]);
 }
 
 __global__ void k_set_bits(const uint32_t *__restrict__ keys, uint32_t np, uint32_t *__restrict__ bits) {
@@ -206,12 +209,13 @@ cudaError_t launch_postings(const uint4 *words, uint32_t wmax, const uint32_t *e
     return cudaGetLastError();
 }
 
-// Offsets and postings of one table from np (key, posting) pairs.
+// Offsets and postings of one table from np (key, posting) pairs; meta:
+// the query table's meta words, copied into each posting.
 // off: 4^k + 3 words (direct) or np + 3 words (ranked); bits and rank:
 // 4^k / 32 words each (ranked only); sums: device_scan_sums_words(largest
 // scanned length) words.  Lookups then read offsets from off + 2.
-cudaError_t build_table(uint32_t k, bool direct, uint32_t *keys, const uint32_t *pv, uint32_t np, uint32_t *off,
-                        uint32_t *bits, uint32_t *rank, uint32_t *post, uint32_t *sums, cudaStream_t st) {
+cudaError_t build_table(uint32_t k, bool direct, uint32_t *keys, const uint32_t *pv, const uint32_t *meta, uint32_t np,
+                        uint32_t *off, uint32_t *bits, uint32_t *rank, uint2 *post, uint32_t *sums, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     const uint64_t nkeys = 1ull << (2 * k);
     uint64_t noff;
@@ -228,7 +232,7 @@ cudaError_t build_table(uint32_t k, bool direct, uint32_t *keys, const uint32_t 
     if (e == cudaSuccess) e = cudaMemsetAsync(off, 0, noff * sizeof(uint32_t), st);
     if (e == cudaSuccess && np) k_count<<<grid_for(np, 256), 256, 0, st>>>(keys, np, off);
     if (e == cudaSuccess) e = device_scan(off, off, noff, false, false, sums, st);
-    if (e == cudaSuccess && np) k_place<<<grid_for(np, 256), 256, 0, st>>>(keys, pv, np, off, post);
+    if (e == cudaSuccess && np) k_place<<<grid_for(np, 256), 256, 0, st>>>(keys, pv, meta, np, off, post);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e;
 }

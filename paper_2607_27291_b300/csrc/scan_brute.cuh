@@ -312,7 +312,7 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
                                            const uint32_t *hw, const uint32_t *lw, const uint32_t *mul,
                                            const uint2 *R, uint32_t e0, uint32_t blk, uint32_t lane,
                                            uint32_t s, const HitSink &sink, WH &wh, uint16_t (*cq)[32],
-                                           uint32_t &qn) {
+                                           uint32_t &qn, bool &queued) {
     constexpr uint32_t kHigh = 0x80808080u;
     constexpr uint32_t cls = MASKED ? kQClassM : 0u;
     uint32_t k = 0;
@@ -327,6 +327,7 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
             if (__any_sync(0xffffffffu, (acc & kHigh) != kHigh)) {
                 // queue the lane's passing entries; drain while a column
                 // could not take another group
+                queued = true;   // warp-uniform: the block ends with a drain
 #pragma unroll
                 for (int i = 0; i < kGroup; i++)
                     if ((v[i] & kHigh) != kHigh) cq[qn++][lane] = static_cast<uint16_t>((k + i) | cls);
@@ -359,6 +360,7 @@ __device__ __forceinline__ void scan_class(const Batch &b, const QueryTable &qt,
         const uint32_t v = packed_counts<MASKED>(q, hw, lw, mul);
         if (__any_sync(0xffffffffu, (v & kHigh) != kHigh)) {
             if constexpr (kQDepth > 0) {
+                queued = true;
                 if ((v & kHigh) != kHigh) cq[qn++][lane] = static_cast<uint16_t>(k | cls);
                 if (__any_sync(0xffffffffu, qn > static_cast<uint32_t>(kQDepth - kGroup)))
                     drain_queue<WMAX>(b, qt, m, cq, qn, hw, lw, mul, R, e0, blk, lane, s, sink, wh);
@@ -524,12 +526,14 @@ __device__ __forceinline__ void scan_blocks(const Batch &b, const QueryTable &qt
             lw[k] = __funnelshift_r(R[k].y, R[k + 1].y, lane);
         }
         const uint32_t bi = static_cast<uint32_t>(blk);
-        uint32_t qn = 0;  // this lane's queued candidates
-        scan_class<WMAX, false>(b, qt, m, m.sF, m.fidx, nF, hw, lw, mul, R, e0, bi, lane, s, sink, wh, cq, qn);
-        scan_class<WMAX, true>(b, qt, m, m.sM, m.midx, nM, hw, lw, mul, R, e0, bi, lane, s, sink, wh, cq, qn);
+        uint32_t qn = 0;       // this lane's queued candidates
+        bool queued = false;   // some group fired in this block (warp-uniform)
+        scan_class<WMAX, false>(b, qt, m, m.sF, m.fidx, nF, hw, lw, mul, R, e0, bi, lane, s, sink, wh, cq, qn,
+                                queued);
+        scan_class<WMAX, true>(b, qt, m, m.sM, m.midx, nM, hw, lw, mul, R, e0, bi, lane, s, sink, wh, cq, qn,
+                               queued);
         if constexpr (kQDepth > 0) {
-            if (__any_sync(0xffffffffu, qn != 0u))
-                drain_queue<WMAX>(b, qt, m, cq, qn, hw, lw, mul, R, e0, bi, lane, s, sink, wh);
+            if (queued) drain_queue<WMAX>(b, qt, m, cq, qn, hw, lw, mul, R, e0, bi, lane, s, sink, wh);
         }
         __syncwarp();
     }

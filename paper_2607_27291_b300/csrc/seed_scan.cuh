@@ -75,9 +75,24 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                 uint32_t id = 0, contig = 0, pos = 0, mm = 0;
                 if (f < total) {
                     const uint64_t j = (blk << 5) + own;
-                    const uint32_t pv = __ldg(T.post + own_beg + (f - own_exc));
-                    const uint32_t e = pv >> 8, o = pv & 0xffu;
-                    const uint32_t meta = __ldg(qt.meta + e);
+                    const uint2 pm = __ldg(T.post + own_beg + (f - own_exc));   // posting and entry meta
+                    const uint32_t e = pm.x >> 8, o = pm.x & 0xffu;
+                    const uint32_t meta = pm.y;
+                    // Issued together, since none depends on another: the
+                    // entry's first word, and the directory entries and first
+                    // two hi/lo words of the window the posting names.  The
+                    // window starts at or before position j, so these reads
+                    // stay in the batch (checked builds: an out-of-range
+                    // directory entry reads as all special, and ref_word
+                    // checks the words).
+                    const uint64_t wa = (o <= j ? j - o : j) >> 5;
+                    const uint4 q0 = __ldg(qt.words + static_cast<size_t>(e) * WMAX);
+                    const bool dok = in_range(b, kBoundsDir, (wa >> 5) + 1, b.ndir);
+                    const uint2 d0 = dok ? __ldg(b.dir + (wa >> 5)) : make_uint2(0xffffffffu, 0u);
+                    const uint2 d1 = dok ? __ldg(b.dir + (wa >> 5) + 1) : make_uint2(0xffffffffu, 0u);
+                    const bool hok = in_range(b, kBoundsWord, wa + 1, b.nwords);
+                    const uint2 ha = hok ? __ldg(b.hl + wa) : make_uint2(0u, 0u);
+                    const uint2 hb = hok ? __ldg(b.hl + wa + 1) : make_uint2(0u, 0u);
                     const uint32_t L = meta_L(meta), W = meta_W(meta);
                     const uint32_t se = entry_s(meta, s);
                     if (o <= j) {
@@ -92,19 +107,8 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                             // the window's words w0 .. w0 + W: hi/lo words, and
                             // the N / piece-start masks only when the directory
                             // marks one of them special
-                            // (checked builds: an out-of-range entry reads as all special,
-                            // and ref_word checks the words)
-                            const bool dok = in_range(b, kBoundsDir, (w0 >> 5) + 1, b.ndir);
-                            const uint2 d0 = dok ? __ldg(b.dir + (w0 >> 5)) : make_uint2(0xffffffffu, 0u);
-                            const uint2 d1 = dok ? __ldg(b.dir + (w0 >> 5) + 1) : make_uint2(0xffffffffu, 0u);
-                            const bool spec = special_bits(d0.x, d1.x, w0, W + 1) != 0u;
-                            uint4 cur;
-                            if (spec) {
-                                cur = ref_word(b, w0);
-                            } else {
-                                const uint2 h0 = __ldg(b.hl + w0);
-                                cur = make_uint4(h0.x, h0.y, 0u, 0u);
-                            }
+                            const bool spec = !hok || special_bits(d0.x, d1.x, w0, W + 1) != 0u;
+                            uint4 cur = spec ? ref_word(b, w0) : make_uint4(ha.x, ha.y, 0u, 0u);
 #pragma unroll
                             for (int w = 0; w < WMAX; w++) {
                                 x[w] = 0;
@@ -112,6 +116,8 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                                     uint4 nx;
                                     if (spec) {
                                         nx = ref_word(b, w0 + w + 1);
+                                    } else if (w == 0) {
+                                        nx = make_uint4(hb.x, hb.y, 0u, 0u);
                                     } else {
                                         const uint2 h2 = __ldg(b.hl + w0 + w + 1);
                                         nx = make_uint4(h2.x, h2.y, 0u, 0u);
@@ -121,7 +127,7 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                                     const uint32_t rn = __funnelshift_r(cur.z, nx.z, sh);
                                     uint32_t rb = __funnelshift_r(cur.w, nx.w, sh);
                                     if (w == 0) rb &= ~1u;
-                                    const uint4 q = __ldg(qt.words + static_cast<size_t>(e) * WMAX + w);
+                                    const uint4 q = w == 0 ? q0 : __ldg(qt.words + static_cast<size_t>(e) * WMAX + w);
                                     x[w] = ((rh ^ q.x) | (rl ^ q.y) | rn) & q.w;
                                     mm += __popc(x[w]);
                                     bnd |= rb & q.w;
@@ -137,9 +143,25 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
 #pragma unroll
                                 for (int w = 0; w < WMAX; w++) {
                                     if (w < static_cast<int>(W) && static_cast<uint32_t>(w) * 32 <= last) {
+                                        // c bit i: a mismatch among the k-mer's cared
+                                        // positions starting at offset base + i
                                         uint32_t c = 0;
-                                        for (uint32_t i = 0; i < k; i++)
-                                            if ((T.care >> i) & 1u) c |= __funnelshift_r(x[w], x[w + 1], i);
+                                        if (T.care == full) {
+                                            // OR of the k shifts by doubling: after the loop
+                                            // the shifts [0, span) are in; one more shift by
+                                            // k - span <= span adds [k - span, k)
+                                            uint64_t cc = x[w] | (static_cast<uint64_t>(x[w + 1]) << 32);
+                                            uint32_t span = 1;
+                                            while (2 * span <= k) {
+                                                cc |= cc >> span;
+                                                span *= 2;
+                                            }
+                                            if (span < k) cc |= cc >> (k - span);
+                                            c = static_cast<uint32_t>(cc);
+                                        } else {
+                                            for (uint32_t i = 0; i < k; i++)
+                                                if ((T.care >> i) & 1u) c |= __funnelshift_r(x[w], x[w + 1], i);
+                                        }
                                         uint32_t valid = 0xffffffffu;
                                         const uint32_t base = static_cast<uint32_t>(w) * 32;
                                         if (last - base < 31) valid = (2u << (last - base)) - 1u;
