@@ -250,7 +250,7 @@ ifa_status rates_on_random(ifa_handle *h, const std::vector<std::string> &qs, co
     RefBufs R;
     cudaError_t e = sc.get(d_ascii, kCalibBases);
     if (e == cudaSuccess) e = sc.get(d_piece, 1);
-    if (e == cudaSuccess) e = refbufs_alloc(R, nwords, nwords, nwords);
+    if (e == cudaSuccess) e = refbufs_alloc(R, nwords, 0, nwords);
     const DevPiece piece{0, 0, 0, 1};
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_piece, &piece, sizeof(piece), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {

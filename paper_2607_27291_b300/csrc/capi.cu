@@ -410,7 +410,7 @@ ifa_status ifa_create(const ifa_config *cfg, ifa_handle **out) {
     h->stream = h->own_stream;
     const uint64_t sb = cfg->segment_bytes;
     const uint64_t words = (sb + kHaloCap + 31) / 32 + kWordPad;
-    CKC(refbufs_alloc(h->ref, words, words, words));
+    CKC(refbufs_alloc(h->ref, words, 0, words));   // streamed batches pack with no mask scratch
     for (int i = 0; i < 2; i++) {
         CKC(cudaMalloc(&h->d_seg[i], sb));
         CKC(cudaMalloc(&h->d_halo[i], kHaloCap));

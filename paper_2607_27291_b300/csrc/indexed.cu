@@ -36,9 +36,14 @@ namespace {
 
 constexpr int kSeedThreads = 256;
 constexpr int kSeedWarps = kSeedThreads / kWarp;
+// Resident CTAs per SM the register allocation is held to: the scan waits
+// on chains of dependent L2 reads, so more resident warps hide more of them.
+#ifndef IFA_SEED_MIN_CTAS
+#define IFA_SEED_MIN_CTAS 4
+#endif
 
 template <int WMAX>
-__global__ void __launch_bounds__(kSeedThreads)
+__global__ void __launch_bounds__(kSeedThreads, IFA_SEED_MIN_CTAS)
 k_seed_scan(Batch b, QueryTable qt, KTablesArg tabs, const uint32_t *__restrict__ entry_minhits,
             uint32_t step, uint32_t s, HitSink sink, unsigned long long *candidates) {
     __shared__ __align__(16) ifa_hit wbuf[kSeedWarps][32];

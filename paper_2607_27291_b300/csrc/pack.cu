@@ -8,10 +8,13 @@
 // continues from the previous segment) followed by the new segment, which
 // therefore starts on a word boundary and is read with aligned vectors.
 //
-// Three steps: k_pack writes the hi/lo words and every word's N mask into a
-// scratch array; k_mark_pieces adds the piece-start (B) bits there;
-// k_build_dir turns the scratch into the directory (one bitmap per 32 words)
-// and the exception entries of the special words (see ifa_internal.cuh).
+// Appends to the resident store take three steps: k_pack writes the hi/lo
+// words and every word's N mask into a scratch array; k_mark_pieces adds
+// the piece-start (B) bits there; k_build_dir turns the scratch into the
+// directory (one bitmap per 32 words) and the exception entries of the
+// special words (see ifa_internal.cuh), continuing a partly filled group.
+// Streamed batches, which always start at word 0, take one fused pass,
+// k_pack_dir, with no scratch.
 #include "ifa_internal.cuh"
 
 namespace ifa {
@@ -141,6 +144,103 @@ k_build_dir(const uint2 *__restrict__ nb, uint64_t w0, uint64_t n, uint2 *__rest
     if (lane == 0) dir[g] = make_uint2(bits, static_cast<uint32_t>(base));
 }
 
+// The first of the n pieces (sorted by start) that starts at or after base
+// x, or n; all lanes of a warp call it and get the answer.  A 32-way
+// search: each round probes 32 evenly spaced pieces of the range [lo, hi)
+// that holds the answer, and the probes below x (a prefix of the lanes)
+// narrow it to one gap between probes; three rounds cover 40,000 pieces.
+__device__ __forceinline__ uint32_t first_piece_at(const DevPiece *__restrict__ pc, uint32_t n, uint64_t x,
+                                                   uint32_t lane) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 32u) {
+        const uint32_t step = (hi - lo + 31u) / 32u;
+        const uint32_t i = lo + lane * step;
+        const bool below = i < hi && pc[i].start < x;
+        const uint32_t c = __popc(__ballot_sync(0xffffffffu, below));
+        const uint32_t nlo = c ? lo + (c - 1u) * step + 1u : lo;
+        hi = min(hi, lo + c * step);
+        lo = nlo;
+    }
+    const uint32_t i = lo + lane;
+    const bool below = i < hi && pc[i].start < x;
+    return lo + __popc(__ballot_sync(0xffffffffu, below));
+}
+
+// Streamed batches in one pass: k_pack's words, the piece-start bits and
+// k_build_dir's directory, with no mask scratch.  Thread w packs word w; a
+// warp is the directory group of its 32 words (256-thread blocks start on
+// group boundaries).  The warp finds the group's first piece start
+// (first_piece_at) and walks the piece starts inside the group.  The grid
+// covers one group past the words' last one, written as an empty entry
+// (see k_build_dir).  exc holds at least nwords entries, so the claims
+// cannot run out; a claim past exc_cap sets exc_n[1] like k_build_dir.
+template <bool ALIGNED>
+__global__ void __launch_bounds__(kPackThreads)
+k_pack_dir(const uint8_t *__restrict__ halo, uint32_t hlen, uint32_t H, const uint8_t *__restrict__ seg,
+           uint64_t slen, uint2 *__restrict__ hl, uint64_t nwords, const DevPiece *__restrict__ pc, uint32_t npieces,
+           bool mark, uint2 *__restrict__ dir, uint2 *__restrict__ exc, uint64_t exc_cap,
+           unsigned long long *__restrict__ exc_n) {
+    const uint64_t w = static_cast<uint64_t>(blockIdx.x) * kPackThreads + threadIdx.x;
+    const uint64_t g = w >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    if (g > ((nwords - 1) >> 5) + 1) return;  // whole warps
+    uint32_t hi = 0, lo = 0, nn = 0, bb = 0;
+    const bool live = w < nwords;
+    if (live) {
+        const uint64_t hw = H >> 5;
+        if (w < hw) {
+            const uint32_t pad = H - hlen;
+            for (uint32_t b = 0; b < 32; b++) {
+                const uint32_t i = static_cast<uint32_t>(w) * 32 + b;
+                pack_byte(i < pad ? 'N' : halo[i - pad], b, hi, lo, nn);
+            }
+        } else {
+            const uint64_t o = (w - hw) * 32;
+            if (ALIGNED && o + 32 <= slen) {
+                const uint4 *v = reinterpret_cast<const uint4 *>(seg + o);
+                const uint4 a = __ldg(v), c = __ldg(v + 1);
+                const uint32_t u[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    uint32_t h4, l4, n4;
+                    pack4(u[j], h4, l4, n4);
+                    hi |= h4 << (4 * j);
+                    lo |= l4 << (4 * j);
+                    nn |= n4 << (4 * j);
+                }
+                hi &= ~nn;
+                lo &= ~nn;
+            } else {
+                for (uint32_t b = 0; b < 32; b++)
+                    pack_byte(o + b < slen ? seg[o + b] : 'N', b, hi, lo, nn);
+            }
+        }
+        hl[w] = make_uint2(hi, lo);
+    }
+    if (mark && npieces) {
+        const uint64_t gs = g << 10, ge = gs + 1024;
+        const uint32_t first = first_piece_at(pc, npieces, gs, lane);
+        for (uint32_t i = first; i < npieces; i++) {
+            const uint64_t p = pc[i].start;   // warp-uniform
+            if (p >= ge) break;
+            if (p != 0 && (p >> 5) == w) bb |= 1u << (p & 31);
+        }
+        if (!live) bb = 0;
+    }
+    const bool special = (nn | bb) != 0u;
+    const uint32_t bits = __ballot_sync(0xffffffffu, special);
+    const uint32_t cnt = __popc(bits);
+    unsigned long long base = 0;
+    if (lane == 0 && cnt) base = atomicAdd(exc_n, static_cast<unsigned long long>(cnt));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base + cnt > exc_cap) {
+        if (lane == 0) exc_n[1] = 1ull;
+        return;
+    }
+    if (special) exc[base + __popc(bits & ((1u << lane) - 1u))] = make_uint2(nn, bb);
+    if (lane == 0) dir[g] = make_uint2(bits, static_cast<uint32_t>(base));
+}
+
 __global__ void k_halo_update(const uint8_t *__restrict__ old_halo, uint32_t old_len,
                               const uint8_t *__restrict__ seg, uint64_t slen, uint32_t new_len,
                               uint8_t *__restrict__ new_halo) {
@@ -213,14 +313,20 @@ void refbufs_free(RefBufs &R) {
 cudaError_t pack_batch(const RefBufs &R, const uint8_t *halo, uint32_t hlen, uint32_t H, const uint8_t *seg,
                        uint64_t slen, uint64_t nwords, const DevPiece *pieces, uint32_t npieces, bool mark,
                        cudaStream_t st, int *launches) {
-    if (nwords > R.words_cap || nwords > R.nb_cap || nwords > R.exc_cap) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(R.exc_n, 0, 2 * sizeof(unsigned long long), st);
-    if (e == cudaSuccess) e = launch_pack(halo, hlen, H, seg, slen, R.hl, R.nb, nwords, st);
-    if (e == cudaSuccess && mark) e = launch_mark_pieces(pieces, npieces, 0, nwords, R.nb, st);
     // every word takes at most one entry, so exc (nwords entries) cannot run out
-    if (e == cudaSuccess) e = launch_build_dir(R.nb, 0, nwords, R.dir, R.exc, R.exc_cap, R.exc_n, st);
-    if (launches) *launches += mark ? 3 : 2;
-    return e;
+    if (nwords == 0 || nwords > R.words_cap || nwords > R.exc_cap) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(R.exc_n, 0, 2 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const uint64_t threads = ((((nwords - 1) >> 5) + 2) << 5);   // one group past the last word's
+    const unsigned grid = static_cast<unsigned>((threads + kPackThreads - 1) / kPackThreads);
+    if ((reinterpret_cast<uintptr_t>(seg) & 15u) == 0)
+        k_pack_dir<true><<<grid, kPackThreads, 0, st>>>(halo, hlen, H, seg, slen, R.hl, nwords, pieces, npieces, mark,
+                                                        R.dir, R.exc, R.exc_cap, R.exc_n);
+    else
+        k_pack_dir<false><<<grid, kPackThreads, 0, st>>>(halo, hlen, H, seg, slen, R.hl, nwords, pieces, npieces,
+                                                         mark, R.dir, R.exc, R.exc_cap, R.exc_n);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
 }
 
 Batch make_batch(const RefBufs &R, uint64_t nbases, uint32_t halo, const DevPiece *pieces, uint32_t npieces) {
