@@ -38,8 +38,11 @@ constexpr int kSeedThreads = 256;
 constexpr int kSeedWarps = kSeedThreads / kWarp;
 // Resident CTAs per SM the register allocation is held to: the scan waits
 // on chains of dependent L2 reads, so more resident warps hide more of them.
+// Measured on B300 (1 Gbp, 10,000 queries, maxSubs 4 / 8 / 16): 4 CTAs
+// (64 registers) 59.5 / 85.0 / 149.6 ms; 5 (48, a few spilled words)
+// 59.2 / 81.9 / 146.5 ms; 6 (40) 59.7 / 81.3 / 148.9 ms.
 #ifndef IFA_SEED_MIN_CTAS
-#define IFA_SEED_MIN_CTAS 4
+#define IFA_SEED_MIN_CTAS 5
 #endif
 
 template <int WMAX>
