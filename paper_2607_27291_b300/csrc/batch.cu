@@ -38,6 +38,13 @@ namespace {
 
 constexpr int kBThreads = 256;
 constexpr int kBWarps = kBThreads / kWarp;
+// Resident CTAs per SM the persistent kernel's registers are held to.
+// Measured on B300 (128 sets vs 5 Gbp, persistent launch): no bound
+// (64 registers, 124 bytes spilled) 3.96 s; 4 CTAs (64 registers, 16-32
+// bytes spilled) 3.76 s; 3 CTAs (80 registers, none spilled) 4.21 s.
+#ifndef IFA_BATCH_MIN_CTAS
+#define IFA_BATCH_MIN_CTAS 4
+#endif
 constexpr uint64_t kStorePad = 16;  // padding words after the last packed word (packed as N)
 
 ifa_status bfail(ifa_handle *h, ifa_status st, const std::string &msg) {
@@ -58,7 +65,7 @@ ifa_status bfail(ifa_handle *h, ifa_status st, const std::string &msg) {
 // (chunk, tile) items in chunk-major order, so a CTA reloads its shared
 // query chunk rarely.
 template <int WMAX, bool MULTI>
-__global__ void __launch_bounds__(kBThreads)
+__global__ void __launch_bounds__(kBThreads, IFA_BATCH_MIN_CTAS)
 k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
     using namespace brute;
     extern __shared__ uint4 smem4[];
