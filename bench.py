@@ -529,7 +529,8 @@ def run_ours(args, rank, world):
                 P.ifa_prime_halo(h, halo[0], halo[1], ref_pin[halo[2] - off:halo[3] - off])
             got, over_any = 0, False
             for a, b, pc in segs:
-                P.ifa_push_segment(h, ref_pin[a - off:b - off], pc)
+                # the pinned reference stays unchanged: no wait for each copy
+                P.ifa_push_segment(h, ref_pin[a - off:b - off], pc, P.IFA_MEM_HOST_PINNED_ASYNC)
                 n, over, _ = P.ifa_poll_hits(h, out[got:])
                 got += n
                 over_any |= over

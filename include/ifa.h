@@ -70,9 +70,14 @@ typedef enum {
 } ifa_brute_kernel;
 
 typedef enum {
-    IFA_MEM_HOST = 0,         /* pageable host memory: copied through pinned staging */
-    IFA_MEM_HOST_PINNED = 1,  /* page-locked host memory: DMA'd directly */
-    IFA_MEM_DEVICE = 2        /* device memory on the handle's device */
+    IFA_MEM_HOST = 0,               /* pageable host memory: copied through pinned staging */
+    IFA_MEM_HOST_PINNED = 1,        /* page-locked host memory: DMA'd directly */
+    IFA_MEM_DEVICE = 2,             /* device memory on the handle's device */
+    IFA_MEM_HOST_PINNED_ASYNC = 3   /* page-locked host memory, DMA'd directly; ifa_push_segment and
+                                       ifa_prime_halo return once the copy is enqueued, so the next
+                                       segment's copy follows with no host round trip: the buffer must
+                                       stay unchanged until ifa_flush (or a drain) returns.  Store
+                                       appends treat it as IFA_MEM_HOST_PINNED. */
 } ifa_mem;
 
 /* One reported alignment (16 bytes). */
@@ -204,7 +209,8 @@ ifa_status ifa_set_mode(ifa_handle *h, ifa_mode mode);
  * segment's last bases.
  * IFA_MEM_HOST / IFA_MEM_HOST_PINNED: returns once the bytes are on the
  * device (the caller may then reuse its buffer); the scan continues
- * asynchronously.  IFA_MEM_DEVICE: the buffer must stay unchanged until
+ * asynchronously.  IFA_MEM_DEVICE and IFA_MEM_HOST_PINNED_ASYNC: returns
+ * once the work is enqueued; the buffer must stay unchanged until
  * ifa_flush() returns.
  * Errors: INVALID_ARG (len > segment_bytes, bad piece table, contig order),
  * BAD_STATE (no queries), CUDA. */

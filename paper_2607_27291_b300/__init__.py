@@ -27,7 +27,7 @@ IFA_ERR_HIT_OVERFLOW = 5
 IFA_ERR_TIMEOUT = 6
 
 IFA_MODE_AUTO, IFA_MODE_BRUTE, IFA_MODE_INDEXED = 0, 1, 2
-IFA_MEM_HOST, IFA_MEM_HOST_PINNED, IFA_MEM_DEVICE = 0, 1, 2
+IFA_MEM_HOST, IFA_MEM_HOST_PINNED, IFA_MEM_DEVICE, IFA_MEM_HOST_PINNED_ASYNC = 0, 1, 2, 3
 IFA_BRUTE_AUTO, IFA_BRUTE_POPC, IFA_BRUTE_TENSOR = 0, 1, 2
 IFA_MAX_QUERY_LEN = 255
 

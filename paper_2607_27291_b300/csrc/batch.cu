@@ -539,7 +539,8 @@ ifa_status ifa_ref_append(ifa_handle *h, const uint8_t *ascii, uint64_t len, con
     if (len == 0 && n == 0) return IFA_OK;
     if (!ascii || !pieces || len == 0 || n == 0)
         return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: bytes and at least one piece needed");
-    if (mem != IFA_MEM_HOST && mem != IFA_MEM_HOST_PINNED && mem != IFA_MEM_DEVICE)
+    if (mem != IFA_MEM_HOST && mem != IFA_MEM_HOST_PINNED && mem != IFA_MEM_DEVICE &&
+        mem != IFA_MEM_HOST_PINNED_ASYNC)
         return bfail(h, IFA_ERR_INVALID_ARG, "ifa_ref_append: unknown memory kind");
     BatchState &B = h->batch;
     if (B.nbases % 32 != 0)

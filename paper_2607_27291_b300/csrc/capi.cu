@@ -540,7 +540,8 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
         return fail(h, IFA_ERR_INVALID_ARG, "a segment needs bytes and at least one piece");
     if (len > h->cfg.segment_bytes) return fail(h, IFA_ERR_INVALID_ARG, "segment longer than segment_bytes");
     const NvtxRange nvtx("ifa_push_segment");
-    if (mem != IFA_MEM_HOST && mem != IFA_MEM_HOST_PINNED && mem != IFA_MEM_DEVICE)
+    if (mem != IFA_MEM_HOST && mem != IFA_MEM_HOST_PINNED && mem != IFA_MEM_DEVICE &&
+        mem != IFA_MEM_HOST_PINNED_ASYNC)
         return fail(h, IFA_ERR_INVALID_ARG, "unknown memory kind");
     if (h->qs.empty()) return fail(h, IFA_ERR_BAD_STATE, "no queries loaded");
     // piece table checks
@@ -602,7 +603,7 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
         CK(h, cudaMemcpyAsync(h->d_seg[slot], h->h_stage[slot], len, cudaMemcpyHostToDevice, h->copy_stream));
         dsrc = h->d_seg[slot];
         h->stats.h2d_bytes += len;
-    } else if (mem == IFA_MEM_HOST_PINNED) {
+    } else if (mem == IFA_MEM_HOST_PINNED || mem == IFA_MEM_HOST_PINNED_ASYNC) {
         CK(h, cudaMemcpyAsync(h->d_seg[slot], ascii, len, cudaMemcpyHostToDevice, h->copy_stream));
         dsrc = h->d_seg[slot];
         h->stats.h2d_bytes += len;
@@ -694,7 +695,7 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
     }
     CK(h, cudaEventRecord(h->ev_consumed[slot], h->stream));
     h->slot_used[slot] = true;
-    if (mem == IFA_MEM_HOST_PINNED) CK(h, cudaEventSynchronize(h->ev_copied[slot]));
+    if (mem == IFA_MEM_HOST_PINNED) CK(h, cudaEventSynchronize(h->ev_copied[slot]));  // the caller may reuse it
 
     // nominal work counters: windows owned by this batch
     h->stats.segments++;
@@ -721,7 +722,8 @@ ifa_status ifa_prime_halo(ifa_handle *h, uint32_t contig, uint64_t offset_in_con
                           uint64_t len, ifa_mem mem) {
     if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
     if (len == 0 || !ascii) return fail(h, IFA_ERR_INVALID_ARG, "the halo needs at least one base");
-    if (mem != IFA_MEM_HOST && mem != IFA_MEM_HOST_PINNED && mem != IFA_MEM_DEVICE)
+    if (mem != IFA_MEM_HOST && mem != IFA_MEM_HOST_PINNED && mem != IFA_MEM_DEVICE &&
+        mem != IFA_MEM_HOST_PINNED_ASYNC)
         return fail(h, IFA_ERR_INVALID_ARG, "unknown memory kind");
     if (h->qs.empty()) return fail(h, IFA_ERR_BAD_STATE, "no queries loaded");
     if (h->open) return fail(h, IFA_ERR_BAD_STATE, "a contig is still open; the halo must come first");
@@ -742,7 +744,7 @@ ifa_status ifa_prime_halo(ifa_handle *h, uint32_t contig, uint64_t offset_in_con
     h->any_contig = true;
     h->last_contig = contig;
     h->pushed = true;
-    if (mem != IFA_MEM_DEVICE) CK(h, cudaStreamSynchronize(h->stream));
+    if (mem != IFA_MEM_DEVICE && mem != IFA_MEM_HOST_PINNED_ASYNC) CK(h, cudaStreamSynchronize(h->stream));
     return IFA_OK;
 }
 

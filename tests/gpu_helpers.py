@@ -15,7 +15,7 @@ def to_mem(arr: np.ndarray, kind: str):
     t = torch.from_numpy(np.ascontiguousarray(arr))
     if kind == "device":
         return t.cuda()
-    if kind == "pinned":
+    if kind in ("pinned", "pinned_async"):
         return t.pin_memory()
     return np.ascontiguousarray(arr)
 
@@ -34,8 +34,8 @@ def gpu_scan(queries, ref, contig_len, max_subs, mode=P.IFA_MODE_BRUTE, seg_byte
         keep = []
         for a, b, pieces in P.segment_pieces(contig_len, seg, contig_ids):
             buf = to_mem(ref[a:b], mem)
-            keep.append(buf)
-            P.ifa_push_segment(h, buf, pieces)
+            keep.append(buf)   # (pinned_async: unchanged until the flush below)
+            P.ifa_push_segment(h, buf, pieces, P.IFA_MEM_HOST_PINNED_ASYNC if mem == "pinned_async" else None)
         P.ifa_flush(h)
         hits, over = P.ifa_drain_hits(h)
         dig, counts = P.ifa_get_digest(h, len(queries))

@@ -28,7 +28,7 @@ def test_small_matches_oracle(seed, s, seg_bytes):
     assert counts.tolist() == np.bincount(exp["query"], minlength=len(wl.queries)).tolist()
 
 
-@pytest.mark.parametrize("mem", ["host", "pinned", "device"])
+@pytest.mark.parametrize("mem", ["host", "pinned", "device", "pinned_async"])
 def test_memory_kinds_agree(mem):
     wl = synth.small_workload(seed=5, n_queries=4, n_contigs=20, cmax=5000)
     got, *_ = gpu_scan(wl.queries, wl.ref, wl.contig_len, 4, seg_bytes=3001, mem=mem)
