@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--slices", type=int, default=16, help="serving: slices per cycle")
     ap.add_argument("--no-solo", action="store_true", help="serving: skip the one-request-at-a-time baseline")
     ap.add_argument("--sizes", default="16,32,64,512,10000", help="brute-kernels: query-set sizes")
+    ap.add_argument("--subs", default="4", help="brute-kernels: maxSubs values")
     ap.add_argument("--solo-max-s", type=float, default=180.0,
                     help="serving: wall-time cap of the one-request-at-a-time baseline")
     ap.add_argument("--max-wall", type=float, default=float("inf"),
@@ -1042,13 +1043,21 @@ def run_brute_kernels(args):
     dev = torch.from_numpy(wl.ref).cuda()
     segs = list(P.segment_pieces(wl.contig_len, SEG))
     allq = synth.random_queries(max(sizes), 20, 40, 11)
+    import math
+
+    def window_hit_rate(qs, s):
+        # mean over queries of P(Binomial(L, 3/4) <= s): a uniform random window hits
+        p = [sum(math.comb(len(q), i) * 0.75 ** i * 0.25 ** (len(q) - i) for i in range(min(s, len(q)) + 1))
+             for q in qs]
+        return sum(p) / len(p)
+
     rows = []
-    for nq in sizes:
-        r = {"queries": nq}
+    for s_max, nq in [(int(x), n) for x in args.subs.split(",") for n in sizes]:
+        r = {"queries": nq, "max_subs": s_max, "mean_window_hit_rate": window_hit_rate(allq[:nq], s_max)}
         for kern, name in ((P.IFA_BRUTE_POPC, "popcount"), (P.IFA_BRUTE_TENSOR, "tensor")):
             h = P.ifa_create(count_only=1, segment_bytes=SEG, profile=1, brute_kernel=kern)
             P.ifa_load_queries(h, allq[:nq])
-            P.ifa_set_max_subs(h, 4)
+            P.ifa_set_max_subs(h, s_max)
             P.ifa_set_mode(h, P.IFA_MODE_BRUTE)
             best = None
             for rep in range(max(1, args.warmup) + args.steps):
@@ -1062,13 +1071,15 @@ def run_brute_kernels(args):
                     best = ms if best is None else min(best, ms)
             dg, _ = P.ifa_get_digest(h)
             P.ifa_destroy(h)
-            r[name] = {"ms": best, "evals_per_s": st["windows"] / (best * 1e-3), "digest": list(dg)}
+            r[name] = {"ms": best, "evals_per_s": st["windows"] / (best * 1e-3), "digest": list(dg),
+                       "hit_rate": dg[0] / max(1, st["windows"])}
         r["speedup"] = r["popcount"]["ms"] / r["tensor"]["ms"]
         r["same_digest"] = r["popcount"]["digest"] == r["tensor"]["digest"]
         rows.append(r)
     line = {"workload": "brute-kernels", "metric": "(query, strand, window) evaluations/s per brute-force kernel",
             "unit": "evaluations/s", "value": rows[-1]["tensor"]["evals_per_s"], "sizes": rows,
-            "config": {"reference_bases": int(wl.ref.size), "query_lengths": "20-40", "max_subs": 4,
+            "config": {"reference_bases": int(wl.ref.size), "query_lengths": "20-40",
+                       "max_subs": [int(x) for x in args.subs.split(",")],
                        "hits": "count only", "timing": "best of --steps passes, library CUDA events"},
             "data": "synthetic"}
     print(json.dumps(line), flush=True)
