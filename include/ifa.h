@@ -442,7 +442,7 @@ ifa_status ifa_serve_stop(ifa_handle *h);
  * fixed memory plan.  The caller passes every input and output buffer; the
  * library's own scratch (packed reference words, encoded queries, piece
  * table, per-query counts when per_query_counts_device is NULL) lives in one
- * file-scope device array of about 26 MB.  No call allocates device or
+ * file-scope device array of about 18 MB.  No call allocates device or
  * pinned memory itself (torch's allocator included).
  *
  * When that array takes device memory: the CUDA runtime loads the library's

@@ -269,7 +269,7 @@ cudaError_t launch_mark_pieces(const DevPiece *pieces, uint32_t n, uint64_t firs
 cudaError_t launch_build_dir(const uint2 *nb, uint64_t w0, uint64_t n, uint2 *dir, uint2 *exc, uint64_t exc_cap,
                              unsigned long long *exc_n, cudaStream_t st);
 // Directory entries a reference of `words` hi/lo words needs (its groups,
-// the group after the last that k_build_dir writes, and one more that a
+// the group after the last that k_build_dir and k_pack_dir write, and one more that a
 // reader of two neighbouring entries may touch).
 inline uint64_t dir_entries(uint64_t words) { return (words + 31) / 32 + 3; }
 // Allocate hl (words), nb (nb_words), dir and exc (exc_entries) and the

@@ -7,7 +7,7 @@
 // entry point that takes the caller's input and output buffers and keeps
 // all of its scratch -- the packed reference planes, the encoded query
 // table, the piece table and the per-query counts -- in a file-scope
-// device array of fixed size (about 26 MB).
+// device array of fixed size (about 18 MB).
 //
 // When the array takes its device memory: the array belongs to this file's
 // CUDA module, and the runtime loads a module into a context when it is
@@ -39,13 +39,12 @@ constexpr uint32_t kNaWmax = 8;                // words per query entry (255 bp)
 constexpr uint64_t kNaWords = kNaMaxBases / 32 + 16;
 
 // Byte offsets of the parts inside the scratch array (256-aligned each):
-// the packed reference (2-bit words, their mask scratch, directory,
-// exception entries and counter), the query table, the piece table and the
-// per-query counts.
+// the packed reference (2-bit words, directory, exception entries and
+// their counter; a streamed batch packs in one pass, with no mask
+// scratch), the query table, the piece table and the per-query counts.
 constexpr uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 constexpr uint64_t kOffHl = 0;
-constexpr uint64_t kOffNb = align256(kOffHl + kNaWords * sizeof(uint2));
-constexpr uint64_t kOffDir = align256(kOffNb + kNaWords * sizeof(uint2));
+constexpr uint64_t kOffDir = align256(kOffHl + kNaWords * sizeof(uint2));
 constexpr uint64_t kOffExc = align256(kOffDir + ((kNaWords + 31) / 32 + 3) * sizeof(uint2));
 constexpr uint64_t kOffExcN = align256(kOffExc + kNaWords * sizeof(uint2));
 constexpr uint64_t kOffQWords = align256(kOffExcN + 2 * sizeof(unsigned long long));
@@ -178,11 +177,12 @@ extern "C" ifa_status ifa_scan_brute_noalloc(int32_t device, const uint8_t *cons
     if (setup_only) return IFA_OK;
     RefBufs ref;
     ref.hl = reinterpret_cast<uint2 *>(base + kOffHl);
-    ref.nb = reinterpret_cast<uint2 *>(base + kOffNb);
+    ref.nb = nullptr;
     ref.dir = reinterpret_cast<uint2 *>(base + kOffDir);
     ref.exc = reinterpret_cast<uint2 *>(base + kOffExc);
     ref.exc_n = reinterpret_cast<unsigned long long *>(base + kOffExcN);
-    ref.words_cap = ref.nb_cap = ref.exc_cap = kNaWords;
+    ref.words_cap = ref.exc_cap = kNaWords;
+    ref.nb_cap = 0;
     uint4 *qwords = reinterpret_cast<uint4 *>(base + kOffQWords);
     uint32_t *qmeta = reinterpret_cast<uint32_t *>(base + kOffQMeta);
     DevPiece *dpieces = reinterpret_cast<DevPiece *>(base + kOffPieces);

@@ -21,8 +21,10 @@
 // the hot loop computes only word 0 for 4 entries x 4 windows, packs each
 // entry's four counts into one word whose byte high bits say "over the
 // threshold" (see packed_counts), and one warp vote per 4 entries decides
-// whether the exact path (all words, hit emission) runs for any of them
-// (then a vote per entry picks which).  Entries whose first word is fully
+// whether any of them passed.  Entries that passed in a lane wait in that
+// lane's column of a small shared queue until the block ends; then every
+// lane recounts its own candidates (all words, hit events) at once
+// (drain_queue).  Entries whose first word is fully
 // counted and that hold no N ("class F") need no care mask, so a window
 // costs 2 LOP3 + 1 POPC on the ALU/POPC pipes plus 1 IMAD on the FMA
 // pipe -- the POPC pipe (16 lanes/clk/SM) is the binding unit.  Other
