@@ -195,10 +195,26 @@ ifa_status ifa_load_queries(ifa_handle *h, const uint8_t *const *seqs, const uin
                             uint32_t n, uint32_t *first_id);
 
 /* maxSubs for segments pushed from now on; any value (no upper limit,
- * Methods; a value >= L reports every window). */
+ * Methods; a value >= L reports every window).  Applies to every query and
+ * clears the per-query values of ifa_set_query_max_subs. */
 ifa_status ifa_set_max_subs(ifa_handle *h, uint32_t max_subs);
 
-/* Brute force, indexed, or automatic by query count (Discussion). */
+/* Each query's own maxSubs for segments pushed from now on: max_subs[i] is
+ * query i's (the paper fixes one maxSubs per run, Methods; a window of query
+ * i is reported when its substitutions are <= max_subs[i]).  n must equal
+ * the number of loaded queries; values of 255 or more report every window.
+ * The array is copied.  Every streaming path honours it: popcount and
+ * tensor-core brute force, the clip pass, indexed mode (one k and MinHits
+ * plan per query for its own value) and the automatic mode choice, which
+ * is redone.  max_subs == NULL with n == 0 goes back to the single value
+ * of ifa_set_max_subs.  ifa_load_queries also goes back to it (the new
+ * queries have no value yet).  Hits already reported are unchanged.
+ * Errors: INVALID_ARG (NULL handle, n != loaded query count, NULL array
+ * with n > 0); CUDA/OOM from re-uploading the query table. */
+ifa_status ifa_set_query_max_subs(ifa_handle *h, const uint32_t *max_subs, uint32_t n);
+
+/* Brute force, indexed, or automatic (Discussion): by rates measured on
+ * this GPU unless ifa_config.auto_crossover sets a query-count rule. */
 ifa_status ifa_set_mode(ifa_handle *h, ifa_mode mode);
 
 /* Stream one reference segment past the queries (Methods, "Algorithm
@@ -271,7 +287,7 @@ ifa_status ifa_get_digest(ifa_handle *h, ifa_digest *d, uint64_t *per_query_coun
 
 /* Forget hits, digest, counts, overflow, a tensor-core timeout status,
  * statistics and the stream position (the next segment may start any
- * contig); keeps the queries, maxSubs and mode. */
+ * contig); keeps the queries, maxSubs (one or per query) and mode. */
 ifa_status ifa_reset_results(ifa_handle *h);
 
 /* Counters since the last reset. */

@@ -81,6 +81,7 @@ _SYMBOLS = {
     "ifa_load_queries": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
                                    C.c_uint32, C.POINTER(C.c_uint32)]),
     "ifa_set_max_subs": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "ifa_set_query_max_subs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32]),
     "ifa_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "ifa_push_segment": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32,
                                    C.c_int]),
@@ -197,6 +198,15 @@ def ifa_load_queries(h, queries: Sequence[bytes]) -> int:
 
 def ifa_set_max_subs(h, s: int) -> None:
     _check(lib().ifa_set_max_subs(h, int(s)), h)
+
+
+def ifa_set_query_max_subs(h, max_subs: Optional[Sequence[int]]) -> None:
+    """Each loaded query's own maxSubs (None: back to the single value)."""
+    if max_subs is None:
+        _check(lib().ifa_set_query_max_subs(h, None, 0), h)
+        return
+    a = np.ascontiguousarray(np.asarray(max_subs, dtype=np.uint32))
+    _check(lib().ifa_set_query_max_subs(h, a.ctypes.data if a.size else None, a.size), h)
 
 
 def ifa_set_mode(h, mode: int) -> None:
@@ -634,13 +644,17 @@ def shard_halo(contig_len: np.ndarray, lo: int, lmax: int, contig_ids=None):
 class Aligner:
     """One handle: load queries once, stream the reference, drain hits."""
 
-    def __init__(self, queries: Sequence[bytes] = (), max_subs: int = 0,
+    def __init__(self, queries: Sequence[bytes] = (), max_subs=0,
                  mode: int = IFA_MODE_BRUTE, **cfg):
+        """max_subs: one value for every query, or a sequence of one per query."""
         self.h = ifa_create(**cfg)
         self.nq = 0
         if queries:
             self.load_queries(queries)
-        ifa_set_max_subs(self.h, max_subs)
+        if np.ndim(max_subs) == 0:
+            ifa_set_max_subs(self.h, int(max_subs))
+        else:
+            ifa_set_query_max_subs(self.h, max_subs)
         ifa_set_mode(self.h, mode)
 
     def close(self):

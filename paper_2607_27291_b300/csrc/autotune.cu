@@ -228,12 +228,11 @@ ifa_status measure_rates(ifa_handle *h, const Batch &b, const std::vector<std::s
     return IFA_OK;
 }
 
-ifa_status choose_mode(ifa_handle *h, const Rates &r, const std::vector<std::string> &qs, uint32_t s,
-                       ifa_mode *mode) {
+ifa_status choose_mode(ifa_handle *h, const Rates &r, const std::vector<std::string> &qs,
+                       const std::vector<uint32_t> &svec, ifa_mode *mode) {
     const uint32_t nq = static_cast<uint32_t>(qs.size());
     IndexedState plan;
-    const ifa_status st = indexed_plan_q(plan, qs, std::vector<uint32_t>(nq, s), std::vector<uint8_t>(nq, 1), h->cfg,
-                                         h->stream, h->err);
+    const ifa_status st = indexed_plan_q(plan, qs, svec, std::vector<uint8_t>(nq, 1), h->cfg, h->stream, h->err);
     if (st != IFA_OK) return st;
     const ModeCost c = predict_cost(r, qs, 0, nq, plan, h->cfg.kmer_step);
     *mode = c.seeded && c.idx_s < c.brute_s ? IFA_MODE_INDEXED : IFA_MODE_BRUTE;

@@ -153,15 +153,18 @@ ifa_status resolve_mode(ifa_handle *h, ifa_mode *out) {
         *out = h->qs.size() >= h->cfg.auto_crossover ? IFA_MODE_INDEXED : IFA_MODE_BRUTE;
         return IFA_OK;
     }
-    if (h->auto_mode == IFA_MODE_AUTO || h->auto_s != h->max_subs) {
+    const uint32_t s_key = h->per_query_s ? kSPerEntry : h->max_subs;
+    if (h->auto_mode == IFA_MODE_AUTO || h->auto_s != s_key) {
+        const std::vector<uint32_t> svec =
+            h->per_query_s ? h->qs_s : std::vector<uint32_t>(h->qs.size(), h->max_subs);
         Rates r;
-        ifa_status st = rates_on_random(h, h->qs, std::vector<uint32_t>(h->qs.size(), h->max_subs), r);
+        ifa_status st = rates_on_random(h, h->qs, svec, r);
         if (st != IFA_OK) return st;
         ifa_mode m = IFA_MODE_BRUTE;
-        st = choose_mode(h, r, h->qs, h->max_subs, &m);
+        st = choose_mode(h, r, h->qs, svec, &m);
         if (st != IFA_OK) return st;
         h->auto_rates = r;
-        h->auto_s = h->max_subs;
+        h->auto_s = s_key;
         h->auto_mode = m;
     }
     *out = h->auto_mode;
@@ -315,8 +318,32 @@ constexpr double kTcAutoMaxHitRate = 2e-4;
 bool use_tensor_cores(const ifa_handle *h) {
     if (!h->d_tcA) return false;
     if (h->cfg.brute_kernel == IFA_BRUTE_TENSOR) return true;
-    return h->cfg.brute_kernel == IFA_BRUTE_AUTO &&
-           tc_auto_choice(h->qs, 0, static_cast<uint32_t>(h->qs.size()), h->max_subs);
+    // per-query thresholds: judged at the largest (the densest hits)
+    uint32_t s = h->max_subs;
+    if (h->per_query_s)
+        s = h->qs_s.empty() ? 0u : *std::max_element(h->qs_s.begin(), h->qs_s.end());
+    return h->cfg.brute_kernel == IFA_BRUTE_AUTO && tc_auto_choice(h->qs, 0, static_cast<uint32_t>(h->qs.size()), s);
+}
+
+// The streaming indexed plan and tables for the current thresholds: one
+// maxSubs for all queries, or each query's own (ifa_set_query_max_subs).
+ifa_status stream_indexed_prepare(ifa_handle *h) {
+    if (!h->per_query_s)
+        return indexed_prepare(h->idx, h->qs, h->qmeta_host, h->qwords_host, h->wmax, h->cfg, h->max_subs,
+                               h->stream, h->err);
+    IndexedState &S = h->idx;
+    if (!(S.plan_valid && !S.plan_uniform && S.plan_s == kSPerEntry)) {
+        const ifa_status st = indexed_plan_q(S, h->qs, h->qs_s, std::vector<uint8_t>(h->qs.size(), 1), h->cfg,
+                                             h->stream, h->err);
+        if (st != IFA_OK) return st;
+        S.plan_uniform = false;
+        S.plan_s = kSPerEntry;
+    }
+    if (S.tables_valid && S.tables_s == kSPerEntry && S.wmax == h->wmax) return IFA_OK;
+    const ifa_status st = indexed_tables(S, h->qs, h->qmeta_host, h->qwords_host, h->wmax, h->cfg, h->stream, h->err);
+    if (st != IFA_OK) return st;
+    S.tables_s = kSPerEntry;
+    return IFA_OK;
 }
 
 }  // namespace
@@ -507,6 +534,7 @@ ifa_status ifa_load_queries(ifa_handle *h, const uint8_t *const *seqs, const uin
         h->lmax = std::max(h->lmax, lens[i]);
     }
     h->qdirty = true;
+    h->per_query_s = false;         // the new queries have no value of their own yet
     h->auto_mode = IFA_MODE_AUTO;   // the automatic choice is redone for the new set
     cudaFree(h->d_qcount);
     h->d_qcount = nullptr;
@@ -521,6 +549,30 @@ ifa_status ifa_set_max_subs(ifa_handle *h, uint32_t s) {
     // 255 or more reports every window (and plans MinHits bins with s >= L);
     // the clamp keeps launches clear of the per-entry threshold sentinel.
     h->max_subs = s < 255u ? s : 255u;
+    h->per_query_s = false;
+    return IFA_OK;
+}
+
+ifa_status ifa_set_query_max_subs(ifa_handle *h, const uint32_t *max_subs, uint32_t n) {
+    if (!h) return fail(nullptr, IFA_ERR_INVALID_ARG, "handle is NULL");
+    if (!max_subs && n == 0) {
+        h->per_query_s = false;
+        return IFA_OK;
+    }
+    if (!max_subs) return fail(h, IFA_ERR_INVALID_ARG, "max_subs is NULL");
+    if (n != h->qs.size()) return fail(h, IFA_ERR_INVALID_ARG, "one maxSubs per loaded query");
+    CK(h, cudaSetDevice(h->dev));
+    // in-flight scans read the query table that the next push re-uploads
+    const ifa_status st = sync_all(h);
+    if (st != IFA_OK) return st;
+    // each value lives in its entries' meta word (bits 24-31), which the
+    // kernels read when the launch threshold is the per-entry sentinel
+    h->qs_s.assign(max_subs, max_subs + n);
+    for (uint32_t &v : h->qs_s) v = std::min<uint32_t>(v, 255u);
+    h->per_query_s = true;
+    h->qdirty = true;
+    h->auto_mode = IFA_MODE_AUTO;
+    h->batch.plan_valid = false;
     return IFA_OK;
 }
 
@@ -573,8 +625,7 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
     if (st != IFA_OK) return st;
     h->mode_run = mode;
     if (mode == IFA_MODE_INDEXED) {
-        st = indexed_prepare(h->idx, h->qs, h->qmeta_host, h->qwords_host, h->wmax, h->cfg, h->max_subs,
-                             h->stream, h->err);
+        st = stream_indexed_prepare(h);
         if (st != IFA_OK) return st;
     }
 
@@ -623,13 +674,15 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
     qt.ids = nullptr;
     qt.n_entries = 2 * static_cast<uint32_t>(h->qs.size());
     qt.wmax = h->wmax;
+    // one threshold for all entries, or each entry's own from its meta word
+    const uint32_t s_run = h->per_query_s ? kSPerEntry : h->max_subs;
     const HitSink sink = make_sink(h);
     cudaEvent_t prof_stop = nullptr;
     st = prof_begin(h, &prof_stop);
     if (st != IFA_OK) return st;
     const int before_scan = launches;
     if (mode == IFA_MODE_INDEXED) {
-        st = indexed_scan(h->idx, b, qt, h->max_subs, sink, h->stream, &launches, h->err);
+        st = indexed_scan(h->idx, b, qt, s_run, sink, h->stream, &launches, h->err);
         if (st != IFA_OK) return st;
     }
     if (mode == IFA_MODE_BRUTE) {
@@ -640,18 +693,18 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
                 CK(h, cudaMalloc(&h->d_tc_status, 2 * sizeof(unsigned int)));
                 CK(h, cudaMemsetAsync(h->d_tc_status, 0, 2 * sizeof(unsigned int), h->stream));
             }
-            CK(h, launch_scan_tc(b, h->d_tcA, h->d_qmeta, qt.n_entries, h->tc_lpad, h->max_subs, sink,
+            CK(h, launch_scan_tc(b, h->d_tcA, h->d_qmeta, qt.n_entries, h->tc_lpad, s_run, sink,
                                  h->d_tc_status, h->stream, h->cfg.test_stall));
             h->tc_used = true;
             launches++;
         } else {
             for (const Chunk &c : h->chunks)
-                CK(h, launch_scan_brute(b, qt, c.e0, c.e1, h->max_subs, c.lmin, c.lmax, sink, h->stream, &launches));
+                CK(h, launch_scan_brute(b, qt, c.e0, c.e1, s_run, c.lmin, c.lmax, sink, h->stream, &launches));
         }
     }
     if (h->cfg.clip_pct) {
         // windows overhanging contig ends, exhaustively in either mode
-        CK(h, launch_clip_scan(b, qt, qt.n_entries, h->cfg.clip_pct, h->max_subs, h->lmax, sink, h->stream));
+        CK(h, launch_clip_scan(b, qt, qt.n_entries, h->cfg.clip_pct, s_run, h->lmax, sink, h->stream));
         launches++;
     }
     st = prof_end(h, prof_stop, launches - before_scan);
@@ -913,7 +966,8 @@ ifa_status ifa_get_query_plan(ifa_handle *h, uint32_t *k, uint32_t *minhits, uin
     CK(h, cudaSetDevice(h->dev));
     ifa_status st = upload_queries(h);
     if (st != IFA_OK) return st;
-    st = indexed_plan(h->idx, h->qs, h->cfg, h->max_subs, h->stream, h->err);
+    st = h->per_query_s ? stream_indexed_prepare(h)
+                        : indexed_plan(h->idx, h->qs, h->cfg, h->max_subs, h->stream, h->err);
     if (st != IFA_OK) return st;
     for (size_t q = 0; q < h->qs.size(); q++) {
         if (k) k[q] = h->idx.plan_k[q];

@@ -91,6 +91,7 @@ struct ifa_handle {
     bool pushed = false;
 
     uint32_t max_subs = 0;
+    bool per_query_s = false;   // qs_s holds each query's own maxSubs (ifa_set_query_max_subs)
     ifa_mode mode = IFA_MODE_BRUTE;
     // IFA_MODE_AUTO by measured rates: rates on the calibration sequence
     // (per maxSubs, auto_s) and the mode they gave for the loaded queries
@@ -141,9 +142,9 @@ ModeCost predict_cost(const Rates &r, const std::vector<std::string> &qs, uint32
 // maxSubs svec; count-only sinks, so no result of the handle changes.
 ifa_status measure_rates(ifa_handle *h, const Batch &b, const std::vector<std::string> &qs,
                          const std::vector<uint32_t> &svec, Rates &out);
-// The mode with the smaller predicted time for qs at maxSubs s.
-ifa_status choose_mode(ifa_handle *h, const Rates &r, const std::vector<std::string> &qs, uint32_t s,
-                       ifa_mode *mode);
+// The mode with the smaller predicted time for qs at maxSubs svec.
+ifa_status choose_mode(ifa_handle *h, const Rates &r, const std::vector<std::string> &qs,
+                       const std::vector<uint32_t> &svec, ifa_mode *mode);
 // Rates measured on 16 Mbp of uniform random bases packed on the device
 // (the streaming calls, and stores smaller than that), or on a slice of
 // the store.

@@ -83,7 +83,7 @@ ifa_status prepare_request(ifa_handle *h, Request &r) {
             const ifa_status st = rates_on_store(h, b, r.qs, std::vector<uint32_t>(r.qs.size(), r.s), S.rates);
             if (st != IFA_OK) return st;
         }
-        const ifa_status st = choose_mode(h, S.rates, r.qs, r.s, &r.mode);
+        const ifa_status st = choose_mode(h, S.rates, r.qs, std::vector<uint32_t>(r.qs.size(), r.s), &r.mode);
         if (st != IFA_OK) return st;
     }
     uint32_t lmax = 1;
