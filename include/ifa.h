@@ -150,7 +150,13 @@ typedef struct {
     uint32_t test_stall;           /* testing only (keep 0): 1 makes each tensor-core CTA withhold its
                                       first tile, so a pipeline wait runs out after its 4 s limit and
                                       ifa_flush reports TIMEOUT -- the bounded-wait path, without a fault */
-    uint32_t reserved[4];
+    uint32_t event_capacity;       /* streaming brute force defers hit expansion: the scan writes one
+                                      16-byte record per (query strand, 32-window group) with a hit into a
+                                      device buffer of this many records (0: max(2^20, segment_bytes / 32)),
+                                      and a second kernel turns them into hits; a launch whose records do
+                                      not fit is scanned again with the hits expanded in line (same
+                                      results, slower) */
+    uint32_t reserved[3];
 } ifa_config;
 
 typedef struct {

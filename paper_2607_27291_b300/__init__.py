@@ -45,7 +45,7 @@ class ifa_config(C.Structure):
                 ("minhits_seed", C.c_uint64), ("clip_pct", C.c_uint32),
                 ("exhaustive_fallback", C.c_uint32), ("auto_crossover", C.c_uint32),
                 ("profile", C.c_uint32), ("brute_kernel", C.c_uint32), ("test_stall", C.c_uint32),
-                ("reserved", C.c_uint32 * 4)]
+                ("event_capacity", C.c_uint32), ("reserved", C.c_uint32 * 3)]
 
 
 class ifa_digest(C.Structure):

@@ -445,6 +445,9 @@ ifa_status ifa_create(const ifa_config *cfg, ifa_handle **out) {
         CKC(cudaEventCreateWithFlags(&h->ev_consumed[i], cudaEventDisableTiming));
     }
     if (!cfg->count_only) CKC(cudaMalloc(&h->d_ring, cfg->hit_capacity * sizeof(ifa_hit)));
+    h->ev.cap = cfg->event_capacity ? cfg->event_capacity : std::max<uint64_t>(1ull << 20, sb / 32);
+    CKC(cudaMalloc(&h->ev.buf, h->ev.cap * sizeof(uint4)));
+    CKC(cudaMalloc(&h->ev.head, sizeof(unsigned long long)));
     CKC(cudaMalloc(&h->d_head, 3 * sizeof(unsigned long long)));
     CKC(cudaMalloc(&h->d_overflow, sizeof(uint32_t)));
     CKC(cudaMalloc(&h->d_digest, 3 * sizeof(unsigned long long)));
@@ -491,6 +494,8 @@ void ifa_destroy(ifa_handle *h) {
     cudaFree(h->d_tcA);
     cudaFree(h->d_tc_status);
     cudaFree(h->d_ring);
+    cudaFree(h->ev.buf);
+    cudaFree(h->ev.head);
     cudaFree(h->d_head);
     if (h->drain_stream) cudaStreamSynchronize(h->drain_stream);
     cudaFreeHost(h->h_marks);
@@ -682,7 +687,7 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
     if (st != IFA_OK) return st;
     const int before_scan = launches;
     if (mode == IFA_MODE_INDEXED) {
-        st = indexed_scan(h->idx, b, qt, s_run, sink, h->stream, &launches, h->err);
+        st = indexed_scan(h->idx, b, qt, s_run, sink, h->stream, &launches, h->err, &h->ev);
         if (st != IFA_OK) return st;
     }
     if (mode == IFA_MODE_BRUTE) {
@@ -699,7 +704,8 @@ ifa_status ifa_push_segment(ifa_handle *h, const uint8_t *ascii, uint64_t len, c
             launches++;
         } else {
             for (const Chunk &c : h->chunks)
-                CK(h, launch_scan_brute(b, qt, c.e0, c.e1, s_run, c.lmin, c.lmax, sink, h->stream, &launches));
+                CK(h, launch_scan_brute(b, qt, c.e0, c.e1, s_run, c.lmin, c.lmax, sink, h->stream, &launches,
+                                        &h->ev));
         }
     }
     if (h->cfg.clip_pct) {

@@ -70,6 +70,7 @@ struct ifa_handle {
     uint32_t *d_overflow = nullptr;
     unsigned long long *d_digest = nullptr;
     unsigned long long *d_qcount = nullptr;
+    ifa::EventSink ev{nullptr, nullptr, 0};  // deferred hits of the brute-force scan
     uint64_t tail = 0;                       // hits drained from the ring
     // per pushed segment, a pinned copy of {head, first dropped claim} taken
     // on the compute stream after its scan, and an event: once the event has

@@ -297,4 +297,62 @@ struct WarpHitsT {
 
 using WarpHits = WarpHitsT<false>;
 
+// The scan side of deferred hits (EventSink).  The same event() call as
+// WarpHits, but the lanes with an event store it straight into the warp's
+// open chunk of kEventChunk slots of the buffer, at their ballot ranks: no
+// shared staging, no piece lookup, digest or ring claim in the scan loop,
+// so the loop carries none of that code either.  A chunk is claimed with
+// one atomic; the slots a warp leaves unused are zeroed (no window bit
+// set), and the expansion skips them.  Slots at or past the capacity are
+// not written (head then tells the expansion to rescan).
+constexpr uint32_t kEventChunk = 128;   // > 32: one claim always fits a call's events
+
+struct WarpEvents {
+    EventSink es;
+    unsigned long long at, end;   // the warp's open chunk [at, end) (warp-uniform)
+
+    __device__ void init(const EventSink &s) {
+        es = s;
+        at = end = 0;
+    }
+
+    // nothing is staged for emit() (the brute-force loop only makes events)
+    __device__ void flush(const HitSink &, uint32_t) {}
+
+    __device__ __forceinline__ void event(const Batch &, const uint32_t *, uint32_t, uint32_t *, const HitSink &,
+                                          uint32_t lane, bool has, uint32_t e, uint32_t d, uint32_t blk, uint32_t hm) {
+        const uint32_t ballot = __ballot_sync(0xffffffffu, has);
+        if (ballot == 0) return;
+        const uint32_t c = __popc(ballot);
+        if (at + c > end) claim(lane);
+        if (has) {
+            const unsigned long long i = at + __popc(ballot & ((1u << lane) - 1u));
+            if (i < es.cap) es.buf[i] = make_uint4(e | (lane << 16), d, blk, hm);
+        }
+        at += c;
+    }
+
+    // Zero the open chunk's unused slots (all lanes).
+    __device__ void close(uint32_t lane) {
+        for (unsigned long long i = at + lane; i < end; i += 32)
+            if (i < es.cap) es.buf[i] = make_uint4(0u, 0u, 0u, 0u);
+        at = end;
+    }
+
+    __device__ void claim(uint32_t lane) {
+        close(lane);
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(es.head, static_cast<unsigned long long>(kEventChunk));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        at = base;
+        end = base + kEventChunk;
+    }
+
+    // End of a block range.
+    __device__ void flush_events(const Batch &, const uint32_t *, uint32_t, uint32_t *, const HitSink &,
+                                 uint32_t lane) {
+        close(lane);
+    }
+};
+
 }  // namespace ifa

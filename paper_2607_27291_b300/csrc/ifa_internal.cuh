@@ -126,6 +126,19 @@ struct HitSink {
     unsigned long long *ovf_at = nullptr;      // ring mode: first dropped claim (~0 when none)
 };
 
+// Deferred brute-force hits (streaming scan): the scan writes its window
+// events -- one 16-byte record per (entry, lane, block) with a hit, the
+// record the warp staging uses -- into this buffer, and a second kernel
+// expands them into hits.  Slots are claimed a chunk per warp; `head`
+// counts the slots claimed and exceeds `cap` when some did not fit, in
+// which case the second kernel scans the launch's range again with the
+// hits expanded in line.
+struct EventSink {
+    uint4 *buf;
+    unsigned long long *head;
+    unsigned long long cap;
+};
+
 struct QueryTable {
     const uint4 *words;      // entries x wmax
     const uint32_t *meta;    // entries
@@ -289,9 +302,12 @@ unsigned long long *bounds_word();
 cudaError_t launch_halo_update(const uint8_t *old_halo, uint32_t old_len, const uint8_t *seg,
                                uint64_t slen, uint32_t new_len, uint8_t *new_halo, cudaStream_t st);
 
+// Brute-force scan of entries [e0, e1) of qt.  With an event sink the hits
+// are deferred (two kernels, see EventSink); without one they are expanded
+// in the scan loop (one kernel).
 cudaError_t launch_scan_brute(const Batch &b, const QueryTable &qt, uint32_t e0, uint32_t e1,
                               uint32_t max_subs, uint32_t lmin, uint32_t lmax, const HitSink &sink,
-                              cudaStream_t st, int *launches);
+                              cudaStream_t st, int *launches, const EventSink *es = nullptr);
 uint32_t scan_brute_chunk_entries(uint32_t wmax);
 
 cudaError_t launch_minhits(const uint32_t *dL, const uint32_t *dsubs, const uint32_t *dk,

@@ -448,7 +448,8 @@ ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
 }
 
 ifa_status indexed_scan(IndexedState &S, const Batch &b, const QueryTable &qt, uint32_t s,
-                        const HitSink &sink, cudaStream_t st, int *launches, std::string &err) {
+                        const HitSink &sink, cudaStream_t st, int *launches, std::string &err,
+                        const EventSink *es) {
     cudaError_t e = cudaSuccess;
     if (S.targ.n) {
         e = launch_seed_scan(b, qt, S.targ, S.d_entry_minhits, S.step, s, sink, S.d_candidates, st);
@@ -462,7 +463,7 @@ ifa_status indexed_scan(IndexedState &S, const Batch &b, const QueryTable &qt, u
         ex.n_entries = S.ex_entries;
         ex.wmax = qt.wmax;
         for (const auto &c : S.ex_chunks) {
-            e = launch_scan_brute(b, ex, c.e0, c.e1, s, c.lmin, c.lmax, sink, st, launches);
+            e = launch_scan_brute(b, ex, c.e0, c.e1, s, c.lmin, c.lmax, sink, st, launches, es);
             if (e != cudaSuccess) break;
         }
     }

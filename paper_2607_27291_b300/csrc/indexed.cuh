@@ -119,8 +119,11 @@ ifa_status indexed_prepare(IndexedState &S, const std::vector<std::string> &qs,
                            uint32_t wmax, const ifa_config &cfg, uint32_t max_subs, cudaStream_t st,
                            std::string &err);
 
+// The seed scan, then the exhaustive entries by brute force (their hits
+// deferred through es when given).
 ifa_status indexed_scan(IndexedState &S, const Batch &b, const QueryTable &qt, uint32_t max_subs,
-                        const HitSink &sink, cudaStream_t st, int *launches, std::string &err);
+                        const HitSink &sink, cudaStream_t st, int *launches, std::string &err,
+                        const EventSink *es = nullptr);
 
 cudaError_t launch_seed_scan(const Batch &b, const QueryTable &qt, const KTablesArg &tabs,
                              const uint32_t *entry_minhits, uint32_t step, uint32_t max_subs,

@@ -107,6 +107,28 @@ def test_overflow_keeps_digest_exact():
     assert dig == oracle.digest(exp)
 
 
+@pytest.mark.parametrize("cap,count_only", [(128, 0), (700, 0), (128, 1), (1 << 22, 0)])
+def test_event_buffer_too_small_rescans_in_line(cap, count_only):
+    """Deferred hits: when a launch's window events overflow the event
+    buffer (a single chunk of 128 records here, so any two warps with hits
+    overflow it), the expansion kernel scans the range again with the hits
+    expanded in line; tuples, digest and counts stay exact, with or without
+    hit tuples.  A buffer large enough for every event takes the deferred
+    path."""
+    wl = synth.small_workload(seed=29, n_queries=5, lmin=8, lmax=40, n_contigs=12, cmin=100, cmax=20000)
+    s = 5
+    exp = oracle.brute(wl.queries, wl.ref, wl.contig_len, s)
+    assert exp.size > 10 * 700   # far more events than the small buffers hold
+    got, over, dig, counts, _ = gpu_scan(wl.queries, wl.ref, wl.contig_len, s, seg_bytes=1 << 15,
+                                         event_capacity=cap, count_only=count_only,
+                                         brute_kernel=P.IFA_BRUTE_POPC)
+    assert not over
+    if not count_only:
+        assert tuples(got) == tuples(exp)
+    assert dig == oracle.digest(exp)
+    assert counts.tolist() == np.bincount(exp["query"], minlength=len(wl.queries)).tolist()
+
+
 def test_contig_ids_are_the_callers():
     wl = synth.small_workload(seed=19, n_queries=3, n_contigs=7, cmax=2000)
     ids = np.array([3, 10, 11, 40, 41, 1000, 70000], np.int64)
