@@ -170,8 +170,10 @@ ifa_status measure_rates(ifa_handle *h, const Batch &b, const std::vector<std::s
         hi = std::max(hi, meta_L(meta[i]));
     }
     float ms = 0;
-    e = time_ms(st, 2, [&] { return launch_scan_brute(b, qt, 0, ne, kSPerEntry, lo, hi, sink, st, nullptr,
-                                                                 h->ev.buf ? &h->ev : nullptr); }, ms);
+    // the one-kernel scan: what batches run, and within 3 % of the streaming
+    // scan + expansion pair on full segments, whose extra launch would weigh
+    // about 15 % on this short calibration range
+    e = time_ms(st, 2, [&] { return launch_scan_brute(b, qt, 0, ne, kSPerEntry, lo, hi, sink, st, nullptr); }, ms);
     if (e != cudaSuccess) return afail(h, cuda_status(e), std::string("rate measurement: ") + cudaGetErrorString(e));
     Rates r;
     r.brute = ne * static_cast<double>(b.nbases) / std::max(1e-6, ms * 1e-3);
