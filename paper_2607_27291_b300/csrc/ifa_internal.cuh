@@ -247,6 +247,14 @@ __device__ inline uint32_t find_piece(const DevPiece *pc, uint32_t n, uint64_t p
     return lo;
 }
 
+// find_piece starting from a previous answer `hint` (a lane's last piece;
+// ~0 for none): the hint itself when p lies inside it, else the search.
+// Scans move forward through the pieces, so the hint usually holds.
+__device__ inline uint32_t find_piece_from(const DevPiece *pc, uint32_t n, uint64_t p, uint32_t hint) {
+    if (hint < n && pc[hint].start <= p && (hint + 1 == n || pc[hint + 1].start > p)) return hint;
+    return find_piece(pc, n, p);
+}
+
 // ---------------------------------------------------------------- launchers
 // (defined in the .cu files; all enqueue on `st`)
 

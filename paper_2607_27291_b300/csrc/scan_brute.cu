@@ -121,16 +121,6 @@ k_scan_brute_events(Batch b, QueryTable qt, uint32_t e0, uint32_t e1, uint32_t s
                       blockIdx.x * kScanWarps + warp, gridDim.x * kScanWarps, lane, cq[warp]);
 }
 
-// The piece holding base p, starting from a lane's last answer `pidx`
-// (events of one scanning warp come in position order): the cached piece
-// when p is inside it, else a binary search.
-__device__ __forceinline__ uint32_t piece_at(const Batch &b, uint64_t p, uint32_t pidx) {
-    if (pidx < b.npieces && b.pieces[pidx].start <= p &&
-        (pidx + 1 == b.npieces || b.pieces[pidx + 1].start > p))
-        return pidx;
-    return find_piece(b.pieces, b.npieces, p);
-}
-
 // Deferred hits, second kernel (same grid and shared memory).  When every
 // event fit: warp w takes a contiguous range of event records, counts its
 // hits (one bit per window in each record's mask), claims ring slots for
@@ -207,7 +197,7 @@ k_expand_events(Batch b, QueryTable qt, uint32_t e0, uint32_t e1, uint32_t s, ui
                 const uint32_t bit = static_cast<uint32_t>(__ffs(hm) - 1);  // 8 k + 7 for window k
                 hm &= hm - 1u;
                 const uint64_t p = p0 + 4u * (bit - 7u);                     // = p0 + 32 k
-                pidx = piece_at(b, p, pidx);
+                pidx = find_piece_from(b.pieces, b.npieces, p, pidx);
                 const DevPiece pc = b.pieces[pidx];
                 const uint32_t hpos = static_cast<uint32_t>(pc.contig_off + (p - pc.start));
                 const uint32_t mm = (ev.y >> (bit - 7u)) & 0xffu;

@@ -18,6 +18,7 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                                             uint32_t s, const HitSink &sink, WH &wh, uint64_t blk,
                                             uint64_t blk_end, uint64_t stride, uint32_t lane,
                                             unsigned long long &ncand) {
+    uint32_t pidx = 0xffffffffu;   // the lane's last hit's piece
     for (; blk < blk_end; blk += stride) {
         const uint64_t j = (blk << 5) + lane;
         const uint4 A = ref_word(b, blk), B = ref_word(b, blk + 1);
@@ -178,7 +179,8 @@ __device__ __forceinline__ void seed_blocks(const Batch &b, const QueryTable &qt
                                 }
                                 if (first == o && nseed >= __ldg(entry_minhits + e)) {
                                     hit = true;
-                                    const DevPiece pc = b.pieces[find_piece(b.pieces, b.npieces, p)];
+                                    pidx = find_piece_from(b.pieces, b.npieces, p, pidx);
+                                    const DevPiece pc = b.pieces[pidx];
                                     contig = pc.contig;
                                     pos = static_cast<uint32_t>(pc.contig_off + (p - pc.start));
                                     id = e;
