@@ -167,78 +167,97 @@ __device__ __forceinline__ uint32_t first_piece_at(const DevPiece *__restrict__ 
 }
 
 // Streamed batches in one pass: k_pack's words, the piece-start bits and
-// k_build_dir's directory, with no mask scratch.  Thread w packs word w; a
-// warp is the directory group of its 32 words (256-thread blocks start on
-// group boundaries).  The warp finds the group's first piece start
-// (first_piece_at) and walks the piece starts inside the group.  The grid
-// covers one group past the words' last one, written as an empty entry
-// (see k_build_dir).  exc holds at least nwords entries, so the claims
-// cannot run out; a claim past exc_cap sets exc_n[1] like k_build_dir.
+// k_build_dir's directory, with no mask scratch.  A warp packs kPackGroups
+// consecutive directory groups of 32 words, lane l word l of each: it
+// issues its ASCII loads for all of them first (8 x 16 bytes per lane in
+// flight), finds the first group's first piece start once (first_piece_at)
+// and walks the piece starts forward across its groups.  The grid covers
+// one group past the words' last one, written as an empty entry (see
+// k_build_dir).  exc holds at least nwords entries, so the claims cannot
+// run out; a claim past exc_cap sets exc_n[1] like k_build_dir.
+constexpr int kPackGroups = 4;
+
 template <bool ALIGNED>
 __global__ void __launch_bounds__(kPackThreads)
 k_pack_dir(const uint8_t *__restrict__ halo, uint32_t hlen, uint32_t H, const uint8_t *__restrict__ seg,
            uint64_t slen, uint2 *__restrict__ hl, uint64_t nwords, const DevPiece *__restrict__ pc, uint32_t npieces,
            bool mark, uint2 *__restrict__ dir, uint2 *__restrict__ exc, uint64_t exc_cap,
            unsigned long long *__restrict__ exc_n) {
-    const uint64_t w = static_cast<uint64_t>(blockIdx.x) * kPackThreads + threadIdx.x;
-    const uint64_t g = w >> 5;
     const uint32_t lane = threadIdx.x & 31u;
-    if (g > ((nwords - 1) >> 5) + 1) return;  // whole warps
-    uint32_t hi = 0, lo = 0, nn = 0, bb = 0;
-    const bool live = w < nwords;
-    if (live) {
-        const uint64_t hw = H >> 5;
-        if (w < hw) {
-            const uint32_t pad = H - hlen;
-            for (uint32_t b = 0; b < 32; b++) {
-                const uint32_t i = static_cast<uint32_t>(w) * 32 + b;
-                pack_byte(i < pad ? 'N' : halo[i - pad], b, hi, lo, nn);
-            }
-        } else {
-            const uint64_t o = (w - hw) * 32;
-            if (ALIGNED && o + 32 <= slen) {
-                const uint4 *v = reinterpret_cast<const uint4 *>(seg + o);
-                const uint4 a = __ldg(v), c = __ldg(v + 1);
-                const uint32_t u[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+    const uint64_t g0 = ((static_cast<uint64_t>(blockIdx.x) * kPackThreads + threadIdx.x) >> 5) * kPackGroups;
+    const uint64_t last_g = ((nwords - 1) >> 5) + 1;   // one group past the last word's
+    if (g0 > last_g) return;                           // whole warps
+    const uint64_t hw = H >> 5;
+    uint4 va[kPackGroups], vc[kPackGroups];
 #pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    uint32_t h4, l4, n4;
-                    pack4(u[j], h4, l4, n4);
-                    hi |= h4 << (4 * j);
-                    lo |= l4 << (4 * j);
-                    nn |= n4 << (4 * j);
+    for (int t = 0; t < kPackGroups; t++) {
+        va[t] = vc[t] = make_uint4(0u, 0u, 0u, 0u);
+        const uint64_t w = (g0 + t) * 32 + lane;
+        if (ALIGNED && w < nwords && w >= hw && (w - hw) * 32 + 32 <= slen) {
+            const uint4 *v = reinterpret_cast<const uint4 *>(seg + (w - hw) * 32);
+            va[t] = __ldg(v);
+            vc[t] = __ldg(v + 1);
+        }
+    }
+    uint32_t pi = mark && npieces ? first_piece_at(pc, npieces, g0 << 10, lane) : 0u;
+#pragma unroll
+    for (int t = 0; t < kPackGroups; t++) {
+        const uint64_t g = g0 + t;
+        if (g > last_g) break;   // warp-uniform
+        const uint64_t w = g * 32 + lane;
+        uint32_t hi = 0, lo = 0, nn = 0, bb = 0;
+        const bool live = w < nwords;
+        if (live) {
+            if (w < hw) {
+                const uint32_t pad = H - hlen;
+                for (uint32_t b = 0; b < 32; b++) {
+                    const uint32_t i = static_cast<uint32_t>(w) * 32 + b;
+                    pack_byte(i < pad ? 'N' : halo[i - pad], b, hi, lo, nn);
                 }
-                hi &= ~nn;
-                lo &= ~nn;
             } else {
-                for (uint32_t b = 0; b < 32; b++)
-                    pack_byte(o + b < slen ? seg[o + b] : 'N', b, hi, lo, nn);
+                const uint64_t o = (w - hw) * 32;
+                if (ALIGNED && o + 32 <= slen) {
+                    const uint32_t u[8] = {va[t].x, va[t].y, va[t].z, va[t].w, vc[t].x, vc[t].y, vc[t].z, vc[t].w};
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        uint32_t h4, l4, n4;
+                        pack4(u[j], h4, l4, n4);
+                        hi |= h4 << (4 * j);
+                        lo |= l4 << (4 * j);
+                        nn |= n4 << (4 * j);
+                    }
+                    hi &= ~nn;
+                    lo &= ~nn;
+                } else {
+                    for (uint32_t b = 0; b < 32; b++)
+                        pack_byte(o + b < slen ? seg[o + b] : 'N', b, hi, lo, nn);
+                }
             }
+            hl[w] = make_uint2(hi, lo);
         }
-        hl[w] = make_uint2(hi, lo);
-    }
-    if (mark && npieces) {
-        const uint64_t gs = g << 10, ge = gs + 1024;
-        const uint32_t first = first_piece_at(pc, npieces, gs, lane);
-        for (uint32_t i = first; i < npieces; i++) {
-            const uint64_t p = pc[i].start;   // warp-uniform
-            if (p >= ge) break;
-            if (p != 0 && (p >> 5) == w) bb |= 1u << (p & 31);
+        if (mark && npieces) {
+            // the starts in this group; pi ends at the first start of the next
+            const uint64_t ge = (g + 1) << 10;
+            for (; pi < npieces; pi++) {
+                const uint64_t p = pc[pi].start;   // warp-uniform
+                if (p >= ge) break;
+                if (p != 0 && (p >> 5) == w) bb |= 1u << (p & 31);
+            }
+            if (!live) bb = 0;
         }
-        if (!live) bb = 0;
+        const bool special = (nn | bb) != 0u;
+        const uint32_t bits = __ballot_sync(0xffffffffu, special);
+        const uint32_t cnt = __popc(bits);
+        unsigned long long base = 0;
+        if (lane == 0 && cnt) base = atomicAdd(exc_n, static_cast<unsigned long long>(cnt));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base + cnt > exc_cap) {
+            if (lane == 0) exc_n[1] = 1ull;
+            return;
+        }
+        if (special) exc[base + __popc(bits & ((1u << lane) - 1u))] = make_uint2(nn, bb);
+        if (lane == 0) dir[g] = make_uint2(bits, static_cast<uint32_t>(base));
     }
-    const bool special = (nn | bb) != 0u;
-    const uint32_t bits = __ballot_sync(0xffffffffu, special);
-    const uint32_t cnt = __popc(bits);
-    unsigned long long base = 0;
-    if (lane == 0 && cnt) base = atomicAdd(exc_n, static_cast<unsigned long long>(cnt));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base + cnt > exc_cap) {
-        if (lane == 0) exc_n[1] = 1ull;
-        return;
-    }
-    if (special) exc[base + __popc(bits & ((1u << lane) - 1u))] = make_uint2(nn, bb);
-    if (lane == 0) dir[g] = make_uint2(bits, static_cast<uint32_t>(base));
 }
 
 __global__ void k_halo_update(const uint8_t *__restrict__ old_halo, uint32_t old_len,
@@ -317,7 +336,8 @@ cudaError_t pack_batch(const RefBufs &R, const uint8_t *halo, uint32_t hlen, uin
     if (nwords == 0 || nwords > R.words_cap || nwords > R.exc_cap) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(R.exc_n, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    const uint64_t threads = ((((nwords - 1) >> 5) + 2) << 5);   // one group past the last word's
+    const uint64_t groups = ((nwords - 1) >> 5) + 2;   // one group past the last word's
+    const uint64_t threads = (groups + kPackGroups - 1) / kPackGroups * 32;
     const unsigned grid = static_cast<unsigned>((threads + kPackThreads - 1) / kPackThreads);
     if ((reinterpret_cast<uintptr_t>(seg) & 15u) == 0)
         k_pack_dir<true><<<grid, kPackThreads, 0, st>>>(halo, hlen, H, seg, slen, R.hl, nwords, pieces, npieces, mark,
