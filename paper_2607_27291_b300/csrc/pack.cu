@@ -32,26 +32,62 @@ __device__ __forceinline__ void pack_byte(uint32_t c, uint32_t bit, uint32_t &hi
     nn |= (ok ^ 1u) << bit;
 }
 
-// Bits 0, 8, 16, 24 of m gathered into bits 24..27 by one multiply: the
-// partial products of 2^24, 2^17, 2^10, 2^3 land on distinct bits, so no
-// carries occur and bits 24..27 hold exactly the four selected bits.
-__device__ __forceinline__ uint32_t gather_nibble(uint32_t m) { return (m * 0x01020408u) >> 24; }
+// Two words' selected bits -- bits 0, 8, 16, 24 (word a) and 4, 12, 20,
+// 28 (word b) of t -- gathered into bits 24..31 of the product by one
+// multiply: the partial products of 2^24, 2^17, 2^10, 2^3 put the
+// selected bits on 24..31 in base order and every other bit on a distinct
+// position below 24 or past 31, so no carry reaches the top byte.
+__device__ __forceinline__ uint32_t gather_pair(uint32_t t) { return t * 0x01020408u; }
 
-// Four ASCII bytes (byte j of u = base j) -> bits 0..3 of the hi, lo and N
-// planes.  The 2-bit code is (byte >> 1) & 3 (A 0, C 1, T 2, G 3); a byte is
-// a base exactly when, with the case bit set, it equals the lower-case
-// letter its code bits name, tested for all four bytes at once with an
-// exact zero-byte test.  Code bits of non-bases are cleared by the caller.
-__device__ __forceinline__ void pack4(uint32_t u, uint32_t &h4, uint32_t &l4, uint32_t &n4) {
-    const uint32_t l = (u >> 1) & 0x01010101u;
-    const uint32_t h = (u >> 2) & 0x01010101u;
-    // per byte 0x61 + 2 l + 19 h - 15 l h: 'a' 'c' 't' 'g' for codes 0..3 (no carries)
-    const uint32_t letter = 0x61616161u + 2u * l + 19u * h - 15u * (l & h);
-    const uint32_t x = (u | 0x20202020u) ^ letter;
-    const uint32_t nz = (((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x) & 0x80808080u;  // high bit: byte != 0
-    l4 = gather_nibble(l);
-    h4 = gather_nibble(h);
-    n4 = gather_nibble(nz >> 7);
+// The top bytes of four gathered products as one word (byte p from p).
+__device__ __forceinline__ uint32_t top_bytes(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3) {
+    return __byte_perm(__byte_perm(p0, p1, 0x0073u), __byte_perm(p2, p3, 0x0073u), 0x5410u);
+}
+
+// Per byte of u, zero exactly when the byte is A, C, G or T in either case.
+// m = u & 0x06060606 holds the code bits (1, 2).  With the code and case
+// bits masked off (0xD9), a, c and g leave 0x41 and t leaves 0x50, so the
+// byte is compared with 0x41 + 15 [code == 2].
+__device__ __forceinline__ uint32_t letter_miss(uint32_t u, uint32_t m) {
+    const uint32_t t2 = (m >> 2) & ~(m >> 1) & 0x01010101u;
+    return (u & 0xD9D9D9D9u) ^ (t2 * 15u + 0x41414141u);
+}
+
+// 32 ASCII bytes (byte j of u[i] = base 4 i + j) -> the hi, lo and N planes
+// of one word.  The 2-bit code is (byte >> 1) & 3 (A 0, C 1, T 2, G 3).
+// Words are taken in pairs: their code bits are merged into one word
+// (word b's shifted up a nibble) and each plane's 8 bits gathered by one
+// multiply.  The N plane is built only when some byte is not a base; the
+// code bits of non-bases are cleared.
+__device__ __forceinline__ void pack32(const uint32_t *u, uint32_t &hi, uint32_t &lo, uint32_t &nn) {
+    uint32_t pl[4], ph[4], miss = 0;
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        const uint32_t a = u[2 * p], b = u[2 * p + 1];
+        const uint32_t ma = a & 0x06060606u, mb = b & 0x06060606u;
+        const uint32_t v = mb * 16u + ma;   // bits 1, 2 (word a) and 5, 6 (word b) of each byte
+        pl[p] = gather_pair((v >> 1) & 0x11111111u);
+        ph[p] = gather_pair((v >> 2) & 0x11111111u);
+        miss |= letter_miss(a, ma) | letter_miss(b, mb);
+    }
+    lo = top_bytes(pl[0], pl[1], pl[2], pl[3]);
+    hi = top_bytes(ph[0], ph[1], ph[2], ph[3]);
+    nn = 0;
+    if (miss) {
+        uint32_t pn[4];
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            const uint32_t a = u[2 * p], b = u[2 * p + 1];
+            const uint32_t xa = letter_miss(a, a & 0x06060606u), xb = letter_miss(b, b & 0x06060606u);
+            // high bit of each byte: the byte is not a base
+            const uint32_t za = (((xa & 0x7f7f7f7fu) + 0x7f7f7f7fu) | xa) & 0x80808080u;
+            const uint32_t zb = (((xb & 0x7f7f7f7fu) + 0x7f7f7f7fu) | xb) & 0x80808080u;
+            pn[p] = gather_pair((za >> 7) | (zb >> 3));
+        }
+        nn = top_bytes(pn[0], pn[1], pn[2], pn[3]);
+        hi &= ~nn;
+        lo &= ~nn;
+    }
 }
 
 // Word w of the batch.  Words below H/32 hold the halo region: 'N' padding
@@ -78,16 +114,7 @@ k_pack(const uint8_t *__restrict__ halo, uint32_t hlen, uint32_t H, const uint8_
             const uint4 *v = reinterpret_cast<const uint4 *>(seg + o);
             const uint4 a = __ldg(v), c = __ldg(v + 1);
             const uint32_t u[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                uint32_t h4, l4, n4;
-                pack4(u[j], h4, l4, n4);
-                hi |= h4 << (4 * j);
-                lo |= l4 << (4 * j);
-                nn |= n4 << (4 * j);
-            }
-            hi &= ~nn;
-            lo &= ~nn;
+            pack32(u, hi, lo, nn);
         } else {
             for (uint32_t b = 0; b < 32; b++)
                 pack_byte(o + b < slen ? seg[o + b] : 'N', b, hi, lo, nn);
@@ -218,16 +245,7 @@ k_pack_dir(const uint8_t *__restrict__ halo, uint32_t hlen, uint32_t H, const ui
                 const uint64_t o = (w - hw) * 32;
                 if (ALIGNED && o + 32 <= slen) {
                     const uint32_t u[8] = {va[t].x, va[t].y, va[t].z, va[t].w, vc[t].x, vc[t].y, vc[t].z, vc[t].w};
-#pragma unroll
-                    for (int j = 0; j < 8; j++) {
-                        uint32_t h4, l4, n4;
-                        pack4(u[j], h4, l4, n4);
-                        hi |= h4 << (4 * j);
-                        lo |= l4 << (4 * j);
-                        nn |= n4 << (4 * j);
-                    }
-                    hi &= ~nn;
-                    lo &= ~nn;
+                    pack32(u, hi, lo, nn);
                 } else {
                     for (uint32_t b = 0; b < 32; b++)
                         pack_byte(o + b < slen ? seg[o + b] : 'N', b, hi, lo, nn);
