@@ -60,12 +60,26 @@ ifa_status bfail(ifa_handle *h, ifa_status st, const std::string &msg) {
                          std::string(#call) + ": " + cudaGetErrorString(e_));              \
     } while (0)
 
-// One persistent launch: CTAs pull items from w.queue until it runs dry.
-// Items [0, n_items - n_brute_items) are seed tiles, the rest brute-force
-// (chunk, tile) items in chunk-major order, so a CTA reloads its shared
-// query chunk rarely.
-template <int WMAX, bool MULTI>
-__global__ void __launch_bounds__(kBThreads, IFA_BATCH_MIN_CTAS)
+// Resident CTAs per SM of the seed-only persistent kernel: the seed scan's
+// own bound (48 registers at 5; see k_seed_scan).
+#ifndef IFA_BATCH_SEED_MIN_CTAS
+#define IFA_BATCH_SEED_MIN_CTAS 5
+#endif
+
+// Which items a persistent launch takes: kBoth (one kernel for the whole
+// batch: serving), kSeedOnly or kBruteOnly (the batch call runs one kernel
+// per kind back to back, each held to the register budget its own scan
+// wants; the fused kernel must fit both in 64 registers and spills).
+enum BatchPart { kBoth = 0, kSeedOnly = 1, kBruteOnly = 2 };
+
+// One persistent launch: CTAs pull items from a device queue until it runs
+// dry.  Items [0, n_items - n_brute_items) are seed tiles, the rest
+// brute-force (chunk, tile) items in chunk-major order, so a CTA reloads its
+// shared query chunk rarely.  kBoth and kSeedOnly count items in
+// w.queue[0]; kBruteOnly counts its own in w.queue[1], from the first
+// brute-force item.
+template <int WMAX, bool MULTI, int PART>
+__global__ void __launch_bounds__(kBThreads, PART == kSeedOnly ? IFA_BATCH_SEED_MIN_CTAS : IFA_BATCH_MIN_CTAS)
 k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
     using namespace brute;
     extern __shared__ uint4 smem4[];
@@ -84,12 +98,14 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
     Smem m{};
     uint32_t nent = 0, e0 = 0, lmin = 0, lmax = 0;
     const uint32_t n_seed = w.n_items - w.n_brute_items;
+    const uint32_t item_end = PART == kSeedOnly ? n_seed : w.n_items;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(w.queue, 1u);
+        if (threadIdx.x == 0)
+            s_item = PART == kBruteOnly ? n_seed + atomicAdd(w.queue + 1, 1u) : atomicAdd(w.queue, 1u);
         __syncthreads();
         const uint32_t item = s_item;
-        if (item >= w.n_items) break;
-        if (item < n_seed) {
+        if (item >= item_end) break;
+        if (PART == kSeedOnly || (PART == kBoth && item < n_seed)) {
             const uint64_t lo = w.s_block0 + static_cast<uint64_t>(item) * w.tile_sblocks;
             const uint64_t hi = lo + w.tile_sblocks < w.s_block_end ? lo + w.tile_sblocks : w.s_block_end;
             seed::seed_blocks<WMAX>(b, ft, w.tabs, w.emh, w.step, kSPerEntry, sink, wh, lo + warp, hi,
@@ -124,41 +140,58 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
     if (lane == 0 && ncand) atomicAdd(w.candidates, ncand);
 }
 
-template <int WMAX>
+template <int WMAX, int PART>
 cudaError_t launch_batch_t(const Batch &b, const BatchWork &w, const QueryTable &bt, const QueryTable &ft,
                            const HitSink &sink, int grid, size_t smem, cudaStream_t st) {
     if (sink.q2r)
-        k_batch<WMAX, true><<<grid, kBThreads, smem, st>>>(b, w, bt, ft, sink);
+        k_batch<WMAX, true, PART><<<grid, kBThreads, smem, st>>>(b, w, bt, ft, sink);
     else
-        k_batch<WMAX, false><<<grid, kBThreads, smem, st>>>(b, w, bt, ft, sink);
+        k_batch<WMAX, false, PART><<<grid, kBThreads, smem, st>>>(b, w, bt, ft, sink);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(uint32_t wmax, const Batch &b, const BatchWork &w, const QueryTable &bt,
-                         const QueryTable &ft, const HitSink &sink, int grid, size_t smem, cudaStream_t st) {
+template <int PART>
+cudaError_t launch_batch_p(uint32_t wmax, const Batch &b, const BatchWork &w, const QueryTable &bt,
+                           const QueryTable &ft, const HitSink &sink, int grid, size_t smem, cudaStream_t st) {
     switch (wmax) {
-    case 1: return launch_batch_t<1>(b, w, bt, ft, sink, grid, smem, st);
-    case 2: return launch_batch_t<2>(b, w, bt, ft, sink, grid, smem, st);
-    case 4: return launch_batch_t<4>(b, w, bt, ft, sink, grid, smem, st);
-    case 8: return launch_batch_t<8>(b, w, bt, ft, sink, grid, smem, st);
+    case 1: return launch_batch_t<1, PART>(b, w, bt, ft, sink, grid, smem, st);
+    case 2: return launch_batch_t<2, PART>(b, w, bt, ft, sink, grid, smem, st);
+    case 4: return launch_batch_t<4, PART>(b, w, bt, ft, sink, grid, smem, st);
+    case 8: return launch_batch_t<8, PART>(b, w, bt, ft, sink, grid, smem, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-int batch_grid(uint32_t wmax) {
+cudaError_t launch_batch(uint32_t wmax, const Batch &b, const BatchWork &w, const QueryTable &bt,
+                         const QueryTable &ft, const HitSink &sink, int grid, size_t smem, cudaStream_t st,
+                         int part = kBoth) {
+    if (part == kSeedOnly) return launch_batch_p<kSeedOnly>(wmax, b, w, bt, ft, sink, grid, smem, st);
+    if (part == kBruteOnly) return launch_batch_p<kBruteOnly>(wmax, b, w, bt, ft, sink, grid, smem, st);
+    return launch_batch_p<kBoth>(wmax, b, w, bt, ft, sink, grid, smem, st);
+}
+
+template <int PART>
+int batch_grid_p(uint32_t wmax, size_t smem) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = brute::kScanSmemBudget;
     cudaError_t e = cudaSuccess;
     switch (wmax) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<1, true>, kBThreads, smem); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<2, true>, kBThreads, smem); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<4, true>, kBThreads, smem); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<8, true>, kBThreads, smem); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<1, false, PART>, kBThreads, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<2, false, PART>, kBThreads, smem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<4, false, PART>, kBThreads, smem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<8, false, PART>, kBThreads, smem); break;
     }
     if (e != cudaSuccess || per < 1) per = 1;
     return sms * per;
+}
+
+// SMs x resident CTAs of the persistent kernel for `part` (the seed-only
+// kernel takes no dynamic shared memory).
+int batch_grid(uint32_t wmax, int part = kBoth) {
+    if (part == kSeedOnly) return batch_grid_p<kSeedOnly>(wmax, 0);
+    if (part == kBruteOnly) return batch_grid_p<kBruteOnly>(wmax, brute::kScanSmemBudget);
+    return batch_grid_p<kBoth>(wmax, brute::kScanSmemBudget);
 }
 
 }  // namespace
@@ -460,7 +493,7 @@ ifa_status build_plan(ifa_handle *h) {
     }
 
     // work descriptor and tiles
-    if (!B.d_queue) BCK(h, cudaMalloc(&B.d_queue, sizeof(unsigned int)));
+    if (!B.d_queue) BCK(h, cudaMalloc(&B.d_queue, 2 * sizeof(unsigned int)));   // seed and brute-force items
     if (!B.d_cand) BCK(h, cudaMalloc(&B.d_cand, sizeof(unsigned long long)));
     B.grid = batch_grid(wmax);
     BatchWork &W = B.work;
@@ -762,8 +795,16 @@ ifa_status ifa_batch_run(ifa_handle *h, ifa_batch_kind kind, ifa_set_result *per
             const size_t smem = brute::kScanSmemBudget;
             e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                cudaError_t e1 = cudaMemsetAsync(B.d_queue, 0, sizeof(unsigned int), h->stream);
-                cudaError_t e2 = launch_batch(B.wmax, b, B.work, bt, ft, sink, B.grid, smem, h->stream);
+                cudaError_t e1 = cudaMemsetAsync(B.d_queue, 0, 2 * sizeof(unsigned int), h->stream);
+                // one persistent kernel per kind of item, each at its own
+                // register budget, back to back
+                cudaError_t e2 = cudaSuccess;
+                if (B.work.n_brute_items)
+                    e2 = launch_batch(B.wmax, b, B.work, bt, ft, sink, batch_grid(B.wmax, kBruteOnly), smem,
+                                      h->stream, kBruteOnly);
+                if (e2 == cudaSuccess && B.work.n_items > B.work.n_brute_items)
+                    e2 = launch_batch(B.wmax, b, B.work, bt, ft, sink, batch_grid(B.wmax, kSeedOnly), 0, h->stream,
+                                      kSeedOnly);
                 // the tensor-core sets, every row at its own maxSubs
                 if (e2 == cudaSuccess && B.tc_rows)
                     e2 = launch_scan_tc(b, B.d_tcA, B.d_tcmeta, B.tc_rows, B.tc_lpad, kSPerEntry, sink,
