@@ -38,8 +38,9 @@ namespace {
 
 constexpr int kBThreads = 256;
 constexpr int kBWarps = kBThreads / kWarp;
-// Resident CTAs per SM the persistent kernel's registers are held to.
-// Measured on B300 (128 sets vs 5 Gbp, persistent launch): no bound
+// Resident CTAs per SM the brute-force persistent kernel's registers are
+// held to: 4 (62-64 registers, no spills up to 128-base queries).  When one
+// kernel took both kinds of item it measured (128 sets vs 5 Gbp): no bound
 // (64 registers, 124 bytes spilled) 3.96 s; 4 CTAs (64 registers, 16-32
 // bytes spilled) 3.76 s; 3 CTAs (80 registers, none spilled) 4.21 s.
 #ifndef IFA_BATCH_MIN_CTAS
@@ -66,18 +67,17 @@ ifa_status bfail(ifa_handle *h, ifa_status st, const std::string &msg) {
 #define IFA_BATCH_SEED_MIN_CTAS 5
 #endif
 
-// Which items a persistent launch takes: kBoth (one kernel for the whole
-// batch: serving), kSeedOnly or kBruteOnly (the batch call runs one kernel
-// per kind back to back, each held to the register budget its own scan
-// wants; the fused kernel must fit both in 64 registers and spills).
-enum BatchPart { kBoth = 0, kSeedOnly = 1, kBruteOnly = 2 };
+// Which items a persistent launch takes.  The batch and serving calls run
+// one kernel per kind back to back, each held to the register budget its
+// own scan wants: one kernel for both kinds had to fit both in 64
+// registers and spilled (256 sets vs 16 Gbp: 27.1 s fused, 19.1 s split).
+enum BatchPart { kSeedOnly = 1, kBruteOnly = 2 };
 
-// One persistent launch: CTAs pull items from a device queue until it runs
-// dry.  Items [0, n_items - n_brute_items) are seed tiles, the rest
-// brute-force (chunk, tile) items in chunk-major order, so a CTA reloads its
-// shared query chunk rarely.  kBoth and kSeedOnly count items in
-// w.queue[0]; kBruteOnly counts its own in w.queue[1], from the first
-// brute-force item.
+// One persistent launch: CTAs pull items of their kind from a device queue
+// until it runs dry.  Items [0, n_items - n_brute_items) are seed tiles
+// (counted in w.queue[0]), the rest brute-force (chunk, tile) items in
+// chunk-major order, so a CTA reloads its shared query chunk rarely
+// (counted in w.queue[1], from the first brute-force item).
 template <int WMAX, bool MULTI, int PART>
 __global__ void __launch_bounds__(kBThreads, PART == kSeedOnly ? IFA_BATCH_SEED_MIN_CTAS : IFA_BATCH_MIN_CTAS)
 k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
@@ -105,7 +105,7 @@ k_batch(Batch b, BatchWork w, QueryTable bt, QueryTable ft, HitSink sink) {
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= item_end) break;
-        if (PART == kSeedOnly || (PART == kBoth && item < n_seed)) {
+        if (PART == kSeedOnly) {
             const uint64_t lo = w.s_block0 + static_cast<uint64_t>(item) * w.tile_sblocks;
             const uint64_t hi = lo + w.tile_sblocks < w.s_block_end ? lo + w.tile_sblocks : w.s_block_end;
             seed::seed_blocks<WMAX>(b, ft, w.tabs, w.emh, w.step, kSPerEntry, sink, wh, lo + warp, hi,
@@ -164,10 +164,9 @@ cudaError_t launch_batch_p(uint32_t wmax, const Batch &b, const BatchWork &w, co
 
 cudaError_t launch_batch(uint32_t wmax, const Batch &b, const BatchWork &w, const QueryTable &bt,
                          const QueryTable &ft, const HitSink &sink, int grid, size_t smem, cudaStream_t st,
-                         int part = kBoth) {
+                         int part) {
     if (part == kSeedOnly) return launch_batch_p<kSeedOnly>(wmax, b, w, bt, ft, sink, grid, smem, st);
-    if (part == kBruteOnly) return launch_batch_p<kBruteOnly>(wmax, b, w, bt, ft, sink, grid, smem, st);
-    return launch_batch_p<kBoth>(wmax, b, w, bt, ft, sink, grid, smem, st);
+    return launch_batch_p<kBruteOnly>(wmax, b, w, bt, ft, sink, grid, smem, st);
 }
 
 template <int PART>
@@ -187,20 +186,29 @@ int batch_grid_p(uint32_t wmax, size_t smem) {
 }
 
 // SMs x resident CTAs of the persistent kernel for `part` (the seed-only
-// kernel takes no dynamic shared memory).
-int batch_grid(uint32_t wmax, int part = kBoth) {
+// kernel takes no dynamic shared memory).  Tiles are sized for the
+// brute-force kernel's grid.
+int batch_grid(uint32_t wmax, int part = kBruteOnly) {
     if (part == kSeedOnly) return batch_grid_p<kSeedOnly>(wmax, 0);
-    if (part == kBruteOnly) return batch_grid_p<kBruteOnly>(wmax, brute::kScanSmemBudget);
-    return batch_grid_p<kBoth>(wmax, brute::kScanSmemBudget);
+    return batch_grid_p<kBruteOnly>(wmax, brute::kScanSmemBudget);
 }
 
 }  // namespace
 
 namespace ifa {
-cudaError_t launch_batch_kernel(uint32_t wmax, const Batch &b, const BatchWork &w, const QueryTable &bt,
-                                const QueryTable &ft, const HitSink &sink, int grid, size_t smem,
-                                cudaStream_t st) {
-    return launch_batch(wmax, b, w, bt, ft, sink, grid, smem, st);
+cudaError_t launch_batch_kernels(uint32_t wmax, const Batch &b, const BatchWork &w, const QueryTable &bt,
+                                 const QueryTable &ft, const HitSink &sink, cudaStream_t st, int *launches) {
+    cudaError_t e = cudaSuccess;
+    if (w.n_brute_items) {
+        e = launch_batch(wmax, b, w, bt, ft, sink, batch_grid(wmax, kBruteOnly), brute::kScanSmemBudget, st,
+                         kBruteOnly);
+        if (launches) (*launches)++;
+    }
+    if (e == cudaSuccess && w.n_items > w.n_brute_items) {
+        e = launch_batch(wmax, b, w, bt, ft, sink, batch_grid(wmax, kSeedOnly), 0, st, kSeedOnly);
+        if (launches) (*launches)++;
+    }
+    return e;
 }
 int batch_kernel_grid(uint32_t wmax) { return batch_grid(wmax); }
 }  // namespace ifa

@@ -119,10 +119,12 @@ namespace ifa {
 ifa_status upload_queries(ifa_handle *h);
 // Free the multi-set store and plan.
 void batch_release(ifa_handle *h);
-// The persistent multi-set kernel (batch.cu), for the serving loop.
-cudaError_t launch_batch_kernel(uint32_t wmax, const Batch &b, const BatchWork &w, const QueryTable &bt,
-                                const QueryTable &ft, const HitSink &sink, int grid, size_t smem,
-                                cudaStream_t st);
+// The persistent multi-set kernels (batch.cu), for the serving loop: the
+// brute-force items, then the seed items, each kind in its own persistent
+// launch (w.queue: two counters, zeroed by the caller).  *launches gets
+// the kernels launched.
+cudaError_t launch_batch_kernels(uint32_t wmax, const Batch &b, const BatchWork &w, const QueryTable &bt,
+                                 const QueryTable &ft, const HitSink &sink, cudaStream_t st, int *launches);
 int batch_kernel_grid(uint32_t wmax);
 void encode_entry(const std::string &q, bool rc, uint32_t wmax, uint32_t s_e, uint4 *out, uint32_t *meta);
 void tc_operand(const std::vector<std::string> &qs, uint32_t lpad, std::vector<uint8_t> &out);

@@ -311,7 +311,7 @@ ifa_status ifa_serve_start(ifa_handle *h, uint32_t n_slices, uint64_t hbm_budget
     S.scanned_query_bases = 0;
     S.plan_s = 0;
     S.scan_s = 0;
-    SCK(h, cudaMalloc(&S.d_queue, sizeof(unsigned int)));
+    SCK(h, cudaMalloc(&S.d_queue, 2 * sizeof(unsigned int)));   // brute-force and seed items
     SCK(h, cudaMalloc(&S.d_cand, sizeof(unsigned long long)));
     SCK(h, cudaMemsetAsync(S.d_cand, 0, sizeof(unsigned long long), h->stream));
     // the store's piece table on the device
@@ -435,9 +435,10 @@ ifa_status ifa_serve_step(ifa_handle *h, uint32_t *n_active, uint32_t *n_complet
         w.candidates = S.d_cand;
         const Batch b = make_batch(B.ref, B.nbases, 0, B.d_pieces, B.d_pieces_n);
         const double t1 = now_s();
-        SCK(h, cudaMemsetAsync(S.d_queue, 0, sizeof(unsigned int), h->stream));
-        SCK(h, launch_batch_kernel(S.wmax, b, w, S.bt, S.ft, S.sink, S.grid, brute::kScanSmemBudget, h->stream));
-        h->stats.kernel_launches += 1;
+        SCK(h, cudaMemsetAsync(S.d_queue, 0, 2 * sizeof(unsigned int), h->stream));
+        int nl = 0;
+        SCK(h, launch_batch_kernels(S.wmax, b, w, S.bt, S.ft, S.sink, h->stream, &nl));
+        h->stats.kernel_launches += nl;
         if (S.clip_pct) {
             // soft-clipped windows of the pieces whose first base is in this
             // slice, every active entry exhaustively at its own maxSubs
