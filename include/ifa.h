@@ -64,7 +64,8 @@ typedef enum {
 typedef enum {
     IFA_BRUTE_AUTO = 0,    /* tensor cores from 32 queries on when eligible (queries of at most 64 bases) and
                               hits are sparse: the set's mean probability that a random window hits, over
-                              its queries (uniform bases, Binomial(L, 3/4) <= maxSubs), is at most 2e-4 */
+                              its queries (uniform bases, Binomial(L, 3/4) <= maxSubs; with per-query
+                              values, the largest), is at most 2e-4 */
     IFA_BRUTE_POPC = 1,    /* bit-plane XOR/OR/popcount kernel */
     IFA_BRUTE_TENSOR = 2   /* one-hot GEMM on the tensor cores; queries of at most 64 bases */
 } ifa_brute_kernel;
