@@ -217,7 +217,8 @@ ifa_status ifa_set_max_subs(ifa_handle *h, uint32_t max_subs);
  * of ifa_set_max_subs.  ifa_load_queries also goes back to it (the new
  * queries have no value yet).  Hits already reported are unchanged.
  * Errors: INVALID_ARG (NULL handle, n != loaded query count, NULL array
- * with n > 0); CUDA/OOM from re-uploading the query table. */
+ * with n > 0); BAD_STATE when query sets are registered (ifa_set_add: each
+ * set carries its own maxSubs); CUDA/OOM from re-uploading the query table. */
 ifa_status ifa_set_query_max_subs(ifa_handle *h, const uint32_t *max_subs, uint32_t n);
 
 /* Brute force, indexed, or automatic (Discussion): by rates measured on

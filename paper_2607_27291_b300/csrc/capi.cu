@@ -565,6 +565,9 @@ ifa_status ifa_set_query_max_subs(ifa_handle *h, const uint32_t *max_subs, uint3
         return IFA_OK;
     }
     if (!max_subs) return fail(h, IFA_ERR_INVALID_ARG, "max_subs is NULL");
+    // query sets keep their own maxSubs in the same per-query table
+    if (!h->batch.sets.empty())
+        return fail(h, IFA_ERR_BAD_STATE, "per-query maxSubs is for streaming; query sets carry their own");
     if (n != h->qs.size()) return fail(h, IFA_ERR_INVALID_ARG, "one maxSubs per loaded query");
     CK(h, cudaSetDevice(h->dev));
     // in-flight scans read the query table that the next push re-uploads

@@ -186,3 +186,11 @@ def test_argument_errors():
         P.ifa_set_query_max_subs(h, [1, 2])
     finally:
         P.ifa_destroy(h)
+    # query sets carry their own maxSubs: per-query values are refused there
+    h = P.ifa_create(hit_capacity=1 << 16, segment_bytes=1 << 20)
+    try:
+        P.ifa_set_add(h, [b"ACGTACGTAC"], 2, P.IFA_MODE_BRUTE)
+        with pytest.raises(P.IfaError):
+            P.ifa_set_query_max_subs(h, [1])
+    finally:
+        P.ifa_destroy(h)
