@@ -155,3 +155,24 @@ def test_noalloc_rejects_misaligned_buffers_before_device():
             P.ifa_scan_brute_noalloc(0, q, 0x40000, 64, pieces, 1, hits, 16, counters, per_query)
         assert ei.value.status == P.IFA_ERR_INVALID_ARG
         assert "aligned" in str(ei.value)
+
+
+HANDLE_CALLS = ["ifa_set_stream", "ifa_load_queries", "ifa_set_max_subs", "ifa_set_query_max_subs",
+                "ifa_set_mode", "ifa_push_segment", "ifa_prime_halo", "ifa_flush", "ifa_drain_hits",
+                "ifa_poll_hits", "ifa_get_digest", "ifa_reset_results", "ifa_get_stats", "ifa_get_query_plan",
+                "ifa_ref_append", "ifa_ref_reserve", "ifa_ref_reset", "ifa_set_add", "ifa_batch_run",
+                "ifa_serve_start", "ifa_serve_submit", "ifa_serve_step", "ifa_serve_poll", "ifa_serve_drain",
+                "ifa_serve_stats", "ifa_serve_stop", "ifa_serve_cancel"]
+
+
+def test_every_handle_call_rejects_a_null_handle():
+    """Each entry point that takes a handle returns INVALID_ARG for NULL (no
+    device is touched), whatever its other arguments."""
+    import ctypes as C
+    for name in HANDLE_CALLS:
+        fn = getattr(P.lib(), name)
+        args = []
+        for t in fn.argtypes:
+            args.append(None if (t is C.c_void_p or t is C.c_char_p or hasattr(t, "contents")) else t(0))
+        assert fn(*args) == P.IFA_ERR_INVALID_ARG, name
+    P.lib().ifa_destroy(None)   # a no-op
